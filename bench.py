@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""FastID all-pairs comparison benchmark on GB300.
+
+Metric: query x reference comparisons per second at N loci, bit-exact
+(results are checked against the CPU oracle on a sample by the tests and by
+--check here).  One step = one pass of the whole path over one batch of
+queries: pack the queries' contributor alleles, build the mixtures (OR),
+compare every query with every resident reference and reduce to the
+per-query top-k under a threshold.  The reference database is resident in
+HBM (loaded once, outside the timed region).
+
+Default workload: 2048 unknowns (1024 individuals, 1024 mixtures of 2-5
+people) x 20,000,000 references, N = 2048 loci, top-32, threshold 512.
+
+    python bench.py [--steps K] [--warmup W] [--form plain|tensor|auto]
+    python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
+    torchrun --nproc-per-node N bench.py --gpus N   (N independent replicas)
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+# ----------------------------------------------------------------------------
+# Workloads
+# ----------------------------------------------------------------------------
+
+WORKLOADS = {
+    "c3": dict(workload="2048q_x_20M_refs_N2048_top32_T512", n_q=2048, n_refs=20_000_000, n_loci=2048,
+               k=32, threshold=512, cfg=3),
+    "c2": dict(workload="2048mix_x_1M_refs_N4096_top16", n_q=2048, n_refs=1_000_000, n_loci=4096,
+               k=16, threshold=0xFFFFFFFF, cfg=2),
+    "c1": dict(workload="64q_x_10k_refs_N1024_top32", n_q=64, n_refs=10_000, n_loci=1024,
+               k=32, threshold=0xFFFFFFFF, cfg=1),
+}
+
+METRIC = "query x reference comparisons/s at N loci, bit-exact"
+UNIT = "comparisons/s"
+
+# Peak popcount rate of the plain form's bound: POPC issues 16 results per
+# clock per SM (integer-pipe throughput table for compute capability 10.x),
+# 152 SMs, at the maximum SM clock.
+POPC_PER_CLK_PER_SM = 16
+
+
+def recipe_for(name: str, n_refs: int | None = None, n_q: int | None = None):
+    w = WORKLOADS[name]
+    n_refs = w["n_refs"] if n_refs is None else n_refs
+    n_q = w["n_q"] if n_q is None else n_q
+    seed = gen.config_seed(w["cfg"])
+    if name == "c3":
+        return gen.recipe_c3(seed, n_refs=n_refs, n_q=n_q, n_loci=w["n_loci"])
+    if name == "c2":
+        return gen.recipe_c2(seed, n_refs=n_refs, n_q=n_q, n_loci=w["n_loci"])
+    r = gen.recipe_individuals(n_q, n_refs, w["n_loci"], seed, n_planted=min(8, n_q))
+    return r
+
+
+def build_db(searcher, seed: int, n_refs: int, n_loci: int, flags: int = 0, chunk: int = 1 << 20):
+    """Generate the reference database on the device (gen/gen_gpu.cu), pack it
+    with fastid_pack and load it.  Returns (RefDB, thresholds)."""
+    import torch
+    from paper_1707_00516_gb300 import binding as B
+    thr = gen.maf_thresholds(seed, n_loci)
+    dev = searcher.device
+    thr_dev = torch.from_numpy(thr.view(np.int32)).to(dev)
+    w = (n_loci + 63) // 64
+    packed = torch.empty((n_refs, w), dtype=torch.int64, device=dev)
+    chunk = min(chunk, n_refs)
+    alle = torch.empty((chunk, n_loci), dtype=torch.uint8, device=dev)
+    for r0 in range(0, n_refs, chunk):
+        n = min(chunk, n_refs - r0)
+        gen.allele_rows_device(seed, gen.STREAM_DB, thr_dev, alle[:n], row0=r0)
+        B.fastid_pack(searcher.ctx, alle[:n], n_loci, packed[r0:r0 + n])
+    db = B.fastid_load_refs(searcher.ctx, packed, n_loci, flags)
+    torch.cuda.synchronize()
+    del packed, alle
+    torch.cuda.empty_cache()
+    return db, thr
+
+
+def query_inputs(recipe, thr):
+    """Host arrays of a recipe: contributor alleles, group offsets, modes."""
+    src = gen.source_alleles(recipe, thr)
+    return src, recipe.offsets.astype(np.int32), recipe.modes.astype(np.uint8)
+
+
+# ----------------------------------------------------------------------------
+# Clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# Distributed helpers (independent replicas; barrier + max over ranks only)
+# ----------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    world, rank, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return world, rank
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle legs
+# ----------------------------------------------------------------------------
+
+def oracle_sample_step(q_alleles: np.ndarray, modes: np.ndarray, seed: int, n_refs: int, thr: np.ndarray,
+                       sample_rows: np.ndarray, k: int, threshold: int):
+    """The oracle on a bounded sample: every query against the sampled
+    references (per-locus scores, then top-k over the sample)."""
+    import oracle
+    R = gen.allele_rows(seed, gen.STREAM_DB, sample_rows, thr)
+    t0 = time.perf_counter()
+    mis, une = oracle.scores(R, q_alleles)
+    s = oracle.select(mis, une, modes)
+    oracle.topk(s, k, threshold, ref_ids=sample_rows)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(w: dict, recipe, thr, target_s: float = 12.0):
+    import oracle
+    src, off, modes = query_inputs(recipe, thr)
+    q = oracle.mix(src, off)
+    seed = gen.config_seed(w["cfg"])
+    rng = np.random.default_rng(seed)
+    S = 16
+    t = oracle_sample_step(q, modes, seed, w["n_refs"], thr, np.sort(rng.choice(w["n_refs"], S, replace=False)),
+                           w["k"], w["threshold"])
+    S = int(min(4096, max(16, S * target_s / max(t, 1e-3))))
+    rows = np.sort(rng.choice(w["n_refs"], S, replace=False))
+    t = oracle_sample_step(q, modes, seed, w["n_refs"], thr, rows, w["k"], w["threshold"])
+    return {"value": q.shape[0] * S / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"all {q.shape[0]} queries x {S} sampled references (per-locus scores + top-{w['k']}), "
+                      f"{t:.1f} s"}
+
+
+def run_reference(args, w):
+    """--impl reference: the CPU oracle, each step a bounded sample."""
+    world, rank, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    import oracle
+    oracle.build()
+    seed = gen.config_seed(w["cfg"])
+    recipe = recipe_for(args.config)
+    thr = gen.maf_thresholds(seed, w["n_loci"])
+    src, off, modes = query_inputs(recipe, thr)
+    q = oracle.mix(src, off)
+    rng = np.random.default_rng(seed + 1)
+    # size one step to about 8 s on this host
+    S = 16
+    t = oracle_sample_step(q, modes, seed, w["n_refs"], thr, np.sort(rng.choice(w["n_refs"], S, replace=False)),
+                           w["k"], w["threshold"])
+    S = int(min(4096, max(16, S * 8.0 / max(t, 1e-3))))
+    times = []
+    for i in range(args.warmup + args.steps):
+        rows = np.sort(rng.choice(w["n_refs"], S, replace=False))
+        dt = oracle_sample_step(q, modes, seed, w["n_refs"], thr, rows, w["k"], w["threshold"])
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = q.shape[0] * S * len(times) / tot
+    sample = f"per step: all {q.shape[0]} queries x {S} sampled references (per-locus scores + top-{w['k']})"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": w["workload"], "n_loci": w["n_loci"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("plain.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1707_00516_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes per launch of the main compare kernel from an ncu capture
+# (profiles/), keyed by form and workload, with the source hash it was taken
+# at.  A changed kernel reports null.
+NCU_TRAFFIC = {}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def run_gpu(args, w):
+    import torch
+    world, rank = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1707_00516_gb300 import binding as B
+    from paper_1707_00516_gb300.search import Searcher
+    from paper_1707_00516_gb300.build import build
+    gen.build_gpu()
+    build()
+
+    form = {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "auto": B.FORM_AUTO}[args.form]
+    s = Searcher(local, form)
+    seed = gen.config_seed(w["cfg"])
+    n_refs, n_loci, k, T = w["n_refs"], w["n_loci"], w["k"], w["threshold"]
+    flags = B.REFS_TENSOR if args.form == "tensor" else 0
+    db, thr = build_db(s, seed, n_refs, n_loci, flags)
+    recipe = recipe_for(args.config)
+    src, off, modes = query_inputs(recipe, thr)
+    n_q = recipe.n_queries
+    d_src = torch.from_numpy(src).to(dev)
+    d_off = torch.from_numpy(off).to(dev)
+    d_mod = torch.from_numpy(modes).to(dev)
+    sc = torch.empty((n_q, k), dtype=torch.int32, device=dev)
+    ix = torch.empty((n_q, k), dtype=torch.int64, device=dev)
+
+    def step():
+        q = s.build_queries(d_src, d_off, n_loci)
+        B.fastid_topk(s.ctx, db, q, d_mod, k, T, sc, ix)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clk = ClockSampler(local)
+    clk.start()
+    B.fastid_profile(s.ctx, True)
+    B.fastid_profile_read(s.ctx, reset=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world, dev)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world, dev)
+    ms = e0.elapsed_time(e1)
+    prof = B.fastid_profile_read(s.ctx, reset=True)
+    B.fastid_profile(s.ctx, False)
+    clocks = clk.stop()
+    st = B.fastid_sync_status(s.ctx)
+    if st != B.OK:
+        raise RuntimeError(f"device status {st} after the timed region")
+    ms_max = max_over_ranks(ms, world, dev)
+    pairs_per_step = n_q * n_refs
+    value = pairs_per_step * args.steps * world / (ms_max / 1e3)
+
+    # end to end through the host-buffer API
+    for _ in range(max(1, args.warmup // 2)):
+        s.search_host(db, src, off, modes, k, T)
+    barrier(world, dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, h2d, d2h = s.search_host(db, src, off, modes, k, T)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = pairs_per_step * args.steps * world / e2e_s
+
+    # roofline of the main compare kernel
+    peaks, peak_src = load_peaks()
+    main_ms = prof["main_ms"] / max(1, prof["main_launches"])
+    words32 = 2 * ((n_loci + 63) // 64)
+    popc = pairs_per_step * words32
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tpopc = POPC_PER_CLK_PER_SM * n_sms * sm_max * 1e6 / 1e12
+    achieved = popc / (main_ms / 1e3) / 1e12
+    key = f"plain/{args.config}"
+    tr = NCU_TRAFFIC.get(key)
+    traffic = tr[0] if tr and tr[1] == kernel_source_hash() else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tpopc, "unit": "Tpopc/s",
+                "frac": achieved / peak_tpopc, "traffic": traffic,
+                "kernel": "plain_kernel<EPI_TOPK>", "kernel_ms": main_ms,
+                "peak_source": f"{POPC_PER_CLK_PER_SM} POPC/clk/SM x {n_sms} SMs x {sm_max:.0f} MHz "
+                               f"(max SM clock, {peak_src})"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": w["workload"], "n_queries": n_q, "n_refs": n_refs, "n_loci": n_loci, "k": k,
+                       "threshold": T, "form": args.form, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (packed database %.2f GB)" % (n_refs * n_loci / 8 / 1e9)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(prof["all_launches"]),
+            "roofline": roofline, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, recipe, thr)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    db.close()
+    s.ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["plain", "tensor", "auto"], default="plain")
+    ap.add_argument("--config", choices=sorted(WORKLOADS), default="c3")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    w = WORKLOADS[args.config]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

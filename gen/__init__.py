@@ -247,3 +247,59 @@ def log_uniform_sizes(n: int, lo: int, hi: int, seed: int, salt: int) -> np.ndar
     u = rng.random(n)
     s = np.floor(np.exp(u * np.log(hi + 1))).astype(np.int64)
     return np.clip(s, lo, hi)
+
+
+# --------------------------------------------------------------------------
+# Device generator (gen/gen_gpu.cu), for databases too large for the host.
+# --------------------------------------------------------------------------
+
+import ctypes as _ct
+import os as _os
+import subprocess as _sp
+
+_GEN_DIR = _os.path.dirname(_os.path.abspath(__file__))
+_GEN_SRC = _os.path.join(_GEN_DIR, "gen_gpu.cu")
+_GEN_LIB = _os.path.join(_GEN_DIR, "libgen_gpu.so")
+_gen_lib = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile gen_gpu.cu for sm_103a into gen/libgen_gpu.so."""
+    if (not force and _os.path.exists(_GEN_LIB)
+            and _os.path.getmtime(_GEN_LIB) >= _os.path.getmtime(_GEN_SRC)):
+        return _GEN_LIB
+    nvcc = _os.path.join(_os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    tmp = _GEN_LIB + f".tmp{_os.getpid()}"
+    _sp.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
+             "-shared", _GEN_SRC, "-o", tmp], check=True)
+    _os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _gpu():
+    global _gen_lib
+    if _gen_lib is None:
+        if not _os.path.exists(_GEN_LIB):
+            raise RuntimeError("gen/libgen_gpu.so is missing: call gen.build_gpu()")
+        lib = _ct.CDLL(_GEN_LIB)
+        lib.gen_alleles.restype = _ct.c_int
+        lib.gen_alleles.argtypes = [_ct.c_uint64, _ct.c_uint64, _ct.c_void_p, _ct.c_int64, _ct.c_int64,
+                                    _ct.c_void_p, _ct.c_int32, _ct.c_void_p, _ct.c_int64, _ct.c_void_p]
+        _gen_lib = lib
+    return _gen_lib
+
+
+def allele_rows_device(seed: int, stream: int, thr_dev, out_dev, rows_dev=None, row0: int = 0,
+                       cuda_stream=None) -> None:
+    """Fill the uint8 CUDA tensor out_dev [n_rows, >= n_loci] with allele rows
+    row0 .. row0 + n_rows - 1 (or the int64 CUDA tensor rows_dev) of a stream;
+    thr_dev is the uint32 threshold table as an int32 CUDA tensor."""
+    import torch
+    n_rows = out_dev.shape[0]
+    n_loci = thr_dev.shape[0]
+    st = torch.cuda.current_stream() if cuda_stream is None else cuda_stream
+    err = _gpu().gen_alleles(seed & MASK64, stream, rows_dev.data_ptr() if rows_dev is not None else None,
+                             row0, n_rows, thr_dev.data_ptr(), n_loci, out_dev.data_ptr(),
+                             out_dev.stride(0), st.cuda_stream or None)
+    if err != 0:
+        raise RuntimeError(f"gen_alleles failed with cudaError {err}")

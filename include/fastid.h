@@ -1,0 +1,230 @@
+/*
+ * fastid.h -- C ABI of the GB300 FastID all-pairs comparison library.
+ *
+ * Method: Samsi et al., "A Linear Algebra Approach to Fast DNA Mixture
+ * Analysis Using GPUs" (arXiv:1707.00516).  Every unknown profile Q_q is
+ * compared with every known (reference) profile R_r over N SNP loci, as an
+ * overloaded matrix multiply (Sec. II-B), giving one of two integer scores per
+ * pair (Sec. II-A):
+ *
+ *   mode 0  FASTID_MODE_MISMATCH     popcount(R_r XOR Q_q)
+ *                                    (every minor-allele difference; used to
+ *                                    compare two individuals)
+ *   mode 1  FASTID_MODE_UNEXPLAINED  popcount(AND(XOR(R_r, Q_q), R_r))
+ *                                    = popcount(R_r AND NOT Q_q)      (Eq. 1;
+ *                                    reference alleles the query -- usually a
+ *                                    mixture -- does not explain)
+ *
+ * The score matrix is reduced on the device (the reduction Sec. IV proposes):
+ * per-query top-k (fastid_topk) or the list of pairs under a threshold
+ * (fastid_compare).  fastid_scores writes the full matrix for small problems.
+ *
+ * Conventions shared by every call:
+ *  - Profiles are packed bit vectors: locus l is bit (l mod 64) of 64-bit word
+ *    l / 64, least significant bit first (Sec. II-A's conversion to unsigned
+ *    words; the bit order is this library's reading).  A row has ld_words >=
+ *    ceil(N / 64) words; bits at loci >= N must be zero.
+ *  - "_dev" pointers are device memory of the context's device, owned by the
+ *    caller.  fastid_ctx and fastid_refdb are owned by the library.
+ *  - Every call is asynchronous on the given stream (a cudaStream_t; NULL is
+ *    the legacy default stream) and performs no host synchronisation, except
+ *    fastid_sync_status and fastid_destroy / fastid_free_refs (which
+ *    synchronise the device before freeing).
+ *  - Argument errors are returned synchronously (FASTID_EINVAL,
+ *    FASTID_EUNSUPPORTED) and nothing is enqueued.  Conditions found on the
+ *    device (hit-list overflow, a bounded wait that ran out) are recorded in
+ *    the context's status word and returned by fastid_sync_status.
+ *  - fastid_last_error returns a message for the last failing call of the
+ *    context (thread-local to the context, not to the caller).
+ *  - A context may be used from one host thread at a time.  Calls on
+ *    different streams may overlap on the device; each call uses its own
+ *    scratch memory, allocated stream-ordered on its stream.
+ */
+#ifndef FASTID_H
+#define FASTID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fastid_ctx fastid_ctx;
+typedef struct fastid_refdb fastid_refdb;
+typedef void *fastid_stream; /* cudaStream_t */
+
+typedef enum {
+    FASTID_OK = 0,
+    FASTID_EINVAL = 1,       /* bad argument                                   */
+    FASTID_ENOMEM = 2,       /* device or host allocation failed               */
+    FASTID_ECUDA = 3,        /* a CUDA runtime/driver call failed              */
+    FASTID_EOVERFLOW = 4,    /* hit list longer than its capacity              */
+    FASTID_ETIMEOUT = 5,     /* a bounded device-side wait ran out             */
+    FASTID_EUNSUPPORTED = 6, /* valid request this build/device cannot serve   */
+    FASTID_EDEVICE = 7       /* a device-side consistency check failed         */
+} fastid_status;
+
+enum { FASTID_MODE_MISMATCH = 0, FASTID_MODE_UNEXPLAINED = 1 };
+
+/* Compute form used by the comparison calls. */
+enum {
+    FASTID_FORM_AUTO = 0,   /* tensor form when the database holds its operand copy, else plain */
+    FASTID_FORM_PLAIN = 1,  /* packed words, AND + POPC on the integer pipes            */
+    FASTID_FORM_TENSOR = 2  /* 0/1 and +-1 operands in FP8 e4m3 on tcgen05, FP32 accum  */
+};
+
+/* fastid_load_refs flags */
+enum {
+    FASTID_REFS_TENSOR = 1u /* also build the FP8 operand copy used by the tensor form */
+};
+
+#define FASTID_MAX_K 32          /* largest k accepted by fastid_topk          */
+#define FASTID_MAX_LOCI 65536    /* largest N accepted                         */
+
+/* ---------------------------------------------------------------- context */
+
+/* Library version as MAJOR * 10000 + MINOR * 100 + PATCH. */
+int32_t fastid_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *fastid_status_string(fastid_status s);
+
+/* Create a context on CUDA device `device` (makes it current for the calling
+ * thread).  *out receives the context.  Errors: EINVAL (out NULL, bad
+ * device), ECUDA, ENOMEM. */
+fastid_status fastid_create(fastid_ctx **out, int32_t device);
+
+/* Synchronise the device and free the context.  NULL is accepted. */
+fastid_status fastid_destroy(fastid_ctx *ctx);
+
+/* Message describing the last failure on ctx ("" if none). */
+const char *fastid_last_error(const fastid_ctx *ctx);
+
+/* Choose the compute form for later comparison calls (FASTID_FORM_*). */
+fastid_status fastid_set_form(fastid_ctx *ctx, int32_t form);
+
+/* Synchronise `stream`, read and clear the context's device status word.
+ * Returns FASTID_OK, FASTID_EOVERFLOW, FASTID_ETIMEOUT or FASTID_EDEVICE
+ * (the most severe condition recorded since the last call), or ECUDA. */
+fastid_status fastid_sync_status(fastid_ctx *ctx, fastid_stream stream);
+
+/* Kernel timing and launch counting (off by default).  While enabled, each
+ * comparison call records CUDA events around its main compare kernel on the
+ * call's stream, and every kernel the library launches is counted.
+ * fastid_profile_read synchronises those events, returns the summed duration
+ * of the main kernels (ms), the number of main-kernel launches and the total
+ * number of kernels launched since the last reset (any output may be NULL),
+ * and with reset != 0 clears the counters. */
+fastid_status fastid_profile(fastid_ctx *ctx, int32_t enable);
+fastid_status fastid_profile_read(fastid_ctx *ctx, double *main_ms, int64_t *main_launches,
+                                  int64_t *all_launches, int32_t reset);
+
+/* ------------------------------------------------------------- profiles */
+
+/*
+ * Pack 0/1 alleles into bit vectors (Sec. II-A; conversion of alleles to an
+ * array of unsigned integers, 512 SNPs -> 16 uint32 = 8 uint64 words).
+ *  alleles_dev  uint8 [n][ld_alleles]; entry (i, l) for l < n_loci is the
+ *               allele indicator of locus l (any nonzero byte counts as 1).
+ *  packed_dev   uint64 [n][ld_words], ld_words >= ceil(n_loci / 64); bits at
+ *               loci >= n_loci and words >= ceil(n_loci / 64) are written 0.
+ *  norms_dev    optional uint32 [n]: popcount of each packed row.
+ * Errors: EINVAL on NULL buffers, n < 0, n_loci outside [1, FASTID_MAX_LOCI],
+ * ld_alleles < n_loci or ld_words too small.
+ */
+fastid_status fastid_pack(fastid_ctx *ctx, const uint8_t *alleles_dev, int64_t n, int32_t n_loci,
+                          int64_t ld_alleles, uint64_t *packed_dev, int64_t ld_words,
+                          uint32_t *norms_dev, fastid_stream stream);
+
+/*
+ * Build mixtures: out[m] = OR of src rows offsets[m] .. offsets[m+1]-1 (a
+ * mixture carries every minor allele of its contributors, Sec. I and II-A).
+ * An individual is a group of one row.
+ *  src_dev      uint64 [*][ld_src] packed rows.
+ *  offsets_dev  int32 [n_mix + 1], non-decreasing, offsets[0] >= 0; rows
+ *               offsets[m] .. offsets[m+1]-1 must exist in src.  An empty group
+ *               gives an all-zero profile.
+ *  out_dev      uint64 [n_mix][ld_out]; words >= n_words are written 0.
+ *  norms_dev    optional uint32 [n_mix] popcounts of the mixtures.
+ * Offsets are read on the device and are not validated on the host.
+ */
+fastid_status fastid_mix(fastid_ctx *ctx, const uint64_t *src_dev, int64_t ld_src, int32_t n_words,
+                         const int32_t *offsets_dev, int64_t n_mix, uint64_t *out_dev,
+                         int64_t ld_out, uint32_t *norms_dev, fastid_stream stream);
+
+/* ------------------------------------------------------ reference database */
+
+/*
+ * Copy n_refs packed reference profiles into a device-resident database
+ * owned by the library (the known profiles of Sec. II-B, matrix A), compute
+ * their popcounts, and with FASTID_REFS_TENSOR also build the FP8 operand copy
+ * (1 byte per locus) used by the tensor form.  The caller's buffer may be
+ * freed once the stream has passed this call.
+ *  packed_dev  uint64 [n_refs][ld_words], bits at loci >= n_loci zero.
+ *  n_refs      1 .. 2^31 - 1;  n_loci 1 .. FASTID_MAX_LOCI.
+ * Errors: EINVAL, ENOMEM (database does not fit), ECUDA.
+ */
+fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int64_t n_refs,
+                               int32_t n_loci, int64_t ld_words, uint32_t flags,
+                               fastid_refdb **out, fastid_stream stream);
+
+/* Synchronise the device and free a database.  NULL is accepted. */
+fastid_status fastid_free_refs(fastid_ctx *ctx, fastid_refdb *db);
+
+/* Shape and footprint of a database; any output pointer may be NULL. */
+fastid_status fastid_refs_info(const fastid_refdb *db, int64_t *n_refs, int32_t *n_loci,
+                               uint32_t *flags, int64_t *device_bytes);
+
+/* ---------------------------------------------------------- comparisons */
+/*
+ * Shared arguments:
+ *  queries_dev  uint64 [n_q][ld_q] packed unknown profiles (matrix B of
+ *               Sec. II-B, one row per unknown), same n_loci as the database.
+ *  modes_dev    uint8 [n_q]: FASTID_MODE_MISMATCH or FASTID_MODE_UNEXPLAINED
+ *               per query (any other value is treated as UNEXPLAINED).
+ *  n_q          0 .. 2^31 - 1 (0 is a no-op).
+ */
+
+/*
+ * Full score matrix (Algorithm 2's P_QR): out[q * ld_out + r] for r < n_refs.
+ *  out_bytes  2 (uint16, needs n_loci <= 65535) or 4 (uint32);  ld_out >= n_refs.
+ * Intended for small problems: it writes n_q * n_refs scores.
+ */
+fastid_status fastid_scores(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev,
+                            int64_t ld_q, int64_t n_q, const uint8_t *modes_dev, void *out_dev,
+                            int32_t out_bytes, int64_t ld_out, fastid_stream stream);
+
+/*
+ * Per-query top-k: the k smallest (score, reference index) pairs with
+ * score <= threshold, ascending by score then by index (ties are broken by
+ * the lower reference index, so the result does not depend on scheduling).
+ * Unused slots get (0xFFFFFFFF, -1).  threshold 0xFFFFFFFF means none.
+ *  k                1 .. FASTID_MAX_K.
+ *  out_scores_dev   uint32 [n_q][k];  out_idx_dev  int64 [n_q][k].
+ * The score matrix is never written to memory.
+ */
+fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev,
+                          int64_t ld_q, int64_t n_q, const uint8_t *modes_dev, int32_t k,
+                          uint32_t threshold, uint32_t *out_scores_dev, int64_t *out_idx_dev,
+                          fastid_stream stream);
+
+/*
+ * Hit list: every pair with score <= threshold, sorted by (q, r).
+ *  hit_q_dev, hit_r_dev  int64 [capacity];  hit_score_dev  uint32 [capacity].
+ *  hit_count_dev         int64 [1]: receives the true number of hits.
+ * If the count exceeds capacity, the buffers hold `capacity` valid hits (not a
+ * defined subset, sorted by (q, r)) and the next fastid_sync_status returns
+ * FASTID_EOVERFLOW.  capacity may be 0 (count only).
+ */
+fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev,
+                             int64_t ld_q, int64_t n_q, const uint8_t *modes_dev,
+                             uint32_t threshold, int64_t capacity, int64_t *hit_q_dev,
+                             int64_t *hit_r_dev, uint32_t *hit_score_dev, int64_t *hit_count_dev,
+                             fastid_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTID_H */

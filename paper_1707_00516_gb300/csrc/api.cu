@@ -1,0 +1,515 @@
+// C ABI of the library (declared in include/fastid.h): argument checks,
+// context and database ownership, scratch memory, and launch sequencing.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fastid {
+int64_t hits_sort_elems(int64_t capacity);
+}
+
+using namespace fastid;
+
+struct fastid_ctx {
+    int device = 0;
+    int form = FASTID_FORM_AUTO;
+    int sms = 0;
+    cudaMemPool_t pool = nullptr;
+    uint32_t *dev_status = nullptr;  // [4]
+    int grid_topk = 0, grid_hits = 0, grid_scores = 0;
+    std::string last_error;
+    // profiling (fastid_profile)
+    bool profile = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t events_used = 0;
+    int64_t launches = 0;
+};
+
+struct fastid_refdb {
+    int64_t n_refs = 0;
+    int64_t n_pad = 0;
+    int32_t n_loci = 0;
+    int32_t n_words64 = 0;
+    int64_t ld64 = 0;
+    uint32_t flags = 0;
+    uint64_t *packed = nullptr;  // [n_pad][ld64]
+    uint32_t *norms = nullptr;   // [n_pad]
+    int64_t bytes = 0;
+    int device = 0;
+};
+
+namespace {
+
+fastid_status fail(fastid_ctx *ctx, fastid_status st, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return st;
+}
+
+fastid_status cuda_fail(fastid_ctx *ctx, cudaError_t e, const char *what) {
+    cudaGetLastError();  // clear a sticky launch error of this thread
+    return fail(ctx, e == cudaErrorMemoryAllocation ? FASTID_ENOMEM : FASTID_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define FASTID_CUDA(ctx, call)                              \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Stream-ordered scratch from the context's pool.
+struct Scratch {
+    fastid_ctx *ctx;
+    cudaStream_t s;
+    void *p = nullptr;
+    Scratch(fastid_ctx *c, cudaStream_t st) : ctx(c), s(st) {}
+    cudaError_t alloc(size_t bytes) { return cudaMallocFromPoolAsync(&p, bytes < 256 ? 256 : bytes, ctx->pool, s); }
+    ~Scratch() {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+// Carves aligned sub-buffers out of one allocation.
+struct Carver {
+    size_t off = 0;
+    template <class T>
+    size_t take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        size_t at = off;
+        off += count * sizeof(T);
+        return at;
+    }
+};
+
+template <class T>
+T *at(void *base, size_t off) {
+    return reinterpret_cast<T *>(static_cast<uint8_t *>(base) + off);
+}
+
+fastid_status check_query_args(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q, int64_t ld_q,
+                               int64_t n_q, const uint8_t *modes) {
+    if (!ctx) return FASTID_EINVAL;
+    if (!db) return fail(ctx, FASTID_EINVAL, "database is NULL");
+    if (n_q < 0 || n_q > 0x7fffffffll) return fail(ctx, FASTID_EINVAL, "n_q out of range: %lld", (long long)n_q);
+    if (n_q > 0 && (!q || !modes)) return fail(ctx, FASTID_EINVAL, "queries or modes is NULL");
+    if (ld_q < db->n_words64) return fail(ctx, FASTID_EINVAL, "ld_q %lld < %d words", (long long)ld_q, db->n_words64);
+    if (db->device != ctx->device) return fail(ctx, FASTID_EINVAL, "database belongs to another device");
+    return FASTID_OK;
+}
+
+// Events around one main compare kernel (only while profiling).
+struct MainTimer {
+    fastid_ctx *ctx;
+    cudaStream_t s;
+    cudaEvent_t e1 = nullptr;
+    MainTimer(fastid_ctx *c, cudaStream_t st) : ctx(c), s(st) {
+        if (!ctx->profile) return;
+        if (ctx->events_used == ctx->events.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (cudaEventCreate(&b) != cudaSuccess) {
+                cudaEventDestroy(a);
+                return;
+            }
+            ctx->events.emplace_back(a, b);
+        }
+        auto &pr = ctx->events[ctx->events_used++];
+        cudaEventRecord(pr.first, s);
+        e1 = pr.second;
+    }
+    void done() {
+        if (e1) cudaEventRecord(e1, s);
+        e1 = nullptr;
+    }
+};
+
+void count_launches(fastid_ctx *ctx, int64_t n) { ctx->launches += n; }
+
+int64_t hits_finish_launches(int64_t capacity) {
+    if (capacity == 0) return 1;
+    int64_t P = hits_sort_elems(capacity), n = 4;  // prep, keys, first smem sort, unpack
+    for (int64_t size = 2 * 2048; size <= P; size <<= 1) {
+        for (int64_t j = size >> 1; j >= 2048; j >>= 1) ++n;
+        ++n;
+    }
+    return n;
+}
+
+// Pads the queries into the plain layout and computes per-query coefficients.
+struct PreparedQueries {
+    uint32_t *q32;
+    QueryCoef *coef;
+    int64_t n_q_pad;
+};
+
+}  // namespace
+
+extern "C" {
+
+int32_t fastid_version(void) { return 100; }
+
+const char *fastid_status_string(fastid_status s) {
+    switch (s) {
+        case FASTID_OK: return "FASTID_OK";
+        case FASTID_EINVAL: return "FASTID_EINVAL";
+        case FASTID_ENOMEM: return "FASTID_ENOMEM";
+        case FASTID_ECUDA: return "FASTID_ECUDA";
+        case FASTID_EOVERFLOW: return "FASTID_EOVERFLOW";
+        case FASTID_ETIMEOUT: return "FASTID_ETIMEOUT";
+        case FASTID_EUNSUPPORTED: return "FASTID_EUNSUPPORTED";
+        case FASTID_EDEVICE: return "FASTID_EDEVICE";
+    }
+    return "FASTID_UNKNOWN";
+}
+
+fastid_status fastid_create(fastid_ctx **out, int32_t device) {
+    if (!out) return FASTID_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return FASTID_ECUDA;
+    }
+    if (device < 0 || device >= n) return FASTID_EINVAL;
+    fastid_ctx *ctx = new (std::nothrow) fastid_ctx();
+    if (!ctx) return FASTID_ENOMEM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        e = cudaMemPoolCreate(&ctx->pool, &props);
+    }
+    if (e == cudaSuccess) {
+        uint64_t keep = ~0ull;  // keep freed scratch cached in the pool
+        e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dev_status, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->dev_status, 0, 4 * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->dev_status) cudaFree(ctx->dev_status);
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+        delete ctx;
+        return e == cudaErrorMemoryAllocation ? FASTID_ENOMEM : FASTID_ECUDA;
+    }
+    ctx->grid_topk = plain_grid_target(EPI_TOPK, device);
+    ctx->grid_hits = plain_grid_target(EPI_HITS, device);
+    ctx->grid_scores = plain_grid_target(EPI_SCORES32, device);
+    *out = ctx;
+    return FASTID_OK;
+}
+
+fastid_status fastid_destroy(fastid_ctx *ctx) {
+    if (!ctx) return FASTID_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->dev_status) cudaFree(ctx->dev_status);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    for (auto &pr : ctx->events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    delete ctx;
+    return FASTID_OK;
+}
+
+fastid_status fastid_profile(fastid_ctx *ctx, int32_t enable) {
+    if (!ctx) return FASTID_EINVAL;
+    ctx->profile = enable != 0;
+    return FASTID_OK;
+}
+
+fastid_status fastid_profile_read(fastid_ctx *ctx, double *main_ms, int64_t *main_launches, int64_t *all_launches,
+                                  int32_t reset) {
+    if (!ctx) return FASTID_EINVAL;
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    double ms = 0.0;
+    for (size_t i = 0; i < ctx->events_used; ++i) {
+        FASTID_CUDA(ctx, cudaEventSynchronize(ctx->events[i].second));
+        float t = 0.f;
+        FASTID_CUDA(ctx, cudaEventElapsedTime(&t, ctx->events[i].first, ctx->events[i].second));
+        ms += t;
+    }
+    if (main_ms) *main_ms = ms;
+    if (main_launches) *main_launches = (int64_t)ctx->events_used;
+    if (all_launches) *all_launches = ctx->launches;
+    if (reset) {
+        ctx->events_used = 0;
+        ctx->launches = 0;
+    }
+    return FASTID_OK;
+}
+
+const char *fastid_last_error(const fastid_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+fastid_status fastid_set_form(fastid_ctx *ctx, int32_t form) {
+    if (!ctx) return FASTID_EINVAL;
+    if (form != FASTID_FORM_AUTO && form != FASTID_FORM_PLAIN && form != FASTID_FORM_TENSOR)
+        return fail(ctx, FASTID_EINVAL, "unknown form %d", form);
+    ctx->form = form;
+    return FASTID_OK;
+}
+
+fastid_status fastid_sync_status(fastid_ctx *ctx, fastid_stream stream) {
+    if (!ctx) return FASTID_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    uint32_t host[4];
+    FASTID_CUDA(ctx, cudaMemcpyAsync(host, ctx->dev_status, sizeof host, cudaMemcpyDeviceToHost, s));
+    FASTID_CUDA(ctx, cudaMemsetAsync(ctx->dev_status, 0, sizeof host, s));
+    FASTID_CUDA(ctx, cudaStreamSynchronize(s));
+    if (host[0] & ST_DEVICE) return fail(ctx, FASTID_EDEVICE, "device-side check failed (detail %u)", host[1]);
+    if (host[0] & ST_TIMEOUT) return fail(ctx, FASTID_ETIMEOUT, "bounded device wait ran out (site %u)", host[1]);
+    if (host[0] & ST_OVERFLOW) return fail(ctx, FASTID_EOVERFLOW, "hit list overflow");
+    return FASTID_OK;
+}
+
+fastid_status fastid_pack(fastid_ctx *ctx, const uint8_t *alleles_dev, int64_t n, int32_t n_loci,
+                          int64_t ld_alleles, uint64_t *packed_dev, int64_t ld_words, uint32_t *norms_dev,
+                          fastid_stream stream) {
+    if (!ctx) return FASTID_EINVAL;
+    if (n < 0) return fail(ctx, FASTID_EINVAL, "n < 0");
+    if (n_loci < 1 || n_loci > FASTID_MAX_LOCI) return fail(ctx, FASTID_EINVAL, "n_loci out of range: %d", n_loci);
+    if (ld_alleles < n_loci) return fail(ctx, FASTID_EINVAL, "ld_alleles < n_loci");
+    if (ld_words < (n_loci + 63) / 64) return fail(ctx, FASTID_EINVAL, "ld_words too small");
+    if (n > 0 && (!alleles_dev || !packed_dev)) return fail(ctx, FASTID_EINVAL, "NULL buffer");
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    FASTID_CUDA(ctx, launch_pack(alleles_dev, n, n_loci, ld_alleles, packed_dev, ld_words, norms_dev,
+                                 (cudaStream_t)stream));
+    count_launches(ctx, n > 0);
+    return FASTID_OK;
+}
+
+fastid_status fastid_mix(fastid_ctx *ctx, const uint64_t *src_dev, int64_t ld_src, int32_t n_words,
+                         const int32_t *offsets_dev, int64_t n_mix, uint64_t *out_dev, int64_t ld_out,
+                         uint32_t *norms_dev, fastid_stream stream) {
+    if (!ctx) return FASTID_EINVAL;
+    if (n_mix < 0) return fail(ctx, FASTID_EINVAL, "n_mix < 0");
+    if (n_words < 1 || ld_src < n_words || ld_out < n_words)
+        return fail(ctx, FASTID_EINVAL, "bad word counts (n_words %d, ld_src %lld, ld_out %lld)", n_words,
+                    (long long)ld_src, (long long)ld_out);
+    if (n_mix > 0 && (!src_dev || !offsets_dev || !out_dev)) return fail(ctx, FASTID_EINVAL, "NULL buffer");
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    FASTID_CUDA(ctx, launch_mix(src_dev, ld_src, n_words, offsets_dev, n_mix, out_dev, ld_out, norms_dev,
+                                (cudaStream_t)stream));
+    count_launches(ctx, n_mix > 0);
+    return FASTID_OK;
+}
+
+fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int64_t n_refs, int32_t n_loci,
+                               int64_t ld_words, uint32_t flags, fastid_refdb **out, fastid_stream stream) {
+    if (!ctx) return FASTID_EINVAL;
+    if (!out) return fail(ctx, FASTID_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_refs < 1 || n_refs > 0x7fffffffll) return fail(ctx, FASTID_EINVAL, "n_refs out of range");
+    if (n_loci < 1 || n_loci > FASTID_MAX_LOCI) return fail(ctx, FASTID_EINVAL, "n_loci out of range");
+    if (ld_words < (n_loci + 63) / 64) return fail(ctx, FASTID_EINVAL, "ld_words too small");
+    if (!packed_dev) return fail(ctx, FASTID_EINVAL, "packed is NULL");
+    if (flags & ~(uint32_t)FASTID_REFS_TENSOR) return fail(ctx, FASTID_EINVAL, "unknown flags");
+    if (flags & FASTID_REFS_TENSOR) return fail(ctx, FASTID_EUNSUPPORTED, "tensor operand copy not built in");
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    fastid_refdb *db = new (std::nothrow) fastid_refdb();
+    if (!db) return fail(ctx, FASTID_ENOMEM, "host allocation");
+    db->device = ctx->device;
+    db->n_refs = n_refs;
+    db->n_loci = n_loci;
+    db->n_words64 = (n_loci + 63) / 64;
+    db->ld64 = round_up(db->n_words64, 8);
+    db->n_pad = round_up(n_refs, ROW_ALIGN);
+    db->flags = flags;
+    size_t pbytes = (size_t)db->n_pad * db->ld64 * 8, nbytes = (size_t)db->n_pad * 4;
+    cudaError_t e = cudaMalloc(&db->packed, pbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&db->norms, nbytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (db->packed) cudaFree(db->packed);
+        delete db;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? FASTID_ENOMEM : FASTID_ECUDA,
+                    "database allocation (%zu bytes): %s", pbytes + nbytes, cudaGetErrorString(e));
+    }
+    db->bytes = (int64_t)(pbytes + nbytes);
+    e = launch_copy_rows(packed_dev, n_refs, ld_words, db->n_words64, db->packed, db->n_pad, db->ld64, db->norms,
+                         (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaFree(db->packed);
+        cudaFree(db->norms);
+        delete db;
+        return cuda_fail(ctx, e, "copy rows");
+    }
+    count_launches(ctx, 1);
+    *out = db;
+    return FASTID_OK;
+}
+
+fastid_status fastid_free_refs(fastid_ctx *ctx, fastid_refdb *db) {
+    if (!db) return FASTID_OK;
+    cudaSetDevice(db->device);
+    cudaDeviceSynchronize();
+    cudaFree(db->packed);
+    cudaFree(db->norms);
+    delete db;
+    (void)ctx;
+    return FASTID_OK;
+}
+
+fastid_status fastid_refs_info(const fastid_refdb *db, int64_t *n_refs, int32_t *n_loci, uint32_t *flags,
+                               int64_t *device_bytes) {
+    if (!db) return FASTID_EINVAL;
+    if (n_refs) *n_refs = db->n_refs;
+    if (n_loci) *n_loci = db->n_loci;
+    if (flags) *flags = db->flags;
+    if (device_bytes) *device_bytes = db->bytes;
+    return FASTID_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Shared front half of the comparison calls: scratch for the padded queries
+// and coefficients (+ `extra` bytes), query preparation.
+fastid_status prepare(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q, int64_t ld_q, int64_t n_q,
+                      const uint8_t *modes, cudaStream_t s, Scratch &scr, size_t extra, size_t *extra_off,
+                      PreparedQueries *pq) {
+    const int64_t ld32 = db->ld64 * 2;
+    pq->n_q_pad = round_up(n_q, PL_TQ);
+    Carver cv;
+    size_t o_q = cv.take<uint32_t>((size_t)pq->n_q_pad * ld32);
+    size_t o_c = cv.take<QueryCoef>((size_t)pq->n_q_pad);
+    *extra_off = cv.take<uint8_t>(extra);
+    FASTID_CUDA(ctx, scr.alloc(cv.off));
+    pq->q32 = at<uint32_t>(scr.p, o_q);
+    pq->coef = at<QueryCoef>(scr.p, o_c);
+    FASTID_CUDA(ctx, launch_query_prep(q, ld_q, n_q, db->n_words64, modes, pq->q32, pq->n_q_pad, ld32, pq->coef, s));
+    count_launches(ctx, 1);
+    return FASTID_OK;
+}
+
+fastid_status check_form(fastid_ctx *ctx, const fastid_refdb *db) {
+    if (ctx->form == FASTID_FORM_TENSOR)
+        return fail(ctx, FASTID_EUNSUPPORTED, "tensor form requested but not available for this database");
+    (void)db;
+    return FASTID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fastid_status fastid_scores(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev, int64_t ld_q,
+                            int64_t n_q, const uint8_t *modes_dev, void *out_dev, int32_t out_bytes,
+                            int64_t ld_out, fastid_stream stream) {
+    fastid_status st = check_query_args(ctx, db, queries_dev, ld_q, n_q, modes_dev);
+    if (st) return st;
+    if (out_bytes != 2 && out_bytes != 4) return fail(ctx, FASTID_EINVAL, "out_bytes must be 2 or 4");
+    if (out_bytes == 2 && db->n_loci > 65535) return fail(ctx, FASTID_EINVAL, "uint16 scores need n_loci <= 65535");
+    if (ld_out < db->n_refs) return fail(ctx, FASTID_EINVAL, "ld_out < n_refs");
+    if (n_q > 0 && !out_dev) return fail(ctx, FASTID_EINVAL, "out is NULL");
+    if ((st = check_form(ctx, db))) return st;
+    if (n_q == 0) return FASTID_OK;
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch scr(ctx, s);
+    PreparedQueries pq;
+    size_t xo;
+    if ((st = prepare(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, 0, &xo, &pq))) return st;
+    Partition part = make_partition((int32_t)(pq.n_q_pad / PL_TQ), db->n_pad / PL_TR, ctx->grid_scores);
+    MainTimer tm(ctx, s);
+    FASTID_CUDA(ctx, launch_plain(out_bytes == 2 ? EPI_SCORES16 : EPI_SCORES32, (const uint32_t *)db->packed,
+                                  db->norms, db->n_refs, db->ld64 * 2, db->n_words64 * 2, pq.q32, pq.coef, n_q,
+                                  0xFFFFFFFFu, 1, out_dev, ld_out, 0, nullptr, nullptr, nullptr, nullptr,
+                                  nullptr, part, ctx->dev_status, s));
+    tm.done();
+    count_launches(ctx, 1);
+    return FASTID_OK;
+}
+
+fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev, int64_t ld_q,
+                          int64_t n_q, const uint8_t *modes_dev, int32_t k, uint32_t threshold,
+                          uint32_t *out_scores_dev, int64_t *out_idx_dev, fastid_stream stream) {
+    fastid_status st = check_query_args(ctx, db, queries_dev, ld_q, n_q, modes_dev);
+    if (st) return st;
+    if (k < 1 || k > FASTID_MAX_K) return fail(ctx, FASTID_EINVAL, "k out of range: %d", k);
+    if (n_q > 0 && (!out_scores_dev || !out_idx_dev)) return fail(ctx, FASTID_EINVAL, "output is NULL");
+    if ((st = check_form(ctx, db))) return st;
+    if (n_q == 0) return FASTID_OK;
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch scr(ctx, s);
+    const int64_t n_q_pad = round_up(n_q, PL_TQ);
+    Partition part = make_partition((int32_t)(n_q_pad / PL_TQ), db->n_pad / PL_TR, ctx->grid_topk);
+    const size_t partial_elems = (size_t)part.grid * part.max_seg * PL_TQ * k;
+    PreparedQueries pq;
+    size_t xo;
+    if ((st = prepare(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, partial_elems * 8, &xo, &pq))) return st;
+    uint64_t *partial = at<uint64_t>(scr.p, xo);
+    MainTimer tm(ctx, s);
+    FASTID_CUDA(ctx, launch_plain(EPI_TOPK, (const uint32_t *)db->packed, db->norms, db->n_refs, db->ld64 * 2,
+                                  db->n_words64 * 2, pq.q32, pq.coef, n_q, threshold, k, nullptr, 0, 0, nullptr,
+                                  nullptr, nullptr, nullptr, partial, part, ctx->dev_status, s));
+    tm.done();
+    FASTID_CUDA(ctx, launch_topk_merge(partial, part, n_q, k, out_scores_dev, out_idx_dev, s));
+    count_launches(ctx, 2);
+    return FASTID_OK;
+}
+
+fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev, int64_t ld_q,
+                             int64_t n_q, const uint8_t *modes_dev, uint32_t threshold, int64_t capacity,
+                             int64_t *hit_q_dev, int64_t *hit_r_dev, uint32_t *hit_score_dev,
+                             int64_t *hit_count_dev, fastid_stream stream) {
+    fastid_status st = check_query_args(ctx, db, queries_dev, ld_q, n_q, modes_dev);
+    if (st) return st;
+    if (capacity < 0) return fail(ctx, FASTID_EINVAL, "capacity < 0");
+    if (!hit_count_dev) return fail(ctx, FASTID_EINVAL, "hit_count is NULL");
+    if (capacity > 0 && (!hit_q_dev || !hit_r_dev || !hit_score_dev))
+        return fail(ctx, FASTID_EINVAL, "hit buffers are NULL");
+    if ((st = check_form(ctx, db))) return st;
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_q == 0) {
+        FASTID_CUDA(ctx, cudaMemsetAsync(hit_count_dev, 0, sizeof(int64_t), s));
+        return FASTID_OK;
+    }
+    Scratch scr(ctx, s);
+    const int64_t P = hits_sort_elems(capacity);
+    const size_t extra = 256 + (size_t)(2 + P + P / 2 + 1) * 8;
+    PreparedQueries pq;
+    size_t xo;
+    if ((st = prepare(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, extra, &xo, &pq))) return st;
+    unsigned long long *count = at<unsigned long long>(scr.p, xo);
+    uint64_t *sort_tmp = at<uint64_t>(scr.p, xo + 256);
+    FASTID_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
+    Partition part = make_partition((int32_t)(pq.n_q_pad / PL_TQ), db->n_pad / PL_TR, ctx->grid_hits);
+    MainTimer tm(ctx, s);
+    FASTID_CUDA(ctx, launch_plain(EPI_HITS, (const uint32_t *)db->packed, db->norms, db->n_refs, db->ld64 * 2,
+                                  db->n_words64 * 2, pq.q32, pq.coef, n_q, threshold, 1, nullptr, 0, capacity,
+                                  hit_q_dev, hit_r_dev, hit_score_dev, count, nullptr, part, ctx->dev_status, s));
+    tm.done();
+    FASTID_CUDA(ctx, launch_hits_finish(count, capacity, hit_q_dev, hit_r_dev, hit_score_dev, hit_count_dev,
+                                        sort_tmp, ctx->dev_status, s));
+    count_launches(ctx, 1 + hits_finish_launches(capacity));
+    return FASTID_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fastid.h"
+
+namespace fastid {
+
+// Device status word bits (ctx->dev_status[0]); detail in dev_status[1..].
+enum : uint32_t {
+    ST_OVERFLOW = 1u,  // hit list longer than its capacity
+    ST_TIMEOUT = 2u,   // a bounded wait ran out
+    ST_DEVICE = 4u,    // a device-side consistency check failed
+};
+
+// Plain-form tile: 128 references x 128 queries per CTA, K staged in chunks of
+// KC 32-bit words.
+constexpr int PL_TR = 128;       // references per tile
+constexpr int PL_TQ = 128;       // queries per tile
+constexpr int PL_KC = 16;        // u32 words per K stage
+constexpr int PL_THREADS = 256;  // 16 x 16 threads, 8 x 8 outputs each
+constexpr int ROW_ALIGN = 128;   // database rows are padded to this multiple
+constexpr int WORD_ALIGN32 = 32; // database row stride (u32 words) is a multiple of this
+
+// Epilogue kinds of the comparison kernels.
+enum Epi : int { EPI_SCORES16 = 0, EPI_SCORES32 = 1, EPI_HITS = 2, EPI_TOPK = 3 };
+
+// Per-query coefficients for the plain form: score = |R| + b - a * G, where
+// G = popc(R AND Q):  mode 0 (XOR): a = 2, b = |Q|;  mode 1 (Eq. 1): a = 1, b = 0.
+struct QueryCoef {
+    uint32_t a;
+    uint32_t b;
+};
+
+// Work partition of a persistent launch over units = query tiles x reference
+// tiles in query-tile-major order; CTA c takes units [c*U/G, (c+1)*U/G).
+struct Partition {
+    int64_t n_units;   // QT * RT
+    int32_t n_qt;      // query tiles
+    int64_t n_rt;      // reference tiles
+    int32_t grid;      // G
+    int32_t max_seg;   // max query-tile segments per CTA
+};
+
+__host__ __device__ inline int64_t part_begin(const Partition &p, int64_t c) {
+    return (c * p.n_units) / p.grid;
+}
+
+__host__ inline Partition make_partition(int32_t n_qt, int64_t n_rt, int32_t grid_target) {
+    Partition p;
+    p.n_qt = n_qt;
+    p.n_rt = n_rt;
+    p.n_units = (int64_t)n_qt * n_rt;
+    int64_t g = grid_target < 1 ? 1 : grid_target;
+    if (g > p.n_units) g = p.n_units;
+    if (g < 1) g = 1;
+    p.grid = (int32_t)g;
+    int64_t span = (p.n_units + g - 1) / g;
+    p.max_seg = (int32_t)((span + n_rt - 1) / n_rt + 1);
+    return p;
+}
+
+// Top-k keys: (score << 32) | ref, so that ordering keys orders by score then
+// by reference index.  An empty slot holds KEY_EMPTY.
+constexpr uint64_t KEY_EMPTY = ~0ull;
+
+__host__ __device__ inline uint64_t make_key(uint32_t score, uint32_t ref) {
+    return ((uint64_t)score << 32) | ref;
+}
+
+// Initial cutoff: keys strictly below it may enter a list that is not full.
+__host__ __device__ inline uint64_t initial_cut(uint32_t threshold) {
+    return threshold == 0xFFFFFFFFu ? KEY_EMPTY : ((uint64_t)(threshold + 1u) << 32);
+}
+
+}  // namespace fastid
+
+// Launchers implemented in the .cu files (all enqueue on `s`, no sync).
+namespace fastid {
+cudaError_t launch_pack(const uint8_t *alleles, int64_t n, int32_t n_loci, int64_t ld_alleles,
+                        uint64_t *packed, int64_t ld_words, uint32_t *norms, cudaStream_t s);
+cudaError_t launch_mix(const uint64_t *src, int64_t ld_src, int32_t n_words, const int32_t *offsets,
+                       int64_t n_mix, uint64_t *out, int64_t ld_out, uint32_t *norms,
+                       cudaStream_t s);
+cudaError_t launch_copy_rows(const uint64_t *src, int64_t n, int64_t ld_src, int32_t n_words,
+                             uint64_t *dst, int64_t n_pad, int64_t ld_dst, uint32_t *norms,
+                             cudaStream_t s);
+cudaError_t launch_query_prep(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words,
+                              const uint8_t *modes, uint32_t *q32, int64_t n_q_pad, int64_t ld32,
+                              QueryCoef *coef, cudaStream_t s);
+cudaError_t launch_plain(int epi, const uint32_t *refs32, const uint32_t *ref_norms, int64_t n_refs,
+                         int64_t ld32, int32_t k_words32, const uint32_t *q32,
+                         const QueryCoef *coef, int64_t n_q, uint32_t threshold, int32_t k,
+                         void *out, int64_t ld_out, int64_t capacity, int64_t *hit_q,
+                         int64_t *hit_r, uint32_t *hit_score, unsigned long long *hit_count,
+                         uint64_t *partial, const Partition &part, uint32_t *status,
+                         cudaStream_t s);
+int plain_grid_target(int epi, int device);
+cudaError_t launch_topk_merge(const uint64_t *partial, const Partition &part, int64_t n_q,
+                              int32_t k, uint32_t *out_scores, int64_t *out_idx, cudaStream_t s);
+cudaError_t launch_hits_finish(unsigned long long *count, int64_t capacity, int64_t *hit_q,
+                               int64_t *hit_r, uint32_t *hit_score, int64_t *count_out,
+                               uint64_t *sort_tmp, uint32_t *status, cudaStream_t s);
+}  // namespace fastid

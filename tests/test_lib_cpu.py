@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports what include/fastid.h declares;
+host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1707_00516_gb300 import binding as B
+from paper_1707_00516_gb300.build import INCLUDE, LIB, build
+
+HEADER = os.path.join(INCLUDE, "fastid.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return B.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fastid_\w+)\s*\(", src)))
+
+
+def exported_functions():
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True, check=True).stdout
+    return sorted({ln.split()[-1] for ln in out.splitlines() if " T fastid_" in ln})
+
+
+def test_header_exports_match(lib):
+    decl = declared_functions()
+    assert decl, "no declarations parsed"
+    assert decl == exported_functions()
+    assert sorted(B.EXPORTS) == decl
+
+
+def test_version_and_status_strings(lib):
+    assert lib.fastid_version() == 100
+    for code in range(8):
+        assert lib.fastid_status_string(code).decode().startswith("FASTID_")
+
+
+def test_create_without_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = lib.fastid_create(ctypes.byref(h), 0)
+    assert st in (B.ECUDA, B.EINVAL)
+    assert not h.value
+    assert lib.fastid_create(None, 0) == B.EINVAL
+
+
+def test_null_context_is_einval(lib):
+    P = None
+    assert lib.fastid_destroy(P) == B.OK
+    assert lib.fastid_set_form(P, 0) == B.EINVAL
+    assert lib.fastid_sync_status(P, P) == B.EINVAL
+    assert lib.fastid_profile(P, 1) == B.EINVAL
+    assert lib.fastid_profile_read(P, None, None, None, 0) == B.EINVAL
+    assert lib.fastid_pack(P, P, 1, 64, 64, P, 1, P, P) == B.EINVAL
+    assert lib.fastid_mix(P, P, 1, 1, P, 1, P, 1, P, P) == B.EINVAL
+    assert lib.fastid_load_refs(P, P, 1, 64, 1, 0, None, P) == B.EINVAL
+    assert lib.fastid_free_refs(P, P) == B.OK
+    assert lib.fastid_refs_info(P, None, None, None, None) == B.EINVAL
+    assert lib.fastid_scores(P, P, P, 1, 1, P, P, 4, 1, P) == B.EINVAL
+    assert lib.fastid_topk(P, P, P, 1, 1, P, 16, 0, P, P, P) == B.EINVAL
+    assert lib.fastid_compare(P, P, P, 1, 1, P, 0, 0, P, P, P, P, P) == B.EINVAL
+    assert lib.fastid_last_error(P) == b""
+
+
+def test_library_missing_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(B, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        B.load_library(str(tmp_path / "nope.so"))
