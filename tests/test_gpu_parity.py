@@ -181,7 +181,7 @@ def test_hits_parity(searcher, T):
     R, Q, modes, _, _ = make_case(3000, 10, 50, 50, 5 + T, low_entropy=True)
     db = load(searcher, R, 10)
     q = pack_dev(searcher, Q, 10)
-    hq, hr, hs, hc = searcher.hits(db, q, torch.from_numpy(modes).cuda(), T, 1 << 16)
+    hq, hr, hs, hc = searcher.hits(db, q, torch.from_numpy(modes).cuda(), T, 1 << 18)
     mis, une = oracle.scores(R, Q)
     oq, orr, osc = oracle.hits(oracle.select(mis, une, modes), T)
     n = int(hc.item())
