@@ -223,6 +223,41 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
                              int64_t *hit_r_dev, uint32_t *hit_score_dev, int64_t *hit_count_dev,
                              fastid_stream stream);
 
+/*
+ * fastid_topk_noalloc -- fastid_topk for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this entry point exists for
+ * deployments, not for the method.
+ *
+ * Some callers may not call cudaMalloc (or any allocator) once they run: a
+ * service that reserves its whole device-memory budget at start-up so that
+ * nothing can fail later under memory pressure, a plug-in inside a host
+ * runtime that owns every device allocation, or a latency-critical loop that
+ * cannot afford an allocator call and its driver locks.  This call does the
+ * same work as fastid_topk with the plain form (same arguments, results, order
+ * and errors) but takes its scratch memory (padded queries, per-query
+ * coefficients and per-segment top-k lists) from one array of
+ * FASTID_NOALLOC_SCRATCH_BYTES that is part of the library's device code.  It
+ * allocates nothing; the caller still provides inputs and outputs.
+ *
+ *  - A request whose scratch would exceed FASTID_NOALLOC_SCRATCH_BYTES
+ *    (roughly: padded queries x loci / 8, plus ~10 MB of lists for k = 32 on
+ *    a 152-SM GPU) returns FASTID_EINVAL with the size it needed in
+ *    fastid_last_error; nothing is enqueued.
+ *  - The first call on a device looks up the array's device address there
+ *    (and may make CUDA load that device code); make that first call before
+ *    any stream capture.  The array stays resident on every device that used
+ *    it until the process exits.
+ *  - Every call uses the same array and it keeps the last call's contents
+ *    (nothing in it needs to start at zero).  Calls whose kernels overlap on
+ *    the GPU -- on different streams or host threads, or with different
+ *    contexts -- race on it: serialise them.
+ */
+#define FASTID_NOALLOC_SCRATCH_BYTES (16u << 20)
+fastid_status fastid_topk_noalloc(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev,
+                                  int64_t ld_q, int64_t n_q, const uint8_t *modes_dev, int32_t k,
+                                  uint32_t threshold, uint32_t *out_scores_dev, int64_t *out_idx_dev,
+                                  fastid_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

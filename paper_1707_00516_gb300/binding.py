@@ -26,6 +26,7 @@ REFS_TENSOR = 1
 MAX_K = 32
 MAX_LOCI = 65536
 NO_THRESHOLD = 0xFFFFFFFF
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
 _lock = threading.Lock()
@@ -63,6 +64,7 @@ _PROTOS = {
     "fastid_scores": (_I32, [_P, _P, _P, _I64, _I64, _P, _P, _I32, _I64, _P]),
     "fastid_topk": (_I32, [_P, _P, _P, _I64, _I64, _P, _I32, _U32, _P, _P, _P]),
     "fastid_compare": (_I32, [_P, _P, _P, _I64, _I64, _P, _U32, _I64, _P, _P, _P, _P, _P]),
+    "fastid_topk_noalloc": (_I32, [_P, _P, _P, _I64, _I64, _P, _I32, _U32, _P, _P, _P]),
 }
 
 # Every symbol the header declares (checked by the CPU tests).
@@ -286,3 +288,18 @@ def fastid_compare(ctx: Context, db: RefDB, queries: torch.Tensor, modes: torch.
     n_q = queries.size(0)
     ctx.check(load_library().fastid_compare(ctx.handle, db.handle, q, _ld(queries), n_q, m, threshold, cap,
                                             hq, hr, hs, hc, _stream_ptr(stream)))
+
+
+def fastid_topk_noalloc(ctx: Context, db: RefDB, queries: torch.Tensor, modes: torch.Tensor, k: int,
+                        threshold: int, out_scores: torch.Tensor, out_idx: torch.Tensor, stream=None) -> None:
+    """fastid_topk without device allocation: scratch comes from a fixed array
+    of NOALLOC_SCRATCH_BYTES inside the library (see include/fastid.h)."""
+    q = _dev(queries, torch.int64, "queries", 2)
+    m = _dev(modes, torch.uint8, "modes", 1)
+    s = _dev(out_scores, torch.int32, "out_scores", 2)
+    i = _dev(out_idx, torch.int64, "out_idx", 2)
+    n_q = queries.size(0)
+    if modes.numel() != n_q or tuple(out_scores.shape) != (n_q, k) or tuple(out_idx.shape) != (n_q, k):
+        raise ValueError("modes / outputs do not match n_q x k")
+    ctx.check(load_library().fastid_topk_noalloc(ctx.handle, db.handle, q, _ld(queries), n_q, m, k, threshold,
+                                                 s, i, _stream_ptr(stream)))

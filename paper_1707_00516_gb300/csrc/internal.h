@@ -1,0 +1,38 @@
+// Library-internal definitions of the opaque C ABI handles, shared by the
+// translation units that implement entry points.
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+struct fastid_ctx {
+    int device = 0;
+    int form = FASTID_FORM_AUTO;
+    int sms = 0;
+    cudaMemPool_t pool = nullptr;
+    uint32_t *dev_status = nullptr;  // [4]
+    int grid_topk = 0, grid_hits = 0, grid_scores = 0;
+    std::string last_error;
+    // profiling (fastid_profile)
+    bool profile = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t events_used = 0;
+    int64_t launches = 0;
+};
+
+struct fastid_refdb {
+    int64_t n_refs = 0;
+    int64_t n_pad = 0;
+    int32_t n_loci = 0;
+    int32_t n_words64 = 0;
+    int64_t ld64 = 0;
+    uint32_t flags = 0;
+    uint64_t *packed = nullptr;  // [n_pad][ld64]
+    uint32_t *norms = nullptr;   // [n_pad]
+    int64_t bytes = 0;
+    int device = 0;
+};
+
