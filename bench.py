@@ -12,7 +12,7 @@ HBM (loaded once, outside the timed region).
 Default workload: 2048 unknowns (1024 individuals, 1024 mixtures of 2-5
 people) x 20,000,000 references, N = 2048 loci, top-32, threshold 512.
 
-    python bench.py [--steps K] [--warmup W] [--form plain|tensor|auto]
+    python bench.py [--steps K] [--warmup W] [--form plain|tensor|both]
     python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
     torchrun --nproc-per-node N bench.py --gpus N   (N independent replicas)
 
@@ -59,6 +59,8 @@ UNIT = "comparisons/s"
 # clock per SM (integer-pipe throughput table for compute capability 10.x),
 # 152 SMs, at the maximum SM clock.
 POPC_PER_CLK_PER_SM = 16
+# Dense e4m3 tensor rate relative to bf16 (nominal 4.5 vs 2.25 PFLOP/s).
+FP8_OVER_BF16 = 2.0
 
 
 def recipe_for(name: str, n_refs: int | None = None, n_q: int | None = None):
@@ -273,9 +275,9 @@ def run_reference(args, w):
 # GPU arm
 # ----------------------------------------------------------------------------
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(form: str) -> str:
     h = hashlib.sha256()
-    for f in ("plain.cu", "common.cuh"):
+    for f in ("plain.cu" if form == "plain" else "tensor.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1707_00516_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -297,6 +299,68 @@ def load_peaks():
             "fallback"
 
 
+def time_form(args, s, db, form_name, step_fn, pairs_per_step, n_loci, world, dev):
+    """Warm up and time `args.steps` steps of one compute form; returns the
+    device-timed result and the roofline of its main compare kernel."""
+    import torch
+    from paper_1707_00516_gb300 import binding as B
+    B.fastid_set_form(s.ctx, B.FORM_PLAIN if form_name == "plain" else B.FORM_TENSOR)
+    for _ in range(args.warmup):
+        step_fn()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    B.fastid_profile(s.ctx, True)
+    B.fastid_profile_read(s.ctx, reset=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world, dev)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world, dev)
+    ms = e0.elapsed_time(e1)
+    prof = B.fastid_profile_read(s.ctx, reset=True)
+    B.fastid_profile(s.ctx, False)
+    clocks = clk.stop()
+    st = B.fastid_sync_status(s.ctx)
+    if st != B.OK:
+        raise RuntimeError(f"device status {st} after the timed region ({form_name})")
+    ms_max = max_over_ranks(ms, world, dev)
+    value = pairs_per_step * args.steps * world / (ms_max / 1e3)
+
+    peaks, peak_src = load_peaks()
+    main_s = prof["main_ms"] / max(1, prof["main_launches"]) / 1e3
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if form_name == "plain":
+        words32 = 2 * ((n_loci + 63) // 64)
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = POPC_PER_CLK_PER_SM * n_sms * sm_max * 1e6 / 1e12
+        achieved = pairs_per_step * words32 / main_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpopc/s",
+                "kernel": "plain_kernel<EPI_TOPK>",
+                "peak_source": f"{POPC_PER_CLK_PER_SM} POPC/clk/SM x {n_sms} SMs x {sm_max:.0f} MHz "
+                               f"(max SM clock, {peak_src})"}
+    else:
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        peak = bf16 * FP8_OVER_BF16
+        achieved = 2.0 * pairs_per_step * n_loci / main_s / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "kernel": "tensor_kernel (tcgen05 kind::f8f6f4, EPI_TOPK)",
+                "peak_source": f"bf16 dense burst {bf16:.1f} TFLOP/s ({peak_src}) x {FP8_OVER_BF16:g} "
+                               f"(nominal e4m3/bf16 dense ratio, 4.5/2.25 PFLOP/s)"}
+    roof["frac"] = achieved / peak
+    roof["kernel_ms"] = main_s * 1e3
+    key = f"{form_name}/{args.config}"
+    tr = NCU_TRAFFIC.get(key)
+    roof["traffic"] = tr[0] if tr and tr[1] == kernel_source_hash(form_name) else None
+    return {"value": value, "ms_per_step": ms_max / args.steps, "roofline": roof, "clocks": clocks,
+            "gpu_launches": int(prof["all_launches"])}
+
+
 def run_gpu(args, w):
     import torch
     world, rank = dist_init("nccl")
@@ -309,11 +373,11 @@ def run_gpu(args, w):
     gen.build_gpu()
     build()
 
-    form = {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "auto": B.FORM_AUTO}[args.form]
-    s = Searcher(local, form)
+    forms = ["plain", "tensor"] if args.form == "both" else [args.form]
+    s = Searcher(local, B.FORM_AUTO)
     seed = gen.config_seed(w["cfg"])
     n_refs, n_loci, k, T = w["n_refs"], w["n_loci"], w["k"], w["threshold"]
-    flags = B.REFS_TENSOR if args.form == "tensor" else 0
+    flags = B.REFS_TENSOR if "tensor" in forms else 0
     db, thr = build_db(s, seed, n_refs, n_loci, flags)
     recipe = recipe_for(args.config)
     src, off, modes = query_inputs(recipe, thr)
@@ -328,36 +392,13 @@ def run_gpu(args, w):
         q = s.build_queries(d_src, d_off, n_loci)
         B.fastid_topk(s.ctx, db, q, d_mod, k, T, sc, ix)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    clk = ClockSampler(local)
-    clk.start()
-    B.fastid_profile(s.ctx, True)
-    B.fastid_profile_read(s.ctx, reset=True)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(world, dev)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world, dev)
-    ms = e0.elapsed_time(e1)
-    prof = B.fastid_profile_read(s.ctx, reset=True)
-    B.fastid_profile(s.ctx, False)
-    clocks = clk.stop()
-    st = B.fastid_sync_status(s.ctx)
-    if st != B.OK:
-        raise RuntimeError(f"device status {st} after the timed region")
-    ms_max = max_over_ranks(ms, world, dev)
     pairs_per_step = n_q * n_refs
-    value = pairs_per_step * args.steps * world / (ms_max / 1e3)
+    res = {f: time_form(args, s, db, f, step, pairs_per_step, n_loci, world, dev) for f in forms}
+    head = max(res, key=lambda f: res[f]["value"])
+    hr = res[head]
 
-    # end to end through the host-buffer API
+    # end to end through the host-buffer API, headline form
+    B.fastid_set_form(s.ctx, B.FORM_PLAIN if head == "plain" else B.FORM_TENSOR)
     for _ in range(max(1, args.warmup // 2)):
         s.search_host(db, src, off, modes, k, T)
     barrier(world, dev)
@@ -367,33 +408,20 @@ def run_gpu(args, w):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_value = pairs_per_step * args.steps * world / e2e_s
 
-    # roofline of the main compare kernel
-    peaks, peak_src = load_peaks()
-    main_ms = prof["main_ms"] / max(1, prof["main_launches"])
-    words32 = 2 * ((n_loci + 63) // 64)
-    popc = pairs_per_step * words32
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_tpopc = POPC_PER_CLK_PER_SM * n_sms * sm_max * 1e6 / 1e12
-    achieved = popc / (main_ms / 1e3) / 1e12
-    key = f"plain/{args.config}"
-    tr = NCU_TRAFFIC.get(key)
-    traffic = tr[0] if tr and tr[1] == kernel_source_hash() else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tpopc, "unit": "Tpopc/s",
-                "frac": achieved / peak_tpopc, "traffic": traffic,
-                "kernel": "plain_kernel<EPI_TOPK>", "kernel_ms": main_ms,
-                "peak_source": f"{POPC_PER_CLK_PER_SM} POPC/clk/SM x {n_sms} SMs x {sm_max:.0f} MHz "
-                               f"(max SM clock, {peak_src})"}
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+    line = {"metric": METRIC, "value": hr["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": hr["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32" if head == "plain" else "e4m3xe4m3->f32",
+            "data": "synthetic",
             "config": {"workload": w["workload"], "n_queries": n_q, "n_refs": n_refs, "n_loci": n_loci, "k": k,
-                       "threshold": T, "form": args.form, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (packed database %.2f GB)" % (n_refs * n_loci / 8 / 1e9)},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": int(prof["all_launches"]),
-            "roofline": roofline, "clocks": clocks}
+                       "threshold": T, "form": head, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (packed database %.2f GB%s)" % (
+                           n_refs * n_loci / 8 / 1e9,
+                           ", e4m3 copy %.1f GB" % (n_refs * n_loci / 1e9) if flags else "")},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": hr["gpu_launches"], "roofline": hr["roofline"], "clocks": hr["clocks"],
+            "forms": {f: {"value": r["value"], "ms_per_step": r["ms_per_step"], "roofline": r["roofline"],
+                          "clocks": r["clocks"]} for f, r in res.items()}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, recipe, thr)
     if rank == 0:
@@ -411,7 +439,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["plain", "tensor", "auto"], default="plain")
+    ap.add_argument("--form", choices=["plain", "tensor", "both"], default="both")
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="c3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

@@ -10,10 +10,6 @@
 
 #include "common.cuh"
 
-namespace fastid {
-int64_t hits_sort_elems(int64_t capacity);
-}
-
 using namespace fastid;
 
 #include "internal.h"
@@ -190,6 +186,7 @@ fastid_status fastid_create(fastid_ctx **out, int32_t device) {
     ctx->grid_topk = plain_grid_target(EPI_TOPK, device);
     ctx->grid_hits = plain_grid_target(EPI_HITS, device);
     ctx->grid_scores = plain_grid_target(EPI_SCORES32, device);
+    ctx->grid_tensor = tensor_grid_target(device);
     *out = ctx;
     return FASTID_OK;
 }
@@ -301,7 +298,6 @@ fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int6
     if (ld_words < (n_loci + 63) / 64) return fail(ctx, FASTID_EINVAL, "ld_words too small");
     if (!packed_dev) return fail(ctx, FASTID_EINVAL, "packed is NULL");
     if (flags & ~(uint32_t)FASTID_REFS_TENSOR) return fail(ctx, FASTID_EINVAL, "unknown flags");
-    if (flags & FASTID_REFS_TENSOR) return fail(ctx, FASTID_EUNSUPPORTED, "tensor operand copy not built in");
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     fastid_refdb *db = new (std::nothrow) fastid_refdb();
     if (!db) return fail(ctx, FASTID_ENOMEM, "host allocation");
@@ -332,6 +328,25 @@ fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int6
         return cuda_fail(ctx, e, "copy rows");
     }
     count_launches(ctx, 1);
+    if (flags & FASTID_REFS_TENSOR) {
+        db->kpad = tensor_kpad(n_loci);
+        const size_t fbytes = (size_t)db->n_pad * db->kpad;
+        e = cudaMalloc(&db->fp8, fbytes);
+        if (e == cudaSuccess) e = launch_refs_e4m3(db->packed, db->ld64, db->n_pad, db->kpad, db->fp8, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = make_operand_map(&db->map_b, db->fp8, db->n_pad, db->kpad, tensor_tile_r());
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamSynchronize((cudaStream_t)stream);
+            if (db->fp8) cudaFree(db->fp8);
+            cudaFree(db->packed);
+            cudaFree(db->norms);
+            delete db;
+            return fail(ctx, e == cudaErrorMemoryAllocation ? FASTID_ENOMEM : FASTID_ECUDA,
+                        "tensor operand copy (%zu bytes): %s", fbytes, cudaGetErrorString(e));
+        }
+        db->bytes += (int64_t)fbytes;
+        count_launches(ctx, 1);
+    }
     *out = db;
     return FASTID_OK;
 }
@@ -342,6 +357,7 @@ fastid_status fastid_free_refs(fastid_ctx *ctx, fastid_refdb *db) {
     cudaDeviceSynchronize();
     cudaFree(db->packed);
     cudaFree(db->norms);
+    if (db->fp8) cudaFree(db->fp8);
     delete db;
     (void)ctx;
     return FASTID_OK;
@@ -380,11 +396,60 @@ fastid_status prepare(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q
     return FASTID_OK;
 }
 
-fastid_status check_form(fastid_ctx *ctx, const fastid_refdb *db) {
-    if (ctx->form == FASTID_FORM_TENSOR)
-        return fail(ctx, FASTID_EUNSUPPORTED, "tensor form requested but not available for this database");
-    (void)db;
+// Chooses the form for a call: *tensor = 1 for the tensor form.
+fastid_status pick_form(fastid_ctx *ctx, const fastid_refdb *db, int *tensor) {
+    *tensor = 0;
+    if (ctx->form == FASTID_FORM_TENSOR) {
+        if (!db->fp8)
+            return fail(ctx, FASTID_EUNSUPPORTED,
+                        "tensor form requested but the database was loaded without FASTID_REFS_TENSOR");
+        *tensor = 1;
+    } else if (ctx->form == FASTID_FORM_AUTO && db->fp8) {
+        *tensor = 1;
+    }
     return FASTID_OK;
+}
+
+// Tensor-form front half: e4m3 query operand + c_q in scratch, its TMA map,
+// and the partition over (128-query tile, 256-reference tile) units.
+struct TensorPrep {
+    CUtensorMap map_a;
+    float *qconst;
+    Partition part;
+};
+
+fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q, int64_t ld_q, int64_t n_q,
+                             const uint8_t *modes, cudaStream_t s, Scratch &scr, size_t (*extra_fn)(const Partition &, void *),
+                             void *extra_arg, size_t *extra_off, TensorPrep *tp) {
+    const int64_t n_q_pad = round_up(n_q, tensor_tile_q());
+    tp->part = make_partition((int32_t)(n_q_pad / tensor_tile_q()), db->n_pad / tensor_tile_r(), ctx->grid_tensor);
+    const size_t extra = extra_fn ? extra_fn(tp->part, extra_arg) : 0;
+    Carver cv;
+    size_t o_a = cv.take<uint8_t>((size_t)n_q_pad * db->kpad);
+    size_t o_c = cv.take<float>((size_t)n_q_pad);
+    *extra_off = cv.take<uint8_t>(extra);
+    FASTID_CUDA(ctx, scr.alloc(cv.off));
+    uint8_t *a = at<uint8_t>(scr.p, o_a);
+    tp->qconst = at<float>(scr.p, o_c);
+    FASTID_CUDA(ctx, launch_queries_e4m3(q, ld_q, n_q, db->n_words64, db->n_loci, modes, n_q_pad, db->kpad, a,
+                                         tp->qconst, s));
+    count_launches(ctx, 1);
+    FASTID_CUDA(ctx, make_operand_map(&tp->map_a, a, n_q_pad, db->kpad, tensor_tile_q()));
+    return FASTID_OK;
+}
+
+uint32_t clamp_threshold(uint32_t t, int32_t n_loci) {
+    if (t == 0xFFFFFFFFu) return t;
+    return t > (uint32_t)n_loci ? (uint32_t)n_loci : t;
+}
+
+size_t topk_extra(const Partition &p, void *karg) {
+    return (size_t)p.grid * p.max_seg * 128 * (size_t)(*static_cast<int32_t *>(karg)) * 8;
+}
+
+size_t hits_extra(const Partition &, void *carg) {
+    const int64_t P = hits_sort_elems(*static_cast<int64_t *>(carg));
+    return 256 + (size_t)(2 + P + P / 2 + 1) * 8;
 }
 
 }  // namespace
@@ -400,13 +465,26 @@ fastid_status fastid_scores(fastid_ctx *ctx, const fastid_refdb *db, const uint6
     if (out_bytes == 2 && db->n_loci > 65535) return fail(ctx, FASTID_EINVAL, "uint16 scores need n_loci <= 65535");
     if (ld_out < db->n_refs) return fail(ctx, FASTID_EINVAL, "ld_out < n_refs");
     if (n_q > 0 && !out_dev) return fail(ctx, FASTID_EINVAL, "out is NULL");
-    if ((st = check_form(ctx, db))) return st;
+    int tensor;
+    if ((st = pick_form(ctx, db, &tensor))) return st;
     if (n_q == 0) return FASTID_OK;
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     Scratch scr(ctx, s);
-    PreparedQueries pq;
     size_t xo;
+    if (tensor) {
+        TensorPrep tp;
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, nullptr, nullptr, &xo, &tp)))
+            return st;
+        MainTimer tm(ctx, s);
+        FASTID_CUDA(ctx, launch_tensor(out_bytes == 2 ? EPI_SCORES16 : EPI_SCORES32, tp.map_a, db->map_b, db->n_refs,
+                                       n_q, db->kpad, tp.qconst, 0xFFFFFFFFu, 1, out_dev, ld_out, 0, nullptr,
+                                       nullptr, nullptr, nullptr, nullptr, tp.part, ctx->dev_status, s));
+        tm.done();
+        count_launches(ctx, 1);
+        return FASTID_OK;
+    }
+    PreparedQueries pq;
     if ((st = prepare(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, 0, &xo, &pq))) return st;
     Partition part = make_partition((int32_t)(pq.n_q_pad / PL_TQ), db->n_pad / PL_TR, ctx->grid_scores);
     MainTimer tm(ctx, s);
@@ -426,11 +504,29 @@ fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_
     if (st) return st;
     if (k < 1 || k > FASTID_MAX_K) return fail(ctx, FASTID_EINVAL, "k out of range: %d", k);
     if (n_q > 0 && (!out_scores_dev || !out_idx_dev)) return fail(ctx, FASTID_EINVAL, "output is NULL");
-    if ((st = check_form(ctx, db))) return st;
+    int tensor;
+    if ((st = pick_form(ctx, db, &tensor))) return st;
     if (n_q == 0) return FASTID_OK;
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     Scratch scr(ctx, s);
+    if (tensor) {
+        TensorPrep tp;
+        size_t xo;
+        int32_t kk = k;
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, topk_extra, &kk, &xo, &tp)))
+            return st;
+        uint64_t *partial = at<uint64_t>(scr.p, xo);
+        MainTimer tm(ctx, s);
+        FASTID_CUDA(ctx, launch_tensor(EPI_TOPK, tp.map_a, db->map_b, db->n_refs, n_q, db->kpad, tp.qconst,
+                                       clamp_threshold(threshold, db->n_loci), k, nullptr, 0, 0, nullptr, nullptr,
+                                       nullptr, nullptr, partial, tp.part, ctx->dev_status, s));
+        tm.done();
+        FASTID_CUDA(ctx, launch_topk_merge_tile(partial, tp.part, tensor_tile_q(), n_q, k, out_scores_dev,
+                                                out_idx_dev, s));
+        count_launches(ctx, 2);
+        return FASTID_OK;
+    }
     const int64_t n_q_pad = round_up(n_q, PL_TQ);
     Partition part = make_partition((int32_t)(n_q_pad / PL_TQ), db->n_pad / PL_TR, ctx->grid_topk);
     const size_t partial_elems = (size_t)part.grid * part.max_seg * PL_TQ * k;
@@ -458,7 +554,8 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
     if (!hit_count_dev) return fail(ctx, FASTID_EINVAL, "hit_count is NULL");
     if (capacity > 0 && (!hit_q_dev || !hit_r_dev || !hit_score_dev))
         return fail(ctx, FASTID_EINVAL, "hit buffers are NULL");
-    if ((st = check_form(ctx, db))) return st;
+    int tensor;
+    if ((st = pick_form(ctx, db, &tensor))) return st;
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     if (n_q == 0) {
@@ -466,6 +563,25 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
         return FASTID_OK;
     }
     Scratch scr(ctx, s);
+    if (tensor) {
+        TensorPrep tp;
+        size_t xo;
+        int64_t cap = capacity;
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, hits_extra, &cap, &xo, &tp)))
+            return st;
+        unsigned long long *count = at<unsigned long long>(scr.p, xo);
+        uint64_t *sort_tmp = at<uint64_t>(scr.p, xo + 256);
+        FASTID_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
+        MainTimer tm(ctx, s);
+        FASTID_CUDA(ctx, launch_tensor(EPI_HITS, tp.map_a, db->map_b, db->n_refs, n_q, db->kpad, tp.qconst,
+                                       clamp_threshold(threshold, db->n_loci), 1, nullptr, 0, capacity, hit_q_dev,
+                                       hit_r_dev, hit_score_dev, count, nullptr, tp.part, ctx->dev_status, s));
+        tm.done();
+        FASTID_CUDA(ctx, launch_hits_finish(count, capacity, hit_q_dev, hit_r_dev, hit_score_dev, hit_count_dev,
+                                            sort_tmp, ctx->dev_status, s));
+        count_launches(ctx, 1 + hits_finish_launches(capacity));
+        return FASTID_OK;
+    }
     const int64_t P = hits_sort_elems(capacity);
     const size_t extra = 256 + (size_t)(2 + P + P / 2 + 1) * 8;
     PreparedQueries pq;

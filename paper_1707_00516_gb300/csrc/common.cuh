@@ -1,6 +1,7 @@
 // Internal definitions shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,7 +22,7 @@ constexpr int PL_TR = 128;       // references per tile
 constexpr int PL_TQ = 128;       // queries per tile
 constexpr int PL_KC = 16;        // u32 words per K stage
 constexpr int PL_THREADS = 256;  // 16 x 16 threads, 8 x 8 outputs each
-constexpr int ROW_ALIGN = 128;   // database rows are padded to this multiple
+constexpr int ROW_ALIGN = 256;   // database rows are padded to this multiple (both forms' tiles)
 constexpr int WORD_ALIGN32 = 32; // database row stride (u32 words) is a multiple of this
 
 // Epilogue kinds of the comparison kernels.
@@ -100,6 +101,25 @@ cudaError_t launch_plain(int epi, const uint32_t *refs32, const uint32_t *ref_no
 int plain_grid_target(int epi, int device);
 cudaError_t launch_topk_merge(const uint64_t *partial, const Partition &part, int64_t n_q,
                               int32_t k, uint32_t *out_scores, int64_t *out_idx, cudaStream_t s);
+cudaError_t launch_topk_merge_tile(const uint64_t *partial, const Partition &part, int32_t tile_q,
+                                   int64_t n_q, int32_t k, uint32_t *out_scores, int64_t *out_idx, cudaStream_t s);
+int64_t hits_sort_elems(int64_t capacity);
+// tensor form (tensor.cu)
+cudaError_t make_operand_map(CUtensorMap *map, const uint8_t *base, int64_t rows, int32_t kpad, int box_rows);
+int tensor_tile_q();
+int tensor_tile_r();
+int tensor_kpad(int32_t n_loci);
+int tensor_grid_target(int device);
+cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_rows, int32_t kpad, uint8_t *out,
+                             cudaStream_t s);
+cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
+                                const uint8_t *modes, int64_t n_q_pad, int32_t kpad, uint8_t *out, float *qconst,
+                                cudaStream_t s);
+cudaError_t launch_tensor(int epi, const CUtensorMap &map_a, const CUtensorMap &map_b, int64_t n_refs, int64_t n_q,
+                          int32_t kpad, const float *qconst, uint32_t threshold, int32_t k, void *out,
+                          int64_t ld_out, int64_t capacity, int64_t *hit_q, int64_t *hit_r, uint32_t *hit_score,
+                          unsigned long long *hit_count, uint64_t *partial, const Partition &part, uint32_t *status,
+                          cudaStream_t s);
 cudaError_t launch_hits_finish(unsigned long long *count, int64_t capacity, int64_t *hit_q,
                                int64_t *hit_r, uint32_t *hit_score, int64_t *count_out,
                                uint64_t *sort_tmp, uint32_t *status, cudaStream_t s);

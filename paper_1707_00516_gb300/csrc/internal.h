@@ -14,7 +14,7 @@ struct fastid_ctx {
     int sms = 0;
     cudaMemPool_t pool = nullptr;
     uint32_t *dev_status = nullptr;  // [4]
-    int grid_topk = 0, grid_hits = 0, grid_scores = 0;
+    int grid_topk = 0, grid_hits = 0, grid_scores = 0, grid_tensor = 0;
     std::string last_error;
     // profiling (fastid_profile)
     bool profile = false;
@@ -32,6 +32,9 @@ struct fastid_refdb {
     uint32_t flags = 0;
     uint64_t *packed = nullptr;  // [n_pad][ld64]
     uint32_t *norms = nullptr;   // [n_pad]
+    uint8_t *fp8 = nullptr;      // [n_pad][kpad] e4m3 0/1 operand (FASTID_REFS_TENSOR)
+    int32_t kpad = 0;            // loci padded to the tensor form's K stage
+    CUtensorMap map_b;           // TMA map over fp8 (boxes of K-stage x reference tile)
     int64_t bytes = 0;
     int device = 0;
 };

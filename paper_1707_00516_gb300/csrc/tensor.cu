@@ -177,6 +177,25 @@ __host__ __device__ constexpr uint32_t idesc_f8(int m, int n) {
            | ((uint32_t)(m >> 4) << 24);  // M >> 4
 }
 
+// Append one hit to the global list (rare path).
+__device__ __noinline__ void append_hit(const TensorArgs &a, int64_t q, int64_t r, uint32_t sc);
+
+// Insert key into this thread's ascending list (column `row` of lists[k][128]);
+// returns the new cut (D must be below it to be a candidate).  References
+// arrive in increasing order, so an equal score never displaces an entry.
+__device__ __noinline__ float list_insert(uint64_t *lists, int row, int k, int *cnt, uint64_t key, float cut,
+                                          float cq) {
+    int i = *cnt < k ? *cnt : k - 1;
+    while (i > 0 && lists[(i - 1) * 128 + row] > key) {
+        lists[i * 128 + row] = lists[(i - 1) * 128 + row];
+        --i;
+    }
+    lists[i * 128 + row] = key;
+    if (*cnt < k) ++*cnt;
+    if (*cnt == k) cut = (float)(uint32_t)(lists[(k - 1) * 128 + row] >> 32) - cq;
+    return cut;
+}
+
 struct TcSmem {
     uint64_t full[TC_STAGES];
     uint64_t empty[TC_STAGES];
@@ -186,6 +205,15 @@ struct TcSmem {
     uint32_t tmem_base;
     int abort_flag;
 };
+
+__device__ __noinline__ void append_hit(const TensorArgs &a, int64_t q, int64_t r, uint32_t sc) {
+    const unsigned long long pos = atomicAdd(a.hit_count, 1ull);
+    if (pos < (unsigned long long)a.capacity) {
+        a.hit_q[pos] = q;
+        a.hit_r[pos] = r;
+        a.hit_score[pos] = sc;
+    }
+}
 
 // Bounded wait that ignores the abort flag: used to drain this CTA's own
 // asynchronous copies and MMAs before it exits.
@@ -347,13 +375,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 cnt = 0;
                 cut = qvalid ? tplus1 - cq : -__int_as_float(0x7f800000);
             }
-            if (!mbar_wait(smem_u32(&ctl->tfull[acc]), acc_phase, abort_flag, args.status, 6)) break;
+            const bool got = mbar_wait(smem_u32(&ctl->tfull[acc]), acc_phase, abort_flag, args.status, 6);
+            __syncwarp();
+            if (!__all_sync(0xffffffffu, got)) break;
             tc_fence_after();
             const int64_t r0 = rt * TC_BN;
             const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * TC_BN);
 #pragma unroll 1
             for (int ch = 0; ch < TC_BN / 32; ++ch) {
                 uint32_t v[32];
+                __syncwarp();  // tcgen05.ld is warp-collective: reconverge first
                 tmem_ld32(taddr + ch * 32, v);
                 if (ch == TC_BN / 32 - 1) {
                     tc_fence_before();
@@ -380,32 +411,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) any |= __uint_as_float(v[j]) < cut;
                 if (!any) continue;
-#pragma unroll 1
+                // rare path; static indices keep v[] in registers
+#pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const float d = __uint_as_float(v[j]);
-                    const int64_t r = rc + j;
-                    if (!(d < cut) || r >= args.n_refs) continue;
-                    const uint32_t sc = (uint32_t)(int32_t)(d + cq);
-                    if (args.epi == EPI_HITS) {
-                        const unsigned long long pos = atomicAdd(args.hit_count, 1ull);
-                        if (pos < (unsigned long long)args.capacity) {
-                            args.hit_q[pos] = q;
-                            args.hit_r[pos] = r;
-                            args.hit_score[pos] = sc;
-                        }
-                    } else {
-                        // insertion into this thread's sorted list (references
-                        // arrive in increasing order, so an equal score never
-                        // displaces an entry)
-                        const uint64_t key = make_key(sc, (uint32_t)r);
-                        int i = cnt < k ? cnt : k - 1;
-                        while (i > 0 && lists[(i - 1) * TC_BM + row] > key) {
-                            lists[i * TC_BM + row] = lists[(i - 1) * TC_BM + row];
-                            --i;
-                        }
-                        lists[i * TC_BM + row] = key;
-                        if (cnt < k) ++cnt;
-                        if (cnt == k) cut = (float)(uint32_t)(lists[(k - 1) * TC_BM + row] >> 32) - cq;
+                    if (d < cut && rc + j < args.n_refs) {
+                        const uint32_t sc = (uint32_t)(int32_t)(d + cq);
+                        if (args.epi == EPI_HITS)
+                            append_hit(args, q, rc + j, sc);
+                        else
+                            cut = list_insert(lists, row, k, &cnt, make_key(sc, (uint32_t)(rc + j)), cut, cq);
                     }
                 }
             }

@@ -23,6 +23,7 @@ class Searcher:
         self.device = torch.device("cuda", device)
         torch.cuda.set_device(self.device)
         self.ctx = B.Context(device)
+        self.form = form
         B.fastid_set_form(self.ctx, form)
         self._pinned: dict[str, torch.Tensor] = {}
         self._devbuf: dict[str, torch.Tensor] = {}
@@ -31,8 +32,14 @@ class Searcher:
     def load_refs_packed(self, packed: torch.Tensor, n_loci: int, flags: int = 0) -> B.RefDB:
         return B.fastid_load_refs(self.ctx, packed, n_loci, flags)
 
-    def load_refs_alleles(self, alleles: torch.Tensor, n_loci: int, flags: int = 0) -> B.RefDB:
+    def default_flags(self) -> int:
+        """Database flags the chosen form needs."""
+        return B.REFS_TENSOR if self.form == B.FORM_TENSOR else 0
+
+    def load_refs_alleles(self, alleles: torch.Tensor, n_loci: int, flags: int | None = None) -> B.RefDB:
         """Pack uint8 allele rows already on the device and load them."""
+        if flags is None:
+            flags = self.default_flags()
         packed = torch.empty((alleles.shape[0], words64(n_loci)), dtype=torch.int64, device=self.device)
         B.fastid_pack(self.ctx, alleles, n_loci, packed)
         db = B.fastid_load_refs(self.ctx, packed, n_loci, flags)

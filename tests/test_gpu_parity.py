@@ -1,5 +1,5 @@
 """GPU parity: every kernel result through the C ABI equals the CPU oracle's,
-element by element (integers: zero tolerance)."""
+element by element (integers: zero tolerance), for both compute forms."""
 import numpy as np
 import pytest
 
@@ -13,11 +13,13 @@ from paper_1707_00516_gb300 import binding as B  # noqa: E402
 from paper_1707_00516_gb300.search import Searcher, words64  # noqa: E402
 
 
-@pytest.fixture(scope="module")
-def searcher():
+@pytest.fixture(scope="module", params=["plain", "tensor"])
+def searcher(request):
+    """One searcher per compute form; databases are loaded with the flags
+    the form needs (the tensor form's e4m3 operand copy)."""
     import __graft_entry__
     __graft_entry__.build()
-    s = Searcher(0, B.FORM_PLAIN)
+    s = Searcher(0, B.FORM_PLAIN if request.param == "plain" else B.FORM_TENSOR)
     yield s
     s.ctx.close()
 

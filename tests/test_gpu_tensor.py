@@ -1,0 +1,99 @@
+"""Tensor form (tcgen05, e4m3 operands, FP32 accumulation): exactness at the
+largest loci counts and form selection.  Scores are integers; the test is
+equality with the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1707_00516_gb300 import binding as B  # noqa: E402
+from paper_1707_00516_gb300.search import Searcher, words64  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ts():
+    import __graft_entry__
+    __graft_entry__.build()
+    s = Searcher(0, B.FORM_TENSOR)
+    yield s
+    s.ctx.close()
+
+
+def _full(s, R, Q, modes, n_loci, dtype=torch.int32):
+    db = s.load_refs_alleles(torch.from_numpy(np.ascontiguousarray(R)).cuda(), n_loci)
+    q = torch.empty((Q.shape[0], words64(n_loci)), dtype=torch.int64, device="cuda")
+    B.fastid_pack(s.ctx, torch.from_numpy(np.ascontiguousarray(Q)).cuda(), n_loci, q)
+    out = s.scores(db, q, torch.from_numpy(modes).cuda(), dtype)
+    torch.cuda.synchronize()
+    assert B.fastid_sync_status(s.ctx) == B.OK
+    db.close()
+    return out.cpu().numpy().view(np.uint32 if dtype == torch.int32 else np.uint16)
+
+
+def test_tiny(ts):
+    rng = np.random.default_rng(0)
+    R = (rng.random((5, 200)) < 0.5).astype(np.uint8)
+    Q = (rng.random((3, 200)) < 0.5).astype(np.uint8)
+    modes = np.array([0, 1, 0], np.uint8)
+    mis, une = oracle.scores(R, Q)
+    assert np.array_equal(_full(ts, R, Q, modes, 200), oracle.select(mis, une, modes))
+
+
+@pytest.mark.parametrize("n_loci", [16384, 65536])
+def test_extreme_counts_exact(ts, n_loci):
+    """All-ones / all-zero / alternating profiles drive the accumulators to
+    +-N, the largest magnitudes the FP32 accumulation must hold exactly."""
+    R = np.zeros((6, n_loci), np.uint8)
+    R[0] = 1
+    R[2, ::2] = 1
+    R[3, 1::2] = 1
+    R[4, : n_loci // 3] = 1
+    R[5] = 1
+    R[5, -1] = 0
+    Q = np.stack([R[0], R[1], R[2], R[5], R[0], R[1]])
+    modes = np.array([0, 0, 0, 1, 1, 1], np.uint8)
+    mis, une = oracle.scores(R, Q)
+    got = _full(ts, R, Q, modes, n_loci)
+    assert np.array_equal(got, oracle.select(mis, une, modes))
+    assert got.max() == n_loci  # reached the extreme
+
+
+@pytest.mark.parametrize("n_loci,p", [(16384, 0.5), (32768, 0.3), (65536, 0.7)])
+def test_random_large_n_exact(ts, n_loci, p):
+    rng = np.random.default_rng(n_loci)
+    R = (rng.random((37, n_loci)) < p).astype(np.uint8)
+    Q = (rng.random((9, n_loci)) < p).astype(np.uint8)
+    modes = (np.arange(9) % 2).astype(np.uint8)
+    mis, une = oracle.scores(R, Q)
+    assert np.array_equal(_full(ts, R, Q, modes, n_loci), oracle.select(mis, une, modes))
+
+
+def test_uint16_scores(ts):
+    rng = np.random.default_rng(3)
+    R = (rng.random((300, 1024)) < 0.4).astype(np.uint8)
+    Q = (rng.random((129, 1024)) < 0.4).astype(np.uint8)
+    modes = (np.arange(129) % 3 == 0).astype(np.uint8)
+    mis, une = oracle.scores(R, Q)
+    exp = oracle.select(mis, une, modes).astype(np.uint16)
+    assert np.array_equal(_full(ts, R, Q, modes, 1024, torch.int16), exp)
+
+
+def test_tensor_form_needs_operand_copy(ts):
+    R = np.ones((10, 64), np.uint8)
+    db = ts.load_refs_alleles(torch.from_numpy(R).cuda(), 64, flags=0)
+    q = torch.zeros((2, 1), dtype=torch.int64, device="cuda")
+    m = torch.zeros(2, dtype=torch.uint8, device="cuda")
+    sc = torch.empty((2, 4), dtype=torch.int32, device="cuda")
+    ix = torch.empty((2, 4), dtype=torch.int64, device="cuda")
+    with pytest.raises(B.FastIDError) as e:
+        B.fastid_topk(ts.ctx, db, q, m, 4, B.NO_THRESHOLD, sc, ix)
+    assert e.value.status == B.EUNSUPPORTED
+    info = db.info()
+    assert info["flags"] == 0
+    db.close()
+    db2 = ts.load_refs_alleles(torch.from_numpy(R).cuda(), 64)
+    assert db2.info()["flags"] == B.REFS_TENSOR
+    db2.close()
