@@ -242,7 +242,7 @@ def run_reference(args, w):
     import oracle
     oracle.build()
     seed = gen.config_seed(w["cfg"])
-    recipe = recipe_for(args.config)
+    recipe = recipe_for(args.config, n_refs=w["n_refs"])
     thr = gen.maf_thresholds(seed, w["n_loci"])
     src, off, modes = query_inputs(recipe, thr)
     q = oracle.mix(src, off)
@@ -379,7 +379,7 @@ def run_gpu(args, w):
     n_refs, n_loci, k, T = w["n_refs"], w["n_loci"], w["k"], w["threshold"]
     flags = B.REFS_TENSOR if "tensor" in forms else 0
     db, thr = build_db(s, seed, n_refs, n_loci, flags)
-    recipe = recipe_for(args.config)
+    recipe = recipe_for(args.config, n_refs=n_refs)
     src, off, modes = query_inputs(recipe, thr)
     n_q = recipe.n_queries
     d_src = torch.from_numpy(src).to(dev)
@@ -436,14 +436,19 @@ def run_gpu(args, w):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", choices=["plain", "tensor", "both"], default="both")
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="c3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--refs", type=int, default=None,
+                    help="override the number of references (smaller captures for profiling)")
     args = ap.parse_args(argv)
-    w = WORKLOADS[args.config]
+    w = dict(WORKLOADS[args.config])
+    if args.refs:
+        w["n_refs"] = args.refs
+        w["workload"] = w["workload"].replace("20M", f"{args.refs}").replace("1M", f"{args.refs}")
     if args.impl == "reference":
         run_reference(args, w)
     else:
