@@ -177,23 +177,30 @@ __host__ __device__ constexpr uint32_t idesc_f8(int m, int n) {
            | ((uint32_t)(m >> 4) << 24);  // M >> 4
 }
 
-// Append one hit to the global list (rare path).
-__device__ __noinline__ void append_hit(const TensorArgs &a, int64_t q, int64_t r, uint32_t sc);
+// Per-thread top-k list held in registers, ascending by score; entries of
+// equal score keep arrival order (references arrive in increasing order, so
+// the earlier entry has the lower index).  Inserting (xs, xr) is a fixed
+// compare-select network, so all lanes of a warp insert in lock-step; a lane
+// with nothing to insert passes xs = INT32_MAX, which changes nothing.
+// For a runtime k <= 32 the first 32 - k slots hold INT32_MIN place-holders
+// that nothing displaces, so the k kept entries sit in slots 32-k .. 31 and
+// the k-th smallest is always slot 31 (static register indices only).
+constexpr int TC_KMAX = 32;
+constexpr int32_t NET_EMPTY = 0x7fffffff;
+constexpr int32_t NET_HOLD = (int32_t)0x80000000;
 
-// Insert key into this thread's ascending list (column `row` of lists[k][128]);
-// returns the new cut (D must be below it to be a candidate).  References
-// arrive in increasing order, so an equal score never displaces an entry.
-__device__ __noinline__ float list_insert(uint64_t *lists, int row, int k, int *cnt, uint64_t key, float cut,
-                                          float cq) {
-    int i = *cnt < k ? *cnt : k - 1;
-    while (i > 0 && lists[(i - 1) * 128 + row] > key) {
-        lists[i * 128 + row] = lists[(i - 1) * 128 + row];
-        --i;
+__device__ __forceinline__ void net_insert(int32_t (&ls)[TC_KMAX], uint32_t (&lr)[TC_KMAX], int32_t xs,
+                                           uint32_t xr) {
+#pragma unroll
+    for (int i = TC_KMAX - 1; i > 0; --i) {
+        const bool shift = xs < ls[i - 1];
+        const bool here = xs < ls[i];
+        ls[i] = shift ? ls[i - 1] : (here ? xs : ls[i]);
+        lr[i] = shift ? lr[i - 1] : (here ? xr : lr[i]);
     }
-    lists[i * 128 + row] = key;
-    if (*cnt < k) ++*cnt;
-    if (*cnt == k) cut = (float)(uint32_t)(lists[(k - 1) * 128 + row] >> 32) - cq;
-    return cut;
+    const bool first = xs < ls[0];
+    ls[0] = first ? xs : ls[0];
+    lr[0] = first ? xr : lr[0];
 }
 
 struct TcSmem {
@@ -206,12 +213,13 @@ struct TcSmem {
     int abort_flag;
 };
 
-__device__ __noinline__ void append_hit(const TensorArgs &a, int64_t q, int64_t r, uint32_t sc) {
-    const unsigned long long pos = atomicAdd(a.hit_count, 1ull);
-    if (pos < (unsigned long long)a.capacity) {
-        a.hit_q[pos] = q;
-        a.hit_r[pos] = r;
-        a.hit_score[pos] = sc;
+__device__ __noinline__ void append_hit(unsigned long long *count, int64_t capacity, int64_t *hq, int64_t *hr,
+                                       uint32_t *hs, int64_t q, int64_t r, uint32_t sc) {
+    const unsigned long long pos = atomicAdd(count, 1ull);
+    if (pos < (unsigned long long)capacity) {
+        hq[pos] = q;
+        hr[pos] = r;
+        hs[pos] = sc;
     }
 }
 
@@ -239,7 +247,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint8_t *sA = base;
     uint8_t *sB = base + TC_STAGES * TC_A_BYTES;
     TcSmem *ctl = reinterpret_cast<TcSmem *>(base + TC_STAGES * (TC_A_BYTES + TC_B_BYTES));
-    uint64_t *lists = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(ctl) + 256);  // [k][128]
+    // per-thread staging of one 32-column chunk, [32][128] floats (rare path)
+    float *stage_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(ctl) + 256);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -355,9 +364,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint32_t acc_phase = 0;
         int64_t qt_prev = -1;
         int seg = 0;
-        int cnt = 0;       // entries in this thread's list
+        int32_t ls[TC_KMAX];  // this thread's top-k scores (see net_insert)
+        uint32_t lr[TC_KMAX]; // and their references
         float cq = 0.f;    // c_q
         float cut = 0.f;   // D must be < cut to be a candidate
+        float cut0 = 0.f;  // cut while the list is not full
         bool qvalid = false;
         int64_t q = 0;
         for (int64_t u = u_begin; u < u_end; ++u) {
@@ -365,15 +376,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (qt != qt_prev) {
                 if (args.epi == EPI_TOPK && qt_prev >= 0) {
                     uint64_t *dst = args.partial + ((c * P.max_seg + seg) * TC_BM + row) * (int64_t)k;
-                    for (int s = 0; s < k; ++s) dst[s] = s < cnt ? lists[s * TC_BM + row] : KEY_EMPTY;
+#pragma unroll
+                    for (int i = 0; i < TC_KMAX; ++i)
+                        if (i >= TC_KMAX - k)
+                            dst[i - (TC_KMAX - k)] = ls[i] == NET_EMPTY ? KEY_EMPTY : make_key((uint32_t)ls[i], lr[i]);
                     ++seg;
                 }
                 qt_prev = qt;
                 q = qt * TC_BM + row;
                 qvalid = q < args.n_q;
                 cq = args.qconst[q];
-                cnt = 0;
-                cut = qvalid ? tplus1 - cq : -__int_as_float(0x7f800000);
+#pragma unroll
+                for (int i = 0; i < TC_KMAX; ++i) {
+                    ls[i] = i < TC_KMAX - k ? NET_HOLD : NET_EMPTY;
+                    lr[i] = 0xFFFFFFFFu;
+                }
+                cut0 = qvalid ? tplus1 - cq : -__int_as_float(0x7f800000);
+                cut = cut0;
             }
             const bool got = mbar_wait(smem_u32(&ctl->tfull[acc]), acc_phase, abort_flag, args.status, 6);
             __syncwarp();
@@ -407,21 +426,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     continue;
                 }
-                bool any = false;
+                uint32_t m = 0;  // columns of this chunk that pass the filter
 #pragma unroll
-                for (int j = 0; j < 32; ++j) any |= __uint_as_float(v[j]) < cut;
-                if (!any) continue;
-                // rare path; static indices keep v[] in registers
+                for (int j = 0; j < 32; ++j) m |= (uint32_t)(__uint_as_float(v[j]) < cut) << j;
+                if (rc + 32 > args.n_refs) m &= rc >= args.n_refs ? 0u : ((1u << (args.n_refs - rc)) - 1u);
+                if (!__any_sync(0xffffffffu, m != 0u)) continue;
+                if (args.epi == EPI_HITS) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float d = __uint_as_float(v[j]);
-                    if (d < cut && rc + j < args.n_refs) {
-                        const uint32_t sc = (uint32_t)(int32_t)(d + cq);
-                        if (args.epi == EPI_HITS)
-                            append_hit(args, q, rc + j, sc);
-                        else
-                            cut = list_insert(lists, row, k, &cnt, make_key(sc, (uint32_t)(rc + j)), cut, cq);
+                    for (int j = 0; j < 32; ++j)
+                        if (m & (1u << j))
+                            append_hit(args.hit_count, args.capacity, args.hit_q, args.hit_r, args.hit_score, q,
+                                       rc + j, (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq));
+                    continue;
+                }
+                // rare path: stage the chunk, then insert candidates in lock-step
+#pragma unroll
+                for (int j = 0; j < 32; ++j) stage_v[j * TC_BM + row] = __uint_as_float(v[j]);
+                while (__any_sync(0xffffffffu, m != 0u)) {
+                    int32_t xs = NET_EMPTY;
+                    uint32_t xr = 0u;
+                    if (m != 0u) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1u;
+                        const float d = stage_v[j * TC_BM + row];
+                        if (d < cut) {
+                            xs = (int32_t)(d + cq);
+                            xr = (uint32_t)(rc + j);
+                        }
                     }
+                    net_insert(ls, lr, xs, xr);
+                    cut = ls[TC_KMAX - 1] == NET_EMPTY ? cut0 : (float)ls[TC_KMAX - 1] - cq;
                 }
             }
             if (++acc == 2) {
@@ -431,7 +465,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         if (args.epi == EPI_TOPK && qt_prev >= 0 && !*abort_flag) {
             uint64_t *dst = args.partial + ((c * P.max_seg + seg) * TC_BM + row) * (int64_t)k;
-            for (int s = 0; s < k; ++s) dst[s] = s < cnt ? lists[s * TC_BM + row] : KEY_EMPTY;
+#pragma unroll
+            for (int i = 0; i < TC_KMAX; ++i)
+                if (i >= TC_KMAX - k)
+                    dst[i - (TC_KMAX - k)] = ls[i] == NET_EMPTY ? KEY_EMPTY : make_key((uint32_t)ls[i], lr[i]);
         }
     }
 
@@ -517,7 +554,7 @@ __global__ void queries_e4m3_kernel(const uint64_t *__restrict__ q, int64_t ld_q
 
 size_t tensor_smem(int epi) {
     size_t s = 1024 + TC_STAGES * (size_t)(TC_A_BYTES + TC_B_BYTES) + 256;
-    if (epi == EPI_TOPK) s += (size_t)FASTID_MAX_K * TC_BM * sizeof(uint64_t);
+    if (epi == EPI_TOPK) s += (size_t)32 * TC_BM * sizeof(float);
     return s;
 }
 
