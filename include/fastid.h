@@ -223,6 +223,57 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
                              int64_t *hit_r_dev, uint32_t *hit_score_dev, int64_t *hit_count_dev,
                              fastid_stream stream);
 
+/* ------------------------------------------------- batched persistent plans */
+/*
+ * Many query batches of uneven size against several reference databases
+ * ("panels", e.g. loci panels of different N) in ONE persistent tensor-form
+ * launch: the per-query top-k of fastid_topk for every batch.  (Batching is
+ * not in the paper; it applies Eq. 1 / the XOR count exactly as fastid_topk.)
+ *
+ * A plan fixes panels, batches, k and threshold and owns all scratch memory,
+ * so fastid_plan_run allocates nothing and never synchronises: it enqueues an
+ * operand-preparation kernel, the persistent compare kernel over the units
+ * (panel, 128-query tile, reference tile) of all panels -- CTAs take
+ * cost-balanced unit ranges -- and a merge kernel that writes each batch's
+ * outputs.  fastid_plan_capture records one run into a CUDA graph;
+ * fastid_plan_replay launches that graph.  Between runs the caller may change
+ * the contents (not the addresses or sizes) of the batch buffers.
+ *
+ * Every panel must have been loaded with FASTID_REFS_TENSOR; at most 8 panels.
+ * Batch queries use the packed layout of fastid_topk; out_scores/out_idx are
+ * [n_q][k] as in fastid_topk.  variant picks the reference-tile width of the
+ * compare kernel (FASTID_VARIANT_*; the autotuner in the Python package
+ * chooses it per workload).  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA.
+ */
+typedef struct fastid_plan fastid_plan;
+
+typedef struct {
+    int32_t panel;               /* index into the plan's databases            */
+    const uint64_t *queries_dev; /* [n_q][ld_q] packed queries                 */
+    int64_t ld_q;
+    int64_t n_q;                 /* 0 allowed                                  */
+    const uint8_t *modes_dev;    /* [n_q] FASTID_MODE_*                        */
+    uint32_t *out_scores_dev;    /* [n_q][k]                                   */
+    int64_t *out_idx_dev;        /* [n_q][k]                                   */
+} fastid_batch;
+
+enum {
+    FASTID_VARIANT_AUTO = 0,        /* the library's default (N256)            */
+    FASTID_VARIANT_TENSOR_N256 = 1, /* 128 x 256 tiles, 3-stage pipeline       */
+    FASTID_VARIANT_TENSOR_N128 = 2  /* 128 x 128 tiles, 5-stage pipeline       */
+};
+
+fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs, int32_t n_panels,
+                                 const fastid_batch *batches, int32_t n_batches, int32_t k,
+                                 uint32_t threshold, int32_t variant, fastid_plan **out);
+fastid_status fastid_plan_run(fastid_plan *plan, fastid_stream stream);
+fastid_status fastid_plan_capture(fastid_plan *plan, fastid_stream stream);
+fastid_status fastid_plan_replay(fastid_plan *plan, fastid_stream stream);
+fastid_status fastid_plan_info(const fastid_plan *plan, int64_t *n_queries, int64_t *n_units, int32_t *grid,
+                               int32_t *variant, int64_t *workspace_bytes);
+/* Synchronises the device and frees the plan.  NULL is accepted. */
+fastid_status fastid_plan_destroy(fastid_plan *plan);
+
 /*
  * fastid_topk_noalloc -- fastid_topk for callers that cannot allocate device
  * memory.  The paper has no counterpart; this entry point exists for

@@ -27,6 +27,7 @@ MAX_K = 32
 MAX_LOCI = 65536
 NO_THRESHOLD = 0xFFFFFFFF
 NOALLOC_SCRATCH_BYTES = 16 << 20
+VARIANT_AUTO, VARIANT_TENSOR_N256, VARIANT_TENSOR_N128 = 0, 1, 2
 
 _lib = None
 _lock = threading.Lock()
@@ -65,6 +66,13 @@ _PROTOS = {
     "fastid_topk": (_I32, [_P, _P, _P, _I64, _I64, _P, _I32, _U32, _P, _P, _P]),
     "fastid_compare": (_I32, [_P, _P, _P, _I64, _I64, _P, _U32, _I64, _P, _P, _P, _P, _P]),
     "fastid_topk_noalloc": (_I32, [_P, _P, _P, _I64, _I64, _P, _I32, _U32, _P, _P, _P]),
+    "fastid_plan_create": (_I32, [_P, _P, _I32, _P, _I32, _I32, _U32, _I32, ctypes.POINTER(_P)]),
+    "fastid_plan_run": (_I32, [_P, _P]),
+    "fastid_plan_capture": (_I32, [_P, _P]),
+    "fastid_plan_replay": (_I32, [_P, _P]),
+    "fastid_plan_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I32),
+                                ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "fastid_plan_destroy": (_I32, [_P]),
 }
 
 # Every symbol the header declares (checked by the CPU tests).
@@ -303,3 +311,71 @@ def fastid_topk_noalloc(ctx: Context, db: RefDB, queries: torch.Tensor, modes: t
         raise ValueError("modes / outputs do not match n_q x k")
     ctx.check(load_library().fastid_topk_noalloc(ctx.handle, db.handle, q, _ld(queries), n_q, m, k, threshold,
                                                  s, i, _stream_ptr(stream)))
+
+
+class FastIDBatch(ctypes.Structure):
+    """Mirror of the C struct fastid_batch."""
+    _fields_ = [("panel", ctypes.c_int32), ("queries_dev", ctypes.c_void_p), ("ld_q", ctypes.c_int64),
+                ("n_q", ctypes.c_int64), ("modes_dev", ctypes.c_void_p), ("out_scores_dev", ctypes.c_void_p),
+                ("out_idx_dev", ctypes.c_void_p)]
+
+
+class Plan:
+    """A fastid_plan: fixed panels and batches, reusable runs and graph replays.
+
+    batches: list of (panel, queries int64 [n_q, ld], modes uint8 [n_q],
+    out_scores int32 [n_q, k], out_idx int64 [n_q, k]) CUDA tensors.  The
+    tensors must stay alive (and at the same addresses) for the plan's life.
+    """
+
+    def __init__(self, ctx: Context, dbs, batches, k: int, threshold: int = NO_THRESHOLD,
+                 variant: int = VARIANT_AUTO):
+        lib = load_library()
+        self.ctx, self._lib = ctx, lib
+        self._keep = [dbs, batches]
+        arr = (FastIDBatch * max(1, len(batches)))()
+        for i, (panel, q, m, sc, ix) in enumerate(batches):
+            n = q.size(0)
+            if n:
+                _dev(q, torch.int64, "queries", 2)
+                _dev(m, torch.uint8, "modes", 1)
+                _dev(sc, torch.int32, "out_scores", 2)
+                _dev(ix, torch.int64, "out_idx", 2)
+                if tuple(sc.shape) != (n, k) or tuple(ix.shape) != (n, k) or m.numel() != n:
+                    raise ValueError("batch outputs must be [n_q, k]")
+            arr[i] = FastIDBatch(panel, q.data_ptr() if n else None, _ld(q) if n else dbs[panel].n_loci // 64 + 1,
+                                 n, m.data_ptr() if n else None, sc.data_ptr() if n else None,
+                                 ix.data_ptr() if n else None)
+        self._arr = arr
+        handles = (_P * len(dbs))(*[d.handle.value for d in dbs])
+        h = _P()
+        ctx.check(lib.fastid_plan_create(ctx.handle, handles, len(dbs), arr, len(batches), k, threshold, variant,
+                                         ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        self.ctx.check(self._lib.fastid_plan_run(self.handle, _stream_ptr(stream)))
+
+    def capture(self, stream=None):
+        self.ctx.check(self._lib.fastid_plan_capture(self.handle, _stream_ptr(stream)))
+
+    def replay(self, stream=None):
+        self.ctx.check(self._lib.fastid_plan_replay(self.handle, _stream_ptr(stream)))
+
+    def info(self) -> dict:
+        nq, nu, g, v, wb = _I64(), _I64(), _I32(), _I32(), _I64()
+        self.ctx.check(self._lib.fastid_plan_info(self.handle, ctypes.byref(nq), ctypes.byref(nu), ctypes.byref(g),
+                                                  ctypes.byref(v), ctypes.byref(wb)))
+        return {"n_queries": nq.value, "n_units": nu.value, "grid": g.value, "variant": v.value,
+                "workspace_bytes": wb.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.fastid_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

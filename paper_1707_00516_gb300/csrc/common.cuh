@@ -63,6 +63,61 @@ __host__ inline Partition make_partition(int32_t n_qt, int64_t n_rt, int32_t gri
     return p;
 }
 
+// Panels (databases) one tensor-form launch can walk, and the tensor form's
+// query-tile height (TMEM lanes).
+constexpr int TC_MAXP = 8;
+constexpr int TC_TILE_Q = 128;
+
+// Batched form: one operand row to encode (src == nullptr: padding row).
+struct PrepJob {
+    const uint64_t *src;   // packed query row
+    const uint8_t *mode;   // its mode byte
+    uint8_t *dst;          // e4m3 operand row [kpad]
+    float *qc;             // its c_q
+    int32_t n_words;
+    int32_t n_loci;
+    int32_t kpad;
+    int32_t pad_;
+};
+
+// Batched form: one query's merge of per-segment lists into its output row.
+struct MergeJob {
+    uint32_t *out_s;  // [k]
+    int64_t *out_i;   // [k]
+    int32_t g;        // global query-tile id
+    int32_t ql;       // row within the tile
+};
+
+// Host-side description of one tensor-form launch over up to TC_MAXP panels.
+struct TcLaunch {
+    int32_t n_panels;
+    CUtensorMap map_a[TC_MAXP];
+    CUtensorMap map_b[TC_MAXP];
+    int64_t n_refs[TC_MAXP];
+    int64_t n_q[TC_MAXP];
+    int64_t n_rt[TC_MAXP];
+    int64_t unit_base[TC_MAXP];
+    int32_t kpad[TC_MAXP];
+    int32_t tile_base[TC_MAXP];
+    const float *qconst[TC_MAXP];
+    int64_t n_units;
+    int32_t grid;
+    int32_t max_seg;
+    const int64_t *cta_units;
+    uint32_t threshold;
+    int32_t k;
+    int32_t epi;
+    void *out;
+    int64_t ld_out;
+    int64_t capacity;
+    int64_t *hit_q;
+    int64_t *hit_r;
+    uint32_t *hit_score;
+    unsigned long long *hit_count;
+    uint64_t *partial;
+    uint32_t *status;
+};
+
 // Top-k keys: (score << 32) | ref, so that ordering keys orders by score then
 // by reference index.  An empty slot holds KEY_EMPTY.
 constexpr uint64_t KEY_EMPTY = ~0ull;
@@ -120,6 +175,11 @@ cudaError_t launch_tensor(int epi, const CUtensorMap &map_a, const CUtensorMap &
                           int64_t ld_out, int64_t capacity, int64_t *hit_q, int64_t *hit_r, uint32_t *hit_score,
                           unsigned long long *hit_count, uint64_t *partial, const Partition &part, uint32_t *status,
                           cudaStream_t s);
+cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s);
+cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s);
+cudaError_t launch_merge_jobs(const uint64_t *partial, const MergeJob *jobs, int64_t n_jobs, const int32_t *g_lo,
+                              const int32_t *g_hi, const int32_t *cta_gfirst, int32_t max_seg, int32_t tile_q,
+                              int32_t k, cudaStream_t s);
 cudaError_t launch_hits_finish(unsigned long long *count, int64_t capacity, int64_t *hit_q,
                                int64_t *hit_r, uint32_t *hit_score, int64_t *count_out,
                                uint64_t *sort_tmp, uint32_t *status, cudaStream_t s);

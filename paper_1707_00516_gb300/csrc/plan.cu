@@ -1,0 +1,380 @@
+// Batched top-k over several reference databases ("panels", e.g. loci
+// panels of different sizes) in one persistent tensor-form launch.
+//
+// A plan fixes the panels, the batches (each a set of queries against one
+// panel, with its own output buffers), k and the threshold.  Creating it
+// allocates and fills every table the launches need; running it enqueues
+// three kernels -- operand preparation for every batch row, one persistent
+// compare launch that walks the units (panel, 128-query tile, reference tile)
+// of all panels, and the merge that writes each batch's results -- with no
+// allocation and no host synchronisation, so a run can be captured once into
+// a CUDA graph (fastid_plan_capture) and replayed (fastid_plan_replay) with
+// new query contents in the same buffers.
+//
+// Work balance: units differ in cost by their panel's K stages, so CTA c
+// takes the units whose cumulative cost falls in [c C / G, (c+1) C / G).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace fastid;
+
+struct fastid_plan {
+    fastid_ctx *ctx = nullptr;
+    int32_t n_panels = 0;
+    int32_t bn = 256;
+    int32_t k = 0;
+    uint32_t threshold = 0;
+    int64_t n_queries = 0;
+    int64_t n_jobs_prep = 0;
+    int64_t n_jobs_merge = 0;
+    TcLaunch launch;
+    void *work = nullptr;  // one device allocation for every table and operand
+    int64_t work_bytes = 0;
+    PrepJob *prep = nullptr;
+    MergeJob *merge = nullptr;
+    int32_t *g_lo = nullptr, *g_hi = nullptr, *cta_gfirst = nullptr;
+    int64_t *cta_units = nullptr;
+    uint64_t *partial = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+};
+
+namespace {
+
+int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+fastid_status perr(fastid_ctx *ctx, fastid_status st, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+fastid_status pcuda(fastid_ctx *ctx, cudaError_t e, const char *what) {
+    cudaGetLastError();
+    return perr(ctx, e == cudaErrorMemoryAllocation ? FASTID_ENOMEM : FASTID_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void free_plan(fastid_plan *p) {
+    if (!p) return;
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->work) cudaFree(p->work);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs, int32_t n_panels,
+                                 const fastid_batch *batches, int32_t n_batches, int32_t k, uint32_t threshold,
+                                 int32_t variant, fastid_plan **out) {
+    if (!ctx) return FASTID_EINVAL;
+    if (!out) return perr(ctx, FASTID_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!dbs || n_panels < 1 || n_panels > TC_MAXP)
+        return perr(ctx, FASTID_EINVAL, "n_panels must be in 1..8 with a database per panel");
+    if (n_batches < 0 || (n_batches > 0 && !batches)) return perr(ctx, FASTID_EINVAL, "bad batch list");
+    if (k < 1 || k > FASTID_MAX_K) return perr(ctx, FASTID_EINVAL, "k out of range");
+    if (variant != FASTID_VARIANT_AUTO && variant != FASTID_VARIANT_TENSOR_N256 &&
+        variant != FASTID_VARIANT_TENSOR_N128)
+        return perr(ctx, FASTID_EINVAL, "unknown variant");
+    for (int p = 0; p < n_panels; ++p) {
+        if (!dbs[p]) return perr(ctx, FASTID_EINVAL, "database is NULL");
+        if (dbs[p]->device != ctx->device) return perr(ctx, FASTID_EINVAL, "database belongs to another device");
+        if (!dbs[p]->fp8)
+            return perr(ctx, FASTID_EUNSUPPORTED, "batched plans use the tensor form: load every panel with "
+                                                  "FASTID_REFS_TENSOR");
+    }
+    for (int b = 0; b < n_batches; ++b) {
+        const fastid_batch &B = batches[b];
+        if (B.panel < 0 || B.panel >= n_panels) return perr(ctx, FASTID_EINVAL, "batch panel out of range");
+        if (B.n_q < 0 || B.n_q > 0x7fffffffll) return perr(ctx, FASTID_EINVAL, "batch n_q out of range");
+        if (B.n_q > 0 && (!B.queries_dev || !B.modes_dev || !B.out_scores_dev || !B.out_idx_dev))
+            return perr(ctx, FASTID_EINVAL, "batch buffer is NULL");
+        if (B.ld_q < dbs[B.panel]->n_words64) return perr(ctx, FASTID_EINVAL, "batch ld_q too small");
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return pcuda(ctx, e, "cudaSetDevice");
+
+    fastid_plan *P = new (std::nothrow) fastid_plan();
+    if (!P) return perr(ctx, FASTID_ENOMEM, "host allocation");
+    P->ctx = ctx;
+    P->n_panels = n_panels;
+    P->bn = variant == FASTID_VARIANT_TENSOR_N128 ? 128 : 256;
+    P->k = k;
+    P->threshold = threshold;
+    const int BN = P->bn;
+
+    // Rows of each panel's operand: its batches' queries, in batch order.
+    std::vector<int64_t> rows(n_panels, 0);
+    for (int b = 0; b < n_batches; ++b) rows[batches[b].panel] += batches[b].n_q;
+    std::vector<int64_t> rows_pad(n_panels), n_qt(n_panels), n_rt(n_panels), unit_base(n_panels + 1),
+        cost_base(n_panels + 1), tile_base(n_panels + 1);
+    unit_base[0] = cost_base[0] = tile_base[0] = 0;
+    for (int p = 0; p < n_panels; ++p) {
+        rows_pad[p] = rup(std::max<int64_t>(rows[p], 1), TC_TILE_Q);
+        n_qt[p] = rows[p] > 0 ? rows_pad[p] / TC_TILE_Q : 0;
+        n_rt[p] = dbs[p]->n_pad / BN;
+        unit_base[p + 1] = unit_base[p] + n_qt[p] * n_rt[p];
+        cost_base[p + 1] = cost_base[p] + n_qt[p] * n_rt[p] * (dbs[p]->kpad / 128);
+        tile_base[p + 1] = tile_base[p] + n_qt[p];
+        P->n_queries += rows[p];
+    }
+    const int64_t U = unit_base[n_panels], C = cost_base[n_panels];
+    const int64_t n_tiles = tile_base[n_panels];
+    int64_t G = std::min<int64_t>(ctx->grid_tensor, std::max<int64_t>(U, 1));
+
+    // Cost-balanced unit ranges.
+    std::vector<int64_t> cta(G + 1);
+    for (int64_t c = 0; c <= G; ++c) {
+        const int64_t T = (c * C) / G;
+        int p = 0;
+        while (p + 1 < n_panels && cost_base[p + 1] <= T) ++p;
+        const int64_t w = dbs[p]->kpad / 128;
+        int64_t u = unit_base[p] + (T - cost_base[p] + w - 1) / w;
+        cta[c] = std::min(u, U);
+    }
+    cta[0] = 0;
+    cta[G] = U;
+    auto tile_of = [&](int64_t u) -> int64_t {
+        int p = 0;
+        while (p + 1 < n_panels && unit_base[p + 1] <= u) ++p;
+        return tile_base[p] + (u - unit_base[p]) / n_rt[p];
+    };
+    std::vector<int32_t> gfirst(G, 0), glo(std::max<int64_t>(n_tiles, 1), INT32_MAX),
+        ghi(std::max<int64_t>(n_tiles, 1), -1);
+    int32_t max_seg = 1;
+    for (int64_t c = 0; c < G; ++c) {
+        if (cta[c + 1] <= cta[c]) continue;
+        const int64_t g0 = tile_of(cta[c]), g1 = tile_of(cta[c + 1] - 1);
+        gfirst[c] = (int32_t)g0;
+        max_seg = std::max<int32_t>(max_seg, (int32_t)(g1 - g0 + 1));
+        for (int64_t g = g0; g <= g1; ++g) {
+            glo[g] = std::min<int32_t>(glo[g], (int32_t)c);
+            ghi[g] = std::max<int32_t>(ghi[g], (int32_t)c);
+        }
+    }
+
+    // Workspace layout.
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        size_t at = off;
+        off += bytes;
+        return at;
+    };
+    std::vector<size_t> o_a(n_panels), o_qc(n_panels);
+    int64_t n_prep = 0;
+    for (int p = 0; p < n_panels; ++p) {
+        o_a[p] = take((size_t)rows_pad[p] * dbs[p]->kpad);
+        o_qc[p] = take((size_t)rows_pad[p] * sizeof(float));
+        n_prep += rows_pad[p];
+    }
+    const size_t o_prep = take((size_t)n_prep * sizeof(PrepJob));
+    const size_t o_merge = take((size_t)std::max<int64_t>(P->n_queries, 1) * sizeof(MergeJob));
+    const size_t o_glo = take((size_t)std::max<int64_t>(n_tiles, 1) * sizeof(int32_t));
+    const size_t o_ghi = take((size_t)std::max<int64_t>(n_tiles, 1) * sizeof(int32_t));
+    const size_t o_gf = take((size_t)G * sizeof(int32_t));
+    const size_t o_cta = take((size_t)(G + 1) * sizeof(int64_t));
+    const size_t o_part = take((size_t)G * max_seg * TC_TILE_Q * k * sizeof(uint64_t));
+    e = cudaMalloc(&P->work, off);
+    if (e != cudaSuccess) {
+        free_plan(P);
+        return pcuda(ctx, e, "plan workspace");
+    }
+    P->work_bytes = (int64_t)off;
+    uint8_t *W = static_cast<uint8_t *>(P->work);
+    P->prep = reinterpret_cast<PrepJob *>(W + o_prep);
+    P->merge = reinterpret_cast<MergeJob *>(W + o_merge);
+    P->g_lo = reinterpret_cast<int32_t *>(W + o_glo);
+    P->g_hi = reinterpret_cast<int32_t *>(W + o_ghi);
+    P->cta_gfirst = reinterpret_cast<int32_t *>(W + o_gf);
+    P->cta_units = reinterpret_cast<int64_t *>(W + o_cta);
+    P->partial = reinterpret_cast<uint64_t *>(W + o_part);
+
+    // Host tables.
+    std::vector<PrepJob> prep(n_prep);
+    std::vector<MergeJob> merge;
+    merge.reserve(P->n_queries);
+    {
+        std::vector<int64_t> fill(n_panels, 0);
+        std::vector<int64_t> prep_base(n_panels, 0);
+        for (int p = 1; p < n_panels; ++p) prep_base[p] = prep_base[p - 1] + rows_pad[p - 1];
+        for (int p = 0; p < n_panels; ++p)
+            for (int64_t r = 0; r < rows_pad[p]; ++r) {
+                PrepJob &j = prep[prep_base[p] + r];
+                j.src = nullptr;
+                j.mode = nullptr;
+                j.dst = W + o_a[p] + (size_t)r * dbs[p]->kpad;
+                j.qc = reinterpret_cast<float *>(W + o_qc[p]) + r;
+                j.n_words = dbs[p]->n_words64;
+                j.n_loci = dbs[p]->n_loci;
+                j.kpad = dbs[p]->kpad;
+                j.pad_ = 0;
+            }
+        for (int b = 0; b < n_batches; ++b) {
+            const fastid_batch &B = batches[b];
+            const int p = B.panel;
+            for (int64_t i = 0; i < B.n_q; ++i) {
+                const int64_t r = fill[p]++;
+                PrepJob &j = prep[prep_base[p] + r];
+                j.src = B.queries_dev + i * B.ld_q;
+                j.mode = B.modes_dev + i;
+                MergeJob m;
+                m.out_s = B.out_scores_dev + i * k;
+                m.out_i = B.out_idx_dev + i * k;
+                m.g = (int32_t)(tile_base[p] + r / TC_TILE_Q);
+                m.ql = (int32_t)(r % TC_TILE_Q);
+                merge.push_back(m);
+            }
+        }
+    }
+    P->n_jobs_prep = n_prep;
+    P->n_jobs_merge = (int64_t)merge.size();
+    e = cudaMemcpy(P->prep, prep.data(), prep.size() * sizeof(PrepJob), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !merge.empty())
+        e = cudaMemcpy(P->merge, merge.data(), merge.size() * sizeof(MergeJob), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_tiles > 0)
+        e = cudaMemcpy(P->g_lo, glo.data(), n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_tiles > 0)
+        e = cudaMemcpy(P->g_hi, ghi.data(), n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->cta_gfirst, gfirst.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->cta_units, cta.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_plan(P);
+        return pcuda(ctx, e, "plan tables");
+    }
+
+    // Launch description.
+    TcLaunch &L = P->launch;
+    memset(&L, 0, sizeof L);
+    L.n_panels = n_panels;
+    for (int p = 0; p < n_panels; ++p) {
+        e = make_operand_map(&L.map_a[p], W + o_a[p], rows_pad[p], dbs[p]->kpad, TC_TILE_Q);
+        if (e == cudaSuccess)
+            e = make_operand_map(&L.map_b[p], dbs[p]->fp8, dbs[p]->n_pad, dbs[p]->kpad, BN);
+        if (e != cudaSuccess) {
+            free_plan(P);
+            return pcuda(ctx, e, "tensor maps");
+        }
+        L.n_refs[p] = dbs[p]->n_refs;
+        L.n_q[p] = rows[p];
+        L.n_rt[p] = n_rt[p];
+        L.unit_base[p] = unit_base[p];
+        L.kpad[p] = dbs[p]->kpad;
+        L.tile_base[p] = (int32_t)tile_base[p];
+        L.qconst[p] = reinterpret_cast<const float *>(W + o_qc[p]);
+    }
+    L.n_units = U;
+    L.grid = (int32_t)G;
+    L.max_seg = max_seg;
+    L.cta_units = P->cta_units;
+    L.threshold = threshold;
+    L.k = k;
+    L.epi = EPI_TOPK;
+    L.partial = P->partial;
+    L.status = ctx->dev_status;
+    // Scores never exceed a panel's loci count; clamp so T + 1 stays exact in FP32.
+    if (threshold != 0xFFFFFFFFu) {
+        int32_t nmax = 0;
+        for (int p = 0; p < n_panels; ++p) nmax = std::max(nmax, dbs[p]->n_loci);
+        L.threshold = threshold > (uint32_t)nmax ? (uint32_t)nmax : threshold;
+    }
+    *out = P;
+    return FASTID_OK;
+}
+
+fastid_status fastid_plan_run(fastid_plan *plan, fastid_stream stream) {
+    if (!plan) return FASTID_EINVAL;
+    fastid_ctx *ctx = plan->ctx;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return pcuda(ctx, e, "cudaSetDevice");
+    if (plan->n_queries == 0) return FASTID_OK;
+    e = launch_prep_jobs(plan->prep, plan->n_jobs_prep, s);
+    if (e != cudaSuccess) return pcuda(ctx, e, "batched operand preparation");
+    e = launch_tensor_multi(plan->bn, plan->launch, s);
+    if (e != cudaSuccess) return pcuda(ctx, e, "batched compare launch");
+    e = launch_merge_jobs(plan->partial, plan->merge, plan->n_jobs_merge, plan->g_lo, plan->g_hi, plan->cta_gfirst,
+                          plan->launch.max_seg, TC_TILE_Q, plan->k, s);
+    if (e != cudaSuccess) return pcuda(ctx, e, "batched merge");
+    ctx->launches += 3;
+    return FASTID_OK;
+}
+
+fastid_status fastid_plan_capture(fastid_plan *plan, fastid_stream stream) {
+    if (!plan) return FASTID_EINVAL;
+    fastid_ctx *ctx = plan->ctx;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return pcuda(ctx, e, "cudaSetDevice");
+    if (plan->graph_exec) {
+        cudaGraphExecDestroy(plan->graph_exec);
+        plan->graph_exec = nullptr;
+    }
+    if (plan->graph) {
+        cudaGraphDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return pcuda(ctx, e, "capture stream");
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return pcuda(ctx, e, "begin capture");
+    }
+    const int64_t launches_before = ctx->launches;
+    fastid_status st = fastid_plan_run(plan, cs);
+    ctx->launches = launches_before;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (st != FASTID_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return pcuda(ctx, e, "end capture");
+    plan->graph = g;
+    e = cudaGraphInstantiate(&plan->graph_exec, g, 0);
+    if (e != cudaSuccess) return pcuda(ctx, e, "graph instantiate");
+    (void)stream;
+    return FASTID_OK;
+}
+
+fastid_status fastid_plan_replay(fastid_plan *plan, fastid_stream stream) {
+    if (!plan) return FASTID_EINVAL;
+    fastid_ctx *ctx = plan->ctx;
+    if (!plan->graph_exec) return perr(ctx, FASTID_EINVAL, "plan has no captured graph: call fastid_plan_capture");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaGraphLaunch(plan->graph_exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return pcuda(ctx, e, "graph launch");
+    if (plan->n_queries > 0) ctx->launches += 3;
+    return FASTID_OK;
+}
+
+fastid_status fastid_plan_info(const fastid_plan *plan, int64_t *n_queries, int64_t *n_units, int32_t *grid,
+                               int32_t *variant, int64_t *workspace_bytes) {
+    if (!plan) return FASTID_EINVAL;
+    if (n_queries) *n_queries = plan->n_queries;
+    if (n_units) *n_units = plan->launch.n_units;
+    if (grid) *grid = plan->launch.grid;
+    if (variant) *variant = plan->bn == 128 ? FASTID_VARIANT_TENSOR_N128 : FASTID_VARIANT_TENSOR_N256;
+    if (workspace_bytes) *workspace_bytes = plan->work_bytes;
+    return FASTID_OK;
+}
+
+fastid_status fastid_plan_destroy(fastid_plan *plan) {
+    if (!plan) return FASTID_OK;
+    cudaSetDevice(plan->ctx->device);
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return FASTID_OK;
+}
+
+}  // extern "C"

@@ -62,6 +62,28 @@ __global__ void topk_merge_kernel(const uint64_t *__restrict__ partial, Partitio
     }
 }
 
+// Batched form: one warp per job; segments of tile g are the CTAs
+// g_lo[g] .. g_hi[g], CTA c holding tile g as its (g - cta_gfirst[c])-th segment.
+__global__ void topk_merge_jobs_kernel(const uint64_t *__restrict__ partial, const MergeJob *__restrict__ jobs,
+                                       int64_t n_jobs, const int32_t *__restrict__ g_lo,
+                                       const int32_t *__restrict__ g_hi, const int32_t *__restrict__ cta_gfirst,
+                                       int32_t max_seg, int32_t tile_q, int32_t k) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n_jobs) return;
+    const MergeJob jb = jobs[j];
+    uint64_t acc = KEY_EMPTY;
+    for (int32_t c = g_lo[jb.g]; c <= g_hi[jb.g]; ++c) {
+        const int64_t slot = (int64_t)c * max_seg + (jb.g - cta_gfirst[c]);
+        uint64_t b = lane < k ? partial[(slot * tile_q + jb.ql) * k + lane] : KEY_EMPTY;
+        acc = warp_merge32(acc, b, lane);
+    }
+    if (lane < k) {
+        jb.out_s[lane] = acc == KEY_EMPTY ? 0xFFFFFFFFu : (uint32_t)(acc >> 32);
+        jb.out_i[lane] = acc == KEY_EMPTY ? -1ll : (int64_t)(uint32_t)acc;
+    }
+}
+
 // ---- hit list finish ----------------------------------------------------
 // sort_tmp layout: [0] = live count n (as u64), [1] = next power of two of n,
 // then keys[P], then vals (u32)[P].
@@ -209,6 +231,17 @@ cudaError_t launch_topk_merge_tile(const uint64_t *partial, const Partition &par
     const int wpb = 8;
     int64_t blocks = (n_q + wpb - 1) / wpb;
     topk_merge_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, part, tile_q, n_q, k, out_scores, out_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_jobs(const uint64_t *partial, const MergeJob *jobs, int64_t n_jobs, const int32_t *g_lo,
+                              const int32_t *g_hi, const int32_t *cta_gfirst, int32_t max_seg, int32_t tile_q,
+                              int32_t k, cudaStream_t s) {
+    if (n_jobs == 0) return cudaSuccess;
+    const int wpb = 8;
+    int64_t blocks = (n_jobs + wpb - 1) / wpb;
+    topk_merge_jobs_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, jobs, n_jobs, g_lo, g_hi, cta_gfirst,
+                                                                 max_seg, tile_q, k);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,8 @@
 // drains and exits.
 #include <cuda.h>
 
+#include <cstring>
+
 #include "common.cuh"
 
 namespace fastid {
@@ -32,32 +34,57 @@ namespace fastid {
 namespace {
 
 constexpr int TC_BM = 128;            // queries per tile
-constexpr int TC_BN = 256;            // references per tile
 constexpr int TC_BK = 128;            // loci (bytes) per stage
-constexpr int TC_STAGES = 3;
 constexpr int TC_THREADS = 192;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK;  // 16 KB
-constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK;  // 32 KB
-constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint64_t WAIT_NS = 2000000000ull;     // 2 s per wait
 
-struct TensorArgs {
+// Kernel variants: references per tile (the MMA's N) and pipeline depth.
+//   BN = 256: 32 KB reference stage, 3 stages, 2 x 256 TMEM columns
+//   BN = 128: 16 KB reference stage, 5 stages, 2 x 128 TMEM columns
+template <int BN>
+struct TcShape {
+    static constexpr int STAGES = BN == 256 ? 3 : 5;
+    static constexpr uint32_t B_BYTES = (uint32_t)BN * TC_BK;
+    static constexpr uint32_t TMEM_COLS = BN == 256 ? 512 : 256;
+};
+
+// One database ("panel") of a launch.  A launch walks the global list of
+// units (panel, query tile, reference tile), panel-major, then query-tile
+// major; panel p's units start at unit_base.
+struct PanelDesc {
     int64_t n_refs;
-    int64_t n_q;
-    int32_t n_kb;  // K stages
-    const float *qconst;  // c_q per padded query
-    uint32_t threshold;   // already clamped to <= N
+    int64_t n_q;          // real query rows (the operand is padded to 128)
+    int64_t n_rt;         // reference tiles
+    int64_t unit_base;
+    int32_t n_kb;         // K stages of 128 loci
+    int32_t tile_base;    // global id of the panel's first query tile
+    const float *qconst;  // c_q per padded query row
+};
+
+struct TcMaps {
+    CUtensorMap a[TC_MAXP];  // query operand of each panel (boxes 128 loci x 128 queries)
+    CUtensorMap b[TC_MAXP];  // reference operand of each panel (boxes 128 loci x BN refs)
+};
+
+struct TensorArgs {
+    int32_t n_panels;
+    PanelDesc panel[TC_MAXP];
+    int64_t n_units;
+    int32_t grid;
+    int32_t max_seg;
+    const int64_t *cta_units;  // [grid + 1] unit ranges, or null: CTA c takes [c U / G, (c+1) U / G)
+    uint32_t threshold;        // already clamped to <= N
     int32_t k;
     int32_t epi;
-    void *out;
+    void *out;  // EPI_SCORES*: panel 0's [n_q][ld_out]
     int64_t ld_out;
-    int64_t capacity;
+    int64_t capacity;  // EPI_HITS: panel 0
     int64_t *hit_q;
     int64_t *hit_r;
     uint32_t *hit_score;
     unsigned long long *hit_count;
-    uint64_t *partial;
-    Partition part;
+    uint64_t *partial;  // EPI_TOPK: [grid * max_seg][128][k]
     uint32_t *status;
 };
 
@@ -204,8 +231,8 @@ __device__ __forceinline__ void net_insert(int32_t (&ls)[TC_KMAX], uint32_t (&lr
 }
 
 struct TcSmem {
-    uint64_t full[TC_STAGES];
-    uint64_t empty[TC_STAGES];
+    uint64_t full[8];
+    uint64_t empty[8];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint64_t done;
@@ -236,30 +263,46 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, uint32
     }
 }
 
+__device__ __forceinline__ void decode_unit(const TensorArgs &a, int64_t u, int &p, int64_t &qt, int64_t &rt) {
+    p = 0;
+#pragma unroll 1
+    while (p + 1 < a.n_panels && u >= a.panel[p + 1].unit_base) ++p;
+    const int64_t local = u - a.panel[p].unit_base;
+    qt = local / a.panel[p].n_rt;
+    rt = local - qt * a.panel[p].n_rt;
+}
+
+template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tensor_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                  const TensorArgs args) {
+    tensor_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TensorArgs args) {
+    using S = TcShape<BN>;
     extern __shared__ uint8_t smem_raw[];
-    // 1024-byte aligned operand stages, then control block, then top-k lists.
+    // 1024-byte aligned operand stages, then control block, then staging.
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     uint8_t *base = smem_raw + pad;
     uint8_t *sA = base;
-    uint8_t *sB = base + TC_STAGES * TC_A_BYTES;
-    TcSmem *ctl = reinterpret_cast<TcSmem *>(base + TC_STAGES * (TC_A_BYTES + TC_B_BYTES));
+    uint8_t *sB = base + S::STAGES * TC_A_BYTES;
+    TcSmem *ctl = reinterpret_cast<TcSmem *>(base + S::STAGES * (TC_A_BYTES + S::B_BYTES));
     // per-thread staging of one 32-column chunk, [32][128] floats (rare path)
     float *stage_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(ctl) + 256);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const Partition &P = args.part;
     const int64_t c = blockIdx.x;
-    const int64_t u_begin = part_begin(P, c), u_end = part_begin(P, c + 1);
+    int64_t u_begin, u_end;
+    if (args.cta_units) {
+        u_begin = args.cta_units[c];
+        u_end = args.cta_units[c + 1];
+    } else {
+        u_begin = (c * args.n_units) / args.grid;
+        u_end = ((c + 1) * args.n_units) / args.grid;
+    }
     volatile int *abort_flag = &ctl->abort_flag;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < S::STAGES; ++s) {
             mbar_init(smem_u32(&ctl->full[s]), 1);
             mbar_init(smem_u32(&ctl->empty[s]), 1);
         }
@@ -274,7 +317,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&ctl->tmem_base)),
-                     "r"(TC_TMEM_COLS)
+                     "r"(S::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -286,23 +329,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
+            for (int p = 0; p < args.n_panels; ++p) {
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[p])) : "memory");
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[p])) : "memory");
+            }
             int stage = 0;
             uint32_t phase = 0;
             int64_t issued = 0;
             bool ok = true;
             for (int64_t u = u_begin; u < u_end && ok; ++u) {
-                const int64_t qt = u / P.n_rt, rt = u - qt * P.n_rt;
-                for (int kb = 0; kb < args.n_kb; ++kb) {
+                int p;
+                int64_t qt, rt;
+                decode_unit(args, u, p, qt, rt);
+                const int n_kb = args.panel[p].n_kb;
+                for (int kb = 0; kb < n_kb; ++kb) {
                     ok = mbar_wait(smem_u32(&ctl->empty[stage]), phase ^ 1u, abort_flag, args.status, 1);
                     if (!ok) break;
                     const uint32_t fb = smem_u32(&ctl->full[stage]);
-                    mbar_expect_tx(fb, TC_A_BYTES + TC_B_BYTES);
-                    tma_load_2d(smem_u32(sA + stage * TC_A_BYTES), &map_a, fb, kb * TC_BK, (int32_t)(qt * TC_BM));
-                    tma_load_2d(smem_u32(sB + stage * TC_B_BYTES), &map_b, fb, kb * TC_BK, (int32_t)(rt * TC_BN));
+                    mbar_expect_tx(fb, TC_A_BYTES + S::B_BYTES);
+                    tma_load_2d(smem_u32(sA + stage * TC_A_BYTES), &maps.a[p], fb, kb * TC_BK, (int32_t)(qt * TC_BM));
+                    tma_load_2d(smem_u32(sB + stage * S::B_BYTES), &maps.b[p], fb, kb * TC_BK, (int32_t)(rt * BN));
                     ++issued;
-                    if (++stage == TC_STAGES) {
+                    if (++stage == S::STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -310,34 +358,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             // Drain: the last fill of every stage has landed before the CTA
             // exits (fill n used stage n % S in phase (n / S) & 1).
-            for (int64_t n = issued - 1; n >= 0 && n >= issued - TC_STAGES; --n)
-                mbar_drain(smem_u32(&ctl->full[n % TC_STAGES]), (uint32_t)((n / TC_STAGES) & 1), args.status, 2);
+            for (int64_t n = issued - 1; n >= 0 && n >= issued - S::STAGES; --n)
+                mbar_drain(smem_u32(&ctl->full[n % S::STAGES]), (uint32_t)((n / S::STAGES) & 1), args.status, 2);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_f8(TC_BM, TC_BN);
+            constexpr uint32_t idesc = idesc_f8(TC_BM, BN);
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
             for (int64_t u = u_begin; u < u_end && ok; ++u) {
+                int p;
+                int64_t qt, rt;
+                decode_unit(args, u, p, qt, rt);
+                const int n_kb = args.panel[p].n_kb;
                 ok = mbar_wait(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, abort_flag, args.status, 3);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * TC_BN);
-                for (int kb = 0; kb < args.n_kb; ++kb) {
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+                for (int kb = 0; kb < n_kb; ++kb) {
                     ok = mbar_wait(smem_u32(&ctl->full[stage]), phase, abort_flag, args.status, 4);
                     if (!ok) break;
                     tc_fence_after();
                     const uint64_t ad = sw128_desc(smem_u32(sA + stage * TC_A_BYTES));
-                    const uint64_t bd = sw128_desc(smem_u32(sB + stage * TC_B_BYTES));
+                    const uint64_t bd = sw128_desc(smem_u32(sB + stage * S::B_BYTES));
 #pragma unroll
                     for (int kk = 0; kk < TC_BK / 32; ++kk)  // K = 32 FP8 per MMA: +32 bytes = +2 in the address field
                         tc_mma_f8(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
                     tc_commit(smem_u32(&ctl->empty[stage]));
-                    if (++stage == TC_STAGES) {
+                    if (++stage == S::STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -362,7 +414,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int k = args.k;
         int acc = 0;
         uint32_t acc_phase = 0;
-        int64_t qt_prev = -1;
+        int64_t g_prev = -1;  // global query-tile id of the current segment
         int seg = 0;
         int32_t ls[TC_KMAX];  // this thread's top-k scores (see net_insert)
         uint32_t lr[TC_KMAX]; // and their references
@@ -370,22 +422,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float cut = 0.f;   // D must be < cut to be a candidate
         float cut0 = 0.f;  // cut while the list is not full
         bool qvalid = false;
-        int64_t q = 0;
+        int64_t q = 0, n_refs = 0;
         for (int64_t u = u_begin; u < u_end; ++u) {
-            const int64_t qt = u / P.n_rt, rt = u - qt * P.n_rt;
-            if (qt != qt_prev) {
-                if (args.epi == EPI_TOPK && qt_prev >= 0) {
-                    uint64_t *dst = args.partial + ((c * P.max_seg + seg) * TC_BM + row) * (int64_t)k;
+            int p;
+            int64_t qt, rt;
+            decode_unit(args, u, p, qt, rt);
+            const int64_t g = args.panel[p].tile_base + qt;
+            if (g != g_prev) {
+                if (args.epi == EPI_TOPK && g_prev >= 0) {
+                    uint64_t *dst = args.partial + ((c * args.max_seg + seg) * TC_BM + row) * (int64_t)k;
 #pragma unroll
                     for (int i = 0; i < TC_KMAX; ++i)
                         if (i >= TC_KMAX - k)
                             dst[i - (TC_KMAX - k)] = ls[i] == NET_EMPTY ? KEY_EMPTY : make_key((uint32_t)ls[i], lr[i]);
                     ++seg;
                 }
-                qt_prev = qt;
+                g_prev = g;
                 q = qt * TC_BM + row;
-                qvalid = q < args.n_q;
-                cq = args.qconst[q];
+                qvalid = q < args.panel[p].n_q;
+                n_refs = args.panel[p].n_refs;
+                cq = args.panel[p].qconst[q];
 #pragma unroll
                 for (int i = 0; i < TC_KMAX; ++i) {
                     ls[i] = i < TC_KMAX - k ? NET_HOLD : NET_EMPTY;
@@ -398,14 +454,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             __syncwarp();
             if (!__all_sync(0xffffffffu, got)) break;
             tc_fence_after();
-            const int64_t r0 = rt * TC_BN;
-            const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * TC_BN);
+            const int64_t r0 = rt * BN;
+            const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * BN);
 #pragma unroll 1
-            for (int ch = 0; ch < TC_BN / 32; ++ch) {
+            for (int ch = 0; ch < BN / 32; ++ch) {
                 uint32_t v[32];
                 __syncwarp();  // tcgen05.ld is warp-collective: reconverge first
                 tmem_ld32(taddr + ch * 32, v);
-                if (ch == TC_BN / 32 - 1) {
+                if (ch == BN / 32 - 1) {
                     tc_fence_before();
                     mbar_arrive(smem_u32(&ctl->tempty[acc]));
                 }
@@ -415,7 +471,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const int64_t r = rc + j;
-                            if (r < args.n_refs) {
+                            if (r < n_refs) {
                                 const uint32_t sc = (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq);
                                 if (args.epi == EPI_SCORES16)
                                     reinterpret_cast<uint16_t *>(args.out)[q * args.ld_out + r] = (uint16_t)sc;
@@ -429,7 +485,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 uint32_t m = 0;  // columns of this chunk that pass the filter
 #pragma unroll
                 for (int j = 0; j < 32; ++j) m |= (uint32_t)(__uint_as_float(v[j]) < cut) << j;
-                if (rc + 32 > args.n_refs) m &= rc >= args.n_refs ? 0u : ((1u << (args.n_refs - rc)) - 1u);
+                if (rc + 32 > n_refs) m &= rc >= n_refs ? 0u : ((1u << (n_refs - rc)) - 1u);
                 if (!__any_sync(0xffffffffu, m != 0u)) continue;
                 if (args.epi == EPI_HITS) {
 #pragma unroll
@@ -463,8 +519,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 acc_phase ^= 1u;
             }
         }
-        if (args.epi == EPI_TOPK && qt_prev >= 0 && !*abort_flag) {
-            uint64_t *dst = args.partial + ((c * P.max_seg + seg) * TC_BM + row) * (int64_t)k;
+        if (args.epi == EPI_TOPK && g_prev >= 0 && !*abort_flag) {
+            uint64_t *dst = args.partial + ((c * args.max_seg + seg) * TC_BM + row) * (int64_t)k;
 #pragma unroll
             for (int i = 0; i < TC_KMAX; ++i)
                 if (i >= TC_KMAX - k)
@@ -476,7 +532,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(S::TMEM_COLS)
                      : "memory");
     }
 }
@@ -509,7 +565,40 @@ __global__ void refs_e4m3_kernel(const uint64_t *__restrict__ packed, int64_t ld
     }
 }
 
-// Query operand per mode (see the header comment) and c_q.  One warp per row.
+// Query operand per mode (see the header comment) and c_q for one row, by one
+// warp.  src == nullptr (a padding row) writes zeros.
+__device__ __forceinline__ void encode_query_row(const uint64_t *__restrict__ src, bool mis, int32_t n_words,
+                                                 int32_t n_loci, int32_t kpad, uint8_t *__restrict__ dst,
+                                                 float *__restrict__ qc, int lane) {
+    const bool valid = src != nullptr;
+    uint32_t pc = 0;
+    for (int32_t c = lane; c < kpad / 16; c += 32) {
+        const int32_t l0 = c * 16;
+        uint32_t bits = 0;
+        if (valid && (l0 >> 6) < n_words) bits = (uint32_t)(src[l0 >> 6] >> (l0 & 63)) & 0xFFFFu;
+        // loci < N inside this 16-locus group
+        const int32_t live = n_loci - l0;
+        const uint32_t in_n = !valid ? 0u : live >= 16 ? 0xFFFFu : live <= 0 ? 0u : ((1u << live) - 1u);
+        bits &= in_n;
+        pc += __popc(bits);
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t qb = (bits >> (4 * i)) & 0xFu;   // Q_l
+            const uint32_t nb = (in_n >> (4 * i)) & 0xFu;   // l < N
+            // mode 1: 1 - Q_l  -> +1 where l < N and Q_l = 0
+            // mode 0: 1 - 2Q_l -> +1 where Q_l = 0, -1 (0xB8 = 0x38 | 0x80) where Q_l = 1
+            const uint32_t plus = bits4_to_e4m3(nb & ~qb);
+            const uint32_t minus = mis ? (bits4_to_e4m3(qb) | (((qb * 0x00204081u) & 0x01010101u) * 0x80u)) : 0u;
+            w[i] = plus | minus;
+        }
+        reinterpret_cast<uint4 *>(dst)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, off);
+    if (lane == 0) *qc = mis ? (float)pc : 0.f;
+}
+
 __global__ void queries_e4m3_kernel(const uint64_t *__restrict__ q, int64_t ld_q, int64_t n_q, int32_t n_words,
                                     int32_t n_loci, const uint8_t *__restrict__ modes, int64_t n_q_pad,
                                     int32_t kpad, uint8_t *__restrict__ out, float *__restrict__ qconst) {
@@ -517,43 +606,26 @@ __global__ void queries_e4m3_kernel(const uint64_t *__restrict__ q, int64_t ld_q
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n_q_pad; r += warps_total) {
         const bool valid = r < n_q;
-        const bool mis = valid && modes[r] == FASTID_MODE_MISMATCH;
-        uint32_t pc = 0;
-        for (int32_t c = lane; c < kpad / 16; c += 32) {
-            const int32_t l0 = c * 16;
-            uint32_t bits = 0;
-            if (valid && (l0 >> 6) < n_words) bits = (uint32_t)(q[r * ld_q + (l0 >> 6)] >> (l0 & 63)) & 0xFFFFu;
-            // loci < N inside this 16-locus group
-            const int32_t live = n_loci - l0;
-            const uint32_t in_n = !valid ? 0u : live >= 16 ? 0xFFFFu : live <= 0 ? 0u : ((1u << live) - 1u);
-            bits &= in_n;
-            pc += __popc(bits);
-            uint4 o;
-            uint32_t w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t qb = (bits >> (4 * i)) & 0xFu;   // Q_l
-                const uint32_t nb = (in_n >> (4 * i)) & 0xFu;   // l < N
-                // mode 1: 1 - Q_l  -> +1 where l < N and Q_l = 0
-                // mode 0: 1 - 2Q_l -> +1 where Q_l = 0, -1 (0xB8 = 0x38 | 0x80) where Q_l = 1
-                uint32_t plus = bits4_to_e4m3(nb & ~qb);
-                uint32_t minus = mis ? (bits4_to_e4m3(qb) | (((qb * 0x00204081u) & 0x01010101u) * 0x80u)) : 0u;
-                w[i] = plus | minus;
-            }
-            o.x = w[0];
-            o.y = w[1];
-            o.z = w[2];
-            o.w = w[3];
-            reinterpret_cast<uint4 *>(out + r * (int64_t)kpad)[c] = o;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, off);
-        if (lane == 0) qconst[r] = mis ? (float)pc : 0.f;
+        encode_query_row(valid ? q + r * ld_q : nullptr, valid && modes[r] == FASTID_MODE_MISMATCH, n_words, n_loci,
+                         kpad, out + r * (int64_t)kpad, qconst + r, lane);
     }
 }
 
+// Batched form: one job per operand row of every panel.
+__global__ void prep_jobs_kernel(const PrepJob *__restrict__ jobs, int64_t n_jobs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_jobs; j += warps_total) {
+        const PrepJob jb = jobs[j];
+        const bool mis = jb.src != nullptr && *jb.mode == FASTID_MODE_MISMATCH;
+        encode_query_row(jb.src, mis, jb.n_words, jb.n_loci, jb.kpad, jb.dst, jb.qc, lane);
+    }
+}
+
+template <int BN>
 size_t tensor_smem(int epi) {
-    size_t s = 1024 + TC_STAGES * (size_t)(TC_A_BYTES + TC_B_BYTES) + 256;
+    using S = TcShape<BN>;
+    size_t s = 1024 + S::STAGES * (size_t)(TC_A_BYTES + S::B_BYTES) + 256;
     if (epi == EPI_TOPK) s += (size_t)32 * TC_BM * sizeof(float);
     return s;
 }
@@ -593,7 +665,7 @@ cudaError_t make_operand_map(CUtensorMap *map, const uint8_t *base, int64_t rows
 }
 
 int tensor_tile_q() { return TC_BM; }
-int tensor_tile_r() { return TC_BN; }
+int tensor_tile_r() { return 256; }
 int tensor_kpad(int32_t n_loci) { return (n_loci + TC_BK - 1) / TC_BK * TC_BK; }
 
 cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_rows, int32_t kpad, uint8_t *out,
@@ -615,10 +687,67 @@ cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, in
     return cudaGetLastError();
 }
 
+cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s) {
+    if (n_jobs == 0) return cudaSuccess;
+    int64_t blocks = (n_jobs + 7) / 8;
+    if (blocks > 65535) blocks = 65535;
+    prep_jobs_kernel<<<(unsigned)blocks, 256, 0, s>>>(jobs, n_jobs);
+    return cudaGetLastError();
+}
+
 int tensor_grid_target(int device) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     return sms;
+}
+
+cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
+    TcMaps maps;
+    TensorArgs a;
+    memset(&maps, 0, sizeof maps);
+    memset(&a, 0, sizeof a);
+    if (L.n_panels < 1 || L.n_panels > TC_MAXP) return cudaErrorInvalidValue;
+    a.n_panels = L.n_panels;
+    for (int p = 0; p < L.n_panels; ++p) {
+        maps.a[p] = L.map_a[p];
+        maps.b[p] = L.map_b[p];
+        a.panel[p].n_refs = L.n_refs[p];
+        a.panel[p].n_q = L.n_q[p];
+        a.panel[p].n_rt = L.n_rt[p];
+        a.panel[p].unit_base = L.unit_base[p];
+        a.panel[p].n_kb = L.kpad[p] / TC_BK;
+        a.panel[p].tile_base = L.tile_base[p];
+        a.panel[p].qconst = L.qconst[p];
+    }
+    a.n_units = L.n_units;
+    a.grid = L.grid;
+    a.max_seg = L.max_seg;
+    a.cta_units = L.cta_units;
+    a.threshold = L.threshold;
+    a.k = L.k;
+    a.epi = L.epi;
+    a.out = L.out;
+    a.ld_out = L.ld_out;
+    a.capacity = L.capacity;
+    a.hit_q = L.hit_q;
+    a.hit_r = L.hit_r;
+    a.hit_score = L.hit_score;
+    a.hit_count = L.hit_count;
+    a.partial = L.partial;
+    a.status = L.status;
+    cudaError_t e;
+    if (bn == 128) {
+        size_t smem = tensor_smem<128>(L.epi);
+        e = cudaFuncSetAttribute(tensor_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        tensor_kernel<128><<<L.grid, TC_THREADS, smem, s>>>(maps, a);
+    } else {
+        size_t smem = tensor_smem<256>(L.epi);
+        e = cudaFuncSetAttribute(tensor_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        tensor_kernel<256><<<L.grid, TC_THREADS, smem, s>>>(maps, a);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tensor(int epi, const CUtensorMap &map_a, const CUtensorMap &map_b, int64_t n_refs, int64_t n_q,
@@ -626,29 +755,35 @@ cudaError_t launch_tensor(int epi, const CUtensorMap &map_a, const CUtensorMap &
                           int64_t ld_out, int64_t capacity, int64_t *hit_q, int64_t *hit_r, uint32_t *hit_score,
                           unsigned long long *hit_count, uint64_t *partial, const Partition &part, uint32_t *status,
                           cudaStream_t s) {
-    TensorArgs a;
-    a.n_refs = n_refs;
-    a.n_q = n_q;
-    a.n_kb = kpad / TC_BK;
-    a.qconst = qconst;
-    a.threshold = threshold;
-    a.k = k;
-    a.epi = epi;
-    a.out = out;
-    a.ld_out = ld_out;
-    a.capacity = capacity;
-    a.hit_q = hit_q;
-    a.hit_r = hit_r;
-    a.hit_score = hit_score;
-    a.hit_count = hit_count;
-    a.partial = partial;
-    a.part = part;
-    a.status = status;
-    size_t smem = tensor_smem(epi);
-    cudaError_t e = cudaFuncSetAttribute(tensor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    tensor_kernel<<<part.grid, TC_THREADS, smem, s>>>(map_a, map_b, a);
-    return cudaGetLastError();
+    TcLaunch L;
+    memset(&L, 0, sizeof L);
+    L.n_panels = 1;
+    L.map_a[0] = map_a;
+    L.map_b[0] = map_b;
+    L.n_refs[0] = n_refs;
+    L.n_q[0] = n_q;
+    L.n_rt[0] = part.n_rt;
+    L.unit_base[0] = 0;
+    L.kpad[0] = kpad;
+    L.tile_base[0] = 0;
+    L.qconst[0] = qconst;
+    L.n_units = part.n_units;
+    L.grid = part.grid;
+    L.max_seg = part.max_seg;
+    L.cta_units = nullptr;
+    L.threshold = threshold;
+    L.k = k;
+    L.epi = epi;
+    L.out = out;
+    L.ld_out = ld_out;
+    L.capacity = capacity;
+    L.hit_q = hit_q;
+    L.hit_r = hit_r;
+    L.hit_score = hit_score;
+    L.hit_count = hit_count;
+    L.partial = partial;
+    L.status = status;
+    return launch_tensor_multi(256, L, s);
 }
 
 }  // namespace fastid
