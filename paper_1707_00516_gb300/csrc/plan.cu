@@ -142,6 +142,17 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     }
     cta[0] = 0;
     cta[G] = U;
+    // Drop empty ranges (a costly panel can leave some): every launched CTA
+    // then holds at least one unit, and the CTAs covering a query tile are
+    // consecutive, which the merge relies on.
+    {
+        std::vector<int64_t> packed_cta;
+        for (int64_t c = 0; c < G; ++c)
+            if (cta[c + 1] > cta[c]) packed_cta.push_back(cta[c]);
+        packed_cta.push_back(U);
+        cta.swap(packed_cta);
+        G = (int64_t)cta.size() - 1;
+    }
     auto tile_of = [&](int64_t u) -> int64_t {
         int p = 0;
         while (p + 1 < n_panels && unit_base[p + 1] <= u) ++p;
