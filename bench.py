@@ -50,6 +50,10 @@ WORKLOADS = {
                k=16, threshold=0xFFFFFFFF, cfg=2),
     "c1": dict(workload="64q_x_10k_refs_N1024_top32", n_q=64, n_refs=10_000, n_loci=1024,
                k=32, threshold=0xFFFFFFFF, cfg=1),
+    "c4": dict(workload="256_batches_1-512q_panels_N512-2048-8192-16384_x_4M_refs_top16", n_refs=4_000_000,
+               panels=(512, 2048, 8192, 16384), n_batches=256, k=16, threshold=0xFFFFFFFF, cfg=4),
+    "c5": dict(workload="serving_poisson200bps_1-256q_N2048_x_20M_refs_top16", n_refs=20_000_000, n_loci=2048,
+               rate=200.0, k=16, threshold=0xFFFFFFFF, cfg=5),
 }
 
 METRIC = "query x reference comparisons/s at N loci, bit-exact"
@@ -433,6 +437,194 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+def device_queries(s, seed: int, recipe, thr_dev, n_loci: int):
+    """Packed queries of a recipe built on the device: contributor alleles from
+    gen/gen_gpu.cu, then fastid_pack and fastid_mix."""
+    import torch
+    dev = s.device
+    n_src = recipe.n_sources
+    src = torch.empty((max(n_src, 1), n_loci), dtype=torch.uint8, device=dev)
+    for stream in (gen.STREAM_DB, gen.STREAM_FRESH):
+        sel = np.nonzero(recipe.src_stream == stream)[0]
+        if sel.size == 0:
+            continue
+        rows = torch.from_numpy(recipe.src_row[sel].astype(np.int64)).to(dev)
+        tmp = torch.empty((sel.size, n_loci), dtype=torch.uint8, device=dev)
+        gen.allele_rows_device(seed, stream, thr_dev, tmp, rows_dev=rows)
+        src[torch.from_numpy(sel).to(dev)] = tmp
+    q = s.build_queries(src[:n_src], torch.from_numpy(recipe.offsets).to(dev), n_loci).clone()
+    return q, torch.from_numpy(recipe.modes).to(dev)
+
+
+def _c4_batches(w):
+    seed = gen.config_seed(w["cfg"])
+    sizes = gen.log_uniform_sizes(w["n_batches"], 1, 512, seed, salt=0xC4)
+    rng = np.random.default_rng([seed, 0xC44])
+    panels = rng.integers(0, len(w["panels"]), w["n_batches"])
+    return seed, sizes, panels
+
+
+def _c4_recipe(w, b, n, p, seed):
+    n_loci = w["panels"][p]
+    rec = gen.recipe_mixtures(int(n), w["n_refs"], n_loci, seed + 10 * p, 1, 4, fresh_base=(b + 1) << 24,
+                              salt=0xB000 + b)
+    rec.modes = np.where(np.diff(rec.offsets) == 1, gen.MODE_MISMATCH, gen.MODE_UNEXPLAINED).astype(np.uint8)
+    return rec
+
+
+def run_c4(args, w):
+    """Batched uneven workload: 256 batches over 4 loci panels in one
+    persistent launch (graph replay), variant from the autotuner."""
+    import torch
+    from paper_1707_00516_gb300 import binding as B
+    from paper_1707_00516_gb300.batched import BatchedSearch
+    from paper_1707_00516_gb300.build import build
+    from paper_1707_00516_gb300.search import Searcher
+    from paper_1707_00516_gb300.tune import Autotuner
+    gen.build_gpu()
+    build()
+    dev = torch.device("cuda", 0)
+    s = Searcher(0, B.FORM_TENSOR)
+    seed, sizes, panels = _c4_batches(w)
+    dbs, thrs = [], []
+    for p, n_loci in enumerate(w["panels"]):
+        db, thr = build_db(s, seed + 10 * p, w["n_refs"], n_loci, B.REFS_TENSOR, chunk=(1 << 28) // n_loci)
+        dbs.append(db)
+        thrs.append(torch.from_numpy(thr.view(np.int32)).to(dev))
+    tuner = Autotuner()
+    bs = BatchedSearch(s.ctx, dbs, panels, sizes, w["k"], w["threshold"], tuner=tuner)
+    host_q, host_m = [], []
+    for b, (n, p) in enumerate(zip(sizes, panels)):
+        rec = _c4_recipe(w, b, n, p, seed)
+        q, m = device_queries(s, seed + 10 * p, rec, thrs[p], w["panels"][p])
+        bs.set_queries(b, q, m)
+        host_q.append(q.cpu().numpy().view(np.uint64))
+        host_m.append(m.cpu().numpy())
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        bs.run_device()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clk = ClockSampler(0)
+    clk.start()
+    ev[0].record()
+    for i in range(args.steps):
+        bs.run_device()
+        ev[i + 1].record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    st = B.fastid_sync_status(s.ctx)
+    if st != B.OK:
+        raise RuntimeError(f"device status {st}")
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    pairs = int(sum(int(n) * w["n_refs"] for n in sizes))
+    flops = float(sum(2.0 * int(n) * w["n_refs"] * w["panels"][p] for n, p in zip(sizes, panels)))
+    value = pairs * args.steps / (total_ms / 1e3)
+    peaks, peak_src = load_peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    achieved = flops * args.steps / (total_ms / 1e3) / 1e12
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, h2d, d2h = bs.run_host(host_q, host_m)
+    e2e_s = time.perf_counter() - t0
+    info = bs.plan.info()
+    line = {"metric": METRIC + " (mixed-N panels); p50/p99 batch latency", "value": value, "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3xe4m3->f32",
+            "data": "synthetic",
+            "config": {"workload": w["workload"], "n_batches": int(len(sizes)), "n_queries": int(sum(sizes)),
+                       "panels": list(w["panels"]), "n_refs_per_panel": w["n_refs"], "k": w["k"],
+                       "variant": int(bs.variant), "autotune_ms": {str(k): v for k, v in tuner.last_timings.items()},
+                       "grid": info["grid"], "units": info["n_units"], "launch": "one persistent launch per step, "
+                       "CUDA graph replay (prep + compare + merge)"},
+            "batch_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "e2e": {"value": pairs * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": 3 * args.steps,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16 * FP8_OVER_BF16, "unit": "TFLOP/s",
+                         "frac": achieved / (bf16 * FP8_OVER_BF16), "traffic": None,
+                         "kernel": "tensor_kernel over 4 panels (whole graph time incl. prep and merge)",
+                         "peak_source": f"bf16 dense burst {bf16:.1f} TFLOP/s ({peak_src}) x {FP8_OVER_BF16:g}"},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    bs.close()
+    for d in dbs:
+        d.close()
+    s.ctx.close()
+
+
+def run_c5(args, w):
+    """Serving: Poisson arrivals of query batches against a resident 20M
+    database, continuous batching, p50/p99 request latency."""
+    import torch
+    from paper_1707_00516_gb300 import binding as B
+    from paper_1707_00516_gb300.build import build
+    from paper_1707_00516_gb300.search import Searcher
+    from paper_1707_00516_gb300.serve import Server
+    gen.build_gpu()
+    build()
+    dev = torch.device("cuda", 0)
+    s = Searcher(0, B.FORM_TENSOR)
+    seed = gen.config_seed(w["cfg"])
+    n_refs, n_loci, k = w["n_refs"], w["n_loci"], w["k"]
+    db, thr = build_db(s, seed, n_refs, n_loci, B.REFS_TENSOR)
+    thr_dev = torch.from_numpy(thr.view(np.int32)).to(dev)
+    rng = np.random.default_rng([seed, 0xC5])
+    horizon = args.warmup_seconds + args.seconds
+    n_req = int(w["rate"] * horizon * 1.2) + 16
+    gaps = rng.exponential(1.0 / w["rate"], n_req)
+    arrivals = np.cumsum(gaps)
+    n_req = int(np.searchsorted(arrivals, horizon))
+    arrivals = arrivals[:n_req]
+    sizes = gen.log_uniform_sizes(n_req, 1, 256, seed, salt=0xC55)
+    total = int(sizes.sum())
+    rec = gen.recipe_mixtures(total, n_refs, n_loci, seed, 1, 5, salt=0xC555)
+    rec.modes = np.where(np.diff(rec.offsets) == 1, gen.MODE_MISMATCH, gen.MODE_UNEXPLAINED).astype(np.uint8)
+    q, m = device_queries(s, seed, rec, thr_dev, n_loci)
+    hq = q.cpu().numpy().view(np.uint64)
+    hm = m.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    srv = Server(s.ctx, db, k, w["threshold"], hbm_budget_bytes=args.hbm_budget, max_wave=args.max_wave,
+                 max_slots=3)
+    futs, t_sub = [], []
+    t_start = time.perf_counter()
+    clk = ClockSampler(0)
+    clk.start()
+    for i in range(n_req):
+        delay = t_start + arrivals[i] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        futs.append(srv.submit(hq[offs[i]:offs[i + 1]], hm[offs[i]:offs[i + 1]]))
+    for f in futs:
+        f.result(timeout=600)
+    t_end = time.perf_counter()
+    clocks = clk.stop()
+    st = srv.stats()
+    # measured window: requests that arrived after the warm-up
+    meas = arrivals >= args.warmup_seconds
+    lat = np.array([l for (ts, l) in srv.records if ts - t_start >= args.warmup_seconds])
+    srv.close()
+    served = int(sizes[meas].sum()) * n_refs
+    window = (t_end - t_start) - args.warmup_seconds
+    line = {"metric": METRIC + "; p50/p99 request latency", "value": served / window, "unit": UNIT,
+            "n_gpus": 1, "steps": int(meas.sum()), "warmup": int((~meas).sum()),
+            "ms_per_step": 1e3 * window / max(1, int(meas.sum())), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "e4m3xe4m3->f32", "data": "synthetic",
+            "config": {"workload": w["workload"], "seconds": args.seconds, "requests": n_req,
+                       "queries": total, "offered_comparisons_per_s": float(total * n_refs / horizon),
+                       "slots": st["slots"], "waves": st["waves"], "mean_wave_queries": st["mean_wave"],
+                       "max_wave": args.max_wave, "hbm_budget_bytes": args.hbm_budget},
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                           "max": float(lat.max() * 1e3)},
+            "e2e": {"value": served / window, "unit": UNIT, "h2d_bytes_per_step": int(hq.nbytes / n_req),
+                    "d2h_bytes_per_step": int(12 * k * total / n_req)},
+            "gpu_launches": None, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    db.close()
+    s.ctx.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -440,10 +632,16 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", choices=["plain", "tensor", "both"], default="both")
-    ap.add_argument("--config", choices=sorted(WORKLOADS), default="c3")
+    ap.add_argument("--config", choices=sorted(WORKLOADS), default="c3",
+                    help="c3 (default): the headline 2048 x 20M workload; c4 batched panels; c5 serving")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--refs", type=int, default=None,
                     help="override the number of references (smaller captures for profiling)")
+    ap.add_argument("--seconds", type=float, default=30.0, help="c5: measured serving time")
+    ap.add_argument("--warmup-seconds", type=float, default=3.0, help="c5: warm-up serving time")
+    ap.add_argument("--max-wave", type=int, default=4096, help="c5: queries per wave")
+    ap.add_argument("--hbm-budget", type=int, default=4 << 30, help="c5: bytes of HBM for in-flight waves")
+
     args = ap.parse_args(argv)
     w = dict(WORKLOADS[args.config])
     if args.refs:
@@ -451,6 +649,10 @@ def main(argv=None):
         w["workload"] = w["workload"].replace("20M", f"{args.refs}").replace("1M", f"{args.refs}")
     if args.impl == "reference":
         run_reference(args, w)
+    elif args.config == "c4":
+        run_c4(args, w)
+    elif args.config == "c5":
+        run_c5(args, w)
     else:
         run_gpu(args, w)
 

@@ -83,6 +83,7 @@ class Server:
         self._inflight: queue.Queue = queue.Queue()
         self._stop = False
         self.latencies: list[float] = []
+        self.records: list[tuple[float, float]] = []  # (submit time, latency) per request
         self.waves = 0
         self.queries = 0
         self.wave_sizes: list[int] = []
@@ -179,6 +180,7 @@ class Server:
             for r in wave:
                 r.future.set_result((sc[o:o + r.n].copy(), ix[o:o + r.n].copy()))
                 self.latencies.append(now - r.t_submit)
+                self.records.append((r.t_submit, now - r.t_submit))
                 o += r.n
             self.waves += 1
             self.queries += n
