@@ -458,9 +458,9 @@ def device_queries(s, seed: int, recipe, thr_dev, n_loci: int):
 
 def _c4_batches(w):
     seed = gen.config_seed(w["cfg"])
-    sizes = gen.log_uniform_sizes(w["n_batches"], 1, 512, seed, salt=0xC4)
+    sizes = [int(x) for x in gen.log_uniform_sizes(w["n_batches"], 1, 512, seed, salt=0xC4)]
     rng = np.random.default_rng([seed, 0xC44])
-    panels = rng.integers(0, len(w["panels"]), w["n_batches"])
+    panels = [int(x) for x in rng.integers(0, len(w["panels"]), w["n_batches"])]
     return seed, sizes, panels
 
 
@@ -495,6 +495,7 @@ def run_c4(args, w):
     bs = BatchedSearch(s.ctx, dbs, panels, sizes, w["k"], w["threshold"], tuner=tuner)
     host_q, host_m = [], []
     for b, (n, p) in enumerate(zip(sizes, panels)):
+        n, p = int(n), int(p)
         rec = _c4_recipe(w, b, n, p, seed)
         q, m = device_queries(s, seed + 10 * p, rec, thrs[p], w["panels"][p])
         bs.set_queries(b, q, m)

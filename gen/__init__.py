@@ -298,7 +298,7 @@ def allele_rows_device(seed: int, stream: int, thr_dev, out_dev, rows_dev=None, 
     n_rows = out_dev.shape[0]
     n_loci = thr_dev.shape[0]
     st = torch.cuda.current_stream() if cuda_stream is None else cuda_stream
-    err = _gpu().gen_alleles(seed & MASK64, stream, rows_dev.data_ptr() if rows_dev is not None else None,
+    err = _gpu().gen_alleles(int(seed) & MASK64, int(stream), rows_dev.data_ptr() if rows_dev is not None else None,
                              row0, n_rows, thr_dev.data_ptr(), n_loci, out_dev.data_ptr(),
                              out_dev.stride(0), st.cuda_stream or None)
     if err != 0:
