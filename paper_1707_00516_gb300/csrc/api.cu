@@ -187,6 +187,7 @@ fastid_status fastid_create(fastid_ctx **out, int32_t device) {
     ctx->grid_hits = plain_grid_target(EPI_HITS, device);
     ctx->grid_scores = plain_grid_target(EPI_SCORES32, device);
     ctx->grid_tensor = tensor_grid_target(device);
+    ctx->pair_clusters = tensor_pair_clusters(device);
     *out = ctx;
     return FASTID_OK;
 }
@@ -334,6 +335,8 @@ fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int6
         e = cudaMalloc(&db->fp8, fbytes);
         if (e == cudaSuccess) e = launch_refs_e4m3(db->packed, db->ld64, db->n_pad, db->kpad, db->fp8, (cudaStream_t)stream);
         if (e == cudaSuccess) e = make_operand_map(&db->map_b, db->fp8, db->n_pad, db->kpad, tensor_tile_r());
+        if (e == cudaSuccess)
+            e = make_operand_map(&db->map_b_half, db->fp8, db->n_pad, db->kpad, tensor_tile_r() / 2);
         if (e != cudaSuccess) {
             cudaGetLastError();
             cudaStreamSynchronize((cudaStream_t)stream);
@@ -415,15 +418,24 @@ fastid_status pick_form(fastid_ctx *ctx, const fastid_refdb *db, int *tensor) {
 struct TensorPrep {
     CUtensorMap map_a;
     float *qconst;
-    Partition part;
+    Partition part;  // over work groups: CTAs, or 2-CTA clusters when paired
+    int pair;
 };
+
+// Paired launches (2-CTA clusters sharing reference stages) once there are
+// enough query tiles that padding to an even count costs little.
+constexpr int PAIR_MIN_TILES = 4;
 
 fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q, int64_t ld_q, int64_t n_q,
                              const uint8_t *modes, cudaStream_t s, Scratch &scr, size_t (*extra_fn)(const Partition &, void *),
                              void *extra_arg, size_t *extra_off, TensorPrep *tp) {
-    const int64_t n_q_pad = round_up(n_q, tensor_tile_q());
-    tp->part = make_partition((int32_t)(n_q_pad / tensor_tile_q()), db->n_pad / tensor_tile_r(), ctx->grid_tensor);
-    const size_t extra = extra_fn ? extra_fn(tp->part, extra_arg) : 0;
+    const int64_t n_qt = round_up(n_q, tensor_tile_q()) / tensor_tile_q();
+    tp->pair = (ctx->pair_clusters > 0 && n_qt >= PAIR_MIN_TILES) ? 1 : 0;
+    const int64_t n_q_pad = round_up(n_q, (int64_t)tensor_tile_q() * (tp->pair ? 2 : 1));
+    const int64_t groups = n_q_pad / tensor_tile_q() / (tp->pair ? 2 : 1);
+    tp->part = make_partition((int32_t)groups, db->n_pad / tensor_tile_r(),
+                              tp->pair ? ctx->pair_clusters : ctx->grid_tensor);
+    const size_t extra = extra_fn ? extra_fn(tp->part, extra_arg) * (tp->pair ? 2 : 1) : 0;
     Carver cv;
     size_t o_a = cv.take<uint8_t>((size_t)n_q_pad * db->kpad);
     size_t o_c = cv.take<float>((size_t)n_q_pad);
@@ -477,7 +489,8 @@ fastid_status fastid_scores(fastid_ctx *ctx, const fastid_refdb *db, const uint6
         if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, nullptr, nullptr, &xo, &tp)))
             return st;
         MainTimer tm(ctx, s);
-        FASTID_CUDA(ctx, launch_tensor(out_bytes == 2 ? EPI_SCORES16 : EPI_SCORES32, tp.map_a, db->map_b, db->n_refs,
+        FASTID_CUDA(ctx, launch_tensor(out_bytes == 2 ? EPI_SCORES16 : EPI_SCORES32, tp.pair, tp.map_a,
+                                       tp.pair ? db->map_b_half : db->map_b, db->n_refs,
                                        n_q, db->kpad, tp.qconst, 0xFFFFFFFFu, 1, out_dev, ld_out, 0, nullptr,
                                        nullptr, nullptr, nullptr, nullptr, tp.part, ctx->dev_status, s));
         tm.done();
@@ -518,11 +531,12 @@ fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_
             return st;
         uint64_t *partial = at<uint64_t>(scr.p, xo);
         MainTimer tm(ctx, s);
-        FASTID_CUDA(ctx, launch_tensor(EPI_TOPK, tp.map_a, db->map_b, db->n_refs, n_q, db->kpad, tp.qconst,
+        FASTID_CUDA(ctx, launch_tensor(EPI_TOPK, tp.pair, tp.map_a, tp.pair ? db->map_b_half : db->map_b, db->n_refs,
+                                       n_q, db->kpad, tp.qconst,
                                        clamp_threshold(threshold, db->n_loci), k, nullptr, 0, 0, nullptr, nullptr,
                                        nullptr, nullptr, partial, tp.part, ctx->dev_status, s));
         tm.done();
-        FASTID_CUDA(ctx, launch_topk_merge_tile(partial, tp.part, tensor_tile_q(), n_q, k, out_scores_dev,
+        FASTID_CUDA(ctx, launch_topk_merge_tile(partial, tp.part, tensor_tile_q(), tp.pair, n_q, k, out_scores_dev,
                                                 out_idx_dev, s));
         count_launches(ctx, 2);
         return FASTID_OK;
@@ -573,7 +587,8 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
         uint64_t *sort_tmp = at<uint64_t>(scr.p, xo + 256);
         FASTID_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
         MainTimer tm(ctx, s);
-        FASTID_CUDA(ctx, launch_tensor(EPI_HITS, tp.map_a, db->map_b, db->n_refs, n_q, db->kpad, tp.qconst,
+        FASTID_CUDA(ctx, launch_tensor(EPI_HITS, tp.pair, tp.map_a, tp.pair ? db->map_b_half : db->map_b, db->n_refs,
+                                       n_q, db->kpad, tp.qconst,
                                        clamp_threshold(threshold, db->n_loci), 1, nullptr, 0, capacity, hit_q_dev,
                                        hit_r_dev, hit_score_dev, count, nullptr, tp.part, ctx->dev_status, s));
         tm.done();

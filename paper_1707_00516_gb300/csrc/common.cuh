@@ -91,6 +91,7 @@ struct MergeJob {
 // Host-side description of one tensor-form launch over up to TC_MAXP panels.
 struct TcLaunch {
     int32_t n_panels;
+    int32_t pair;  // 2-CTA clusters sharing reference stages; grid and units count clusters and pair-units
     CUtensorMap map_a[TC_MAXP];
     CUtensorMap map_b[TC_MAXP];
     int64_t n_refs[TC_MAXP];
@@ -156,7 +157,7 @@ cudaError_t launch_plain(int epi, const uint32_t *refs32, const uint32_t *ref_no
 int plain_grid_target(int epi, int device);
 cudaError_t launch_topk_merge(const uint64_t *partial, const Partition &part, int64_t n_q,
                               int32_t k, uint32_t *out_scores, int64_t *out_idx, cudaStream_t s);
-cudaError_t launch_topk_merge_tile(const uint64_t *partial, const Partition &part, int32_t tile_q,
+cudaError_t launch_topk_merge_tile(const uint64_t *partial, const Partition &part, int32_t tile_q, int32_t pair,
                                    int64_t n_q, int32_t k, uint32_t *out_scores, int64_t *out_idx, cudaStream_t s);
 int64_t hits_sort_elems(int64_t capacity);
 // tensor form (tensor.cu)
@@ -165,12 +166,14 @@ int tensor_tile_q();
 int tensor_tile_r();
 int tensor_kpad(int32_t n_loci);
 int tensor_grid_target(int device);
+int tensor_pair_clusters(int device);
 cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_rows, int32_t kpad, uint8_t *out,
                              cudaStream_t s);
 cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
                                 const uint8_t *modes, int64_t n_q_pad, int32_t kpad, uint8_t *out, float *qconst,
                                 cudaStream_t s);
-cudaError_t launch_tensor(int epi, const CUtensorMap &map_a, const CUtensorMap &map_b, int64_t n_refs, int64_t n_q,
+cudaError_t launch_tensor(int epi, int pair, const CUtensorMap &map_a, const CUtensorMap &map_b, int64_t n_refs,
+                          int64_t n_q,
                           int32_t kpad, const float *qconst, uint32_t threshold, int32_t k, void *out,
                           int64_t ld_out, int64_t capacity, int64_t *hit_q, int64_t *hit_r, uint32_t *hit_score,
                           unsigned long long *hit_count, uint64_t *partial, const Partition &part, uint32_t *status,

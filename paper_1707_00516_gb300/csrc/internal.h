@@ -15,6 +15,7 @@ struct fastid_ctx {
     cudaMemPool_t pool = nullptr;
     uint32_t *dev_status = nullptr;  // [4]
     int grid_topk = 0, grid_hits = 0, grid_scores = 0, grid_tensor = 0;
+    int pair_clusters = 0;  // resident 2-CTA clusters of the paired tensor kernel (0: never pair)
     std::string last_error;
     // profiling (fastid_profile)
     bool profile = false;
@@ -35,6 +36,7 @@ struct fastid_refdb {
     uint8_t *fp8 = nullptr;      // [n_pad][kpad] e4m3 0/1 operand (FASTID_REFS_TENSOR)
     int32_t kpad = 0;            // loci padded to the tensor form's K stage
     CUtensorMap map_b;           // TMA map over fp8 (boxes of K-stage x reference tile)
+    CUtensorMap map_b_half;      // same, boxes of half a reference tile (paired launches)
     int64_t bytes = 0;
     int device = 0;
 };

@@ -37,22 +37,26 @@ __device__ int64_t cta_of(const Partition &P, int64_t u) {
 }
 
 // One warp per query: merge the sorted k-lists of every segment that covered
-// the query's tile.  Segment lists are laid out [slot][tile_q][k] with
-// slot = cta * max_seg + (segment index within the CTA), tile_q = PL_TQ or the
-// tile height the launch used.
-__global__ void topk_merge_kernel(const uint64_t *__restrict__ partial, Partition P, int32_t tile_q,
+// the query's tile.  The partition is over work groups (CTAs, or 2-CTA
+// clusters when paired: a paired unit covers query tiles 2 qq and 2 qq + 1,
+// taken by cluster ranks 0 and 1).  Segment lists are laid out
+// [slot][tile_q][k] with slot = cta * max_seg + (segment index within the CTA).
+__global__ void topk_merge_kernel(const uint64_t *__restrict__ partial, Partition P, int32_t tile_q, int32_t pair,
                                   int64_t n_q, int32_t k, uint32_t *__restrict__ out_scores,
                                   int64_t *__restrict__ out_idx) {
     const int lane = threadIdx.x & 31;
     const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (q >= n_q) return;
     const int64_t qt = q / tile_q, ql = q - qt * tile_q;
-    const int64_t u_lo = qt * P.n_rt, u_hi = u_lo + P.n_rt - 1;
-    const int64_t c_lo = cta_of(P, u_lo), c_hi = cta_of(P, u_hi);
+    const int64_t qq = pair ? qt >> 1 : qt;
+    const int64_t rank = pair ? qt & 1 : 0;
+    const int64_t u_lo = qq * P.n_rt, u_hi = u_lo + P.n_rt - 1;
+    const int64_t w_lo = cta_of(P, u_lo), w_hi = cta_of(P, u_hi);
     uint64_t acc = KEY_EMPTY;
-    for (int64_t c = c_lo; c <= c_hi; ++c) {
-        const int64_t first_qt = part_begin(P, c) / P.n_rt;
-        const int64_t slot = c * P.max_seg + (qt - first_qt);
+    for (int64_t w = w_lo; w <= w_hi; ++w) {
+        const int64_t first_qq = part_begin(P, w) / P.n_rt;
+        const int64_t cta = pair ? 2 * w + rank : w;
+        const int64_t slot = cta * P.max_seg + (qq - first_qq);
         uint64_t b = lane < k ? partial[(slot * tile_q + ql) * k + lane] : KEY_EMPTY;
         acc = warp_merge32(acc, b, lane);
     }
@@ -220,17 +224,18 @@ cudaError_t launch_topk_merge(const uint64_t *partial, const Partition &part, in
     if (n_q == 0) return cudaSuccess;
     const int wpb = 8;
     int64_t blocks = (n_q + wpb - 1) / wpb;
-    topk_merge_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, part, PL_TQ, n_q, k, out_scores, out_idx);
+    topk_merge_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, part, PL_TQ, 0, n_q, k, out_scores, out_idx);
     return cudaGetLastError();
 }
 
-cudaError_t launch_topk_merge_tile(const uint64_t *partial, const Partition &part, int32_t tile_q,
+cudaError_t launch_topk_merge_tile(const uint64_t *partial, const Partition &part, int32_t tile_q, int32_t pair,
                                    int64_t n_q, int32_t k, uint32_t *out_scores, int64_t *out_idx,
                                    cudaStream_t s) {
     if (n_q == 0) return cudaSuccess;
     const int wpb = 8;
     int64_t blocks = (n_q + wpb - 1) / wpb;
-    topk_merge_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, part, tile_q, n_q, k, out_scores, out_idx);
+    topk_merge_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, part, tile_q, pair, n_q, k, out_scores,
+                                                            out_idx);
     return cudaGetLastError();
 }
 

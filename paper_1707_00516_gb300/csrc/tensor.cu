@@ -150,12 +150,43 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// Multicast variant: the box lands at the same shared-memory offset in every
+// CTA of ctamask and completes bytes on the mbarrier at the same offset there.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, uint32_t bar, int32_t x,
+                                               int32_t y, uint16_t ctamask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%2, %3}], [%4], %5;"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(ctamask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA in the cluster.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
+}
+
+// Arrive (when this thread's prior tcgen05 operations complete) on the
+// mbarrier at the same offset in every CTA of ctamask.
+__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t ctamask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(ctamask)
+        : "memory");
 }
 
 __device__ __forceinline__ void tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -263,19 +294,29 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, uint32
     }
 }
 
-__device__ __forceinline__ void decode_unit(const TensorArgs &a, int64_t u, int &p, int64_t &qt, int64_t &rt) {
+// Unit u of the launch -> panel p, query tile qt, reference tile rt.  In
+// paired launches a unit covers two query tiles (one per CTA of the cluster)
+// and the CTA of cluster rank `rank` takes tile 2 qp + rank.
+template <bool PAIR>
+__device__ __forceinline__ void decode_unit(const TensorArgs &a, int64_t u, int rank, int &p, int64_t &qt,
+                                            int64_t &rt) {
     p = 0;
 #pragma unroll 1
     while (p + 1 < a.n_panels && u >= a.panel[p + 1].unit_base) ++p;
     const int64_t local = u - a.panel[p].unit_base;
-    qt = local / a.panel[p].n_rt;
-    rt = local - qt * a.panel[p].n_rt;
+    const int64_t qq = local / a.panel[p].n_rt;
+    rt = local - qq * a.panel[p].n_rt;
+    qt = PAIR ? 2 * qq + rank : qq;
 }
 
-template <int BN>
+// PAIR: 2-CTA clusters; both CTAs walk the same reference tiles for two
+// adjacent query tiles, and each multicasts half of every reference stage
+// into both CTAs' shared memory (BN = 256 only).
+template <int BN, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tensor_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TensorArgs args) {
     using S = TcShape<BN>;
+    static_assert(!PAIR || BN == 256, "paired launches use 256-reference tiles");
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned operand stages, then control block, then staging.
     const uint32_t raw = smem_u32(smem_raw);
@@ -290,21 +331,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const int64_t c = blockIdx.x;
+    const int64_t c = blockIdx.x;                     // this CTA: owner of partial-list slots
+    const int rank = PAIR ? (int)cluster_rank() : 0;
+    const int64_t wg = PAIR ? (c >> 1) : c;            // work group: cluster or CTA
     int64_t u_begin, u_end;
     if (args.cta_units) {
-        u_begin = args.cta_units[c];
-        u_end = args.cta_units[c + 1];
+        u_begin = args.cta_units[wg];
+        u_end = args.cta_units[wg + 1];
     } else {
-        u_begin = (c * args.n_units) / args.grid;
-        u_end = ((c + 1) * args.n_units) / args.grid;
+        u_begin = (wg * args.n_units) / args.grid;
+        u_end = ((wg + 1) * args.n_units) / args.grid;
     }
     volatile int *abort_flag = &ctl->abort_flag;
 
     if (tid == 0) {
         for (int s = 0; s < S::STAGES; ++s) {
             mbar_init(smem_u32(&ctl->full[s]), 1);
-            mbar_init(smem_u32(&ctl->empty[s]), 1);
+            mbar_init(smem_u32(&ctl->empty[s]), PAIR ? 2 : 1);  // both CTAs' MMAs release a paired stage
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl->tfull[a]), 1);
@@ -323,6 +366,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();  // the peer's barriers exist before any multicast targets them
     tc_fence_after();
     const uint32_t tmem_base = ctl->tmem_base;
 
@@ -340,7 +384,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int64_t u = u_begin; u < u_end && ok; ++u) {
                 int p;
                 int64_t qt, rt;
-                decode_unit(args, u, p, qt, rt);
+                decode_unit<PAIR>(args, u, rank, p, qt, rt);
                 const int n_kb = args.panel[p].n_kb;
                 for (int kb = 0; kb < n_kb; ++kb) {
                     ok = mbar_wait(smem_u32(&ctl->empty[stage]), phase ^ 1u, abort_flag, args.status, 1);
@@ -348,7 +392,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t fb = smem_u32(&ctl->full[stage]);
                     mbar_expect_tx(fb, TC_A_BYTES + S::B_BYTES);
                     tma_load_2d(smem_u32(sA + stage * TC_A_BYTES), &maps.a[p], fb, kb * TC_BK, (int32_t)(qt * TC_BM));
-                    tma_load_2d(smem_u32(sB + stage * S::B_BYTES), &maps.b[p], fb, kb * TC_BK, (int32_t)(rt * BN));
+                    if (PAIR)
+                        tma_load_2d_mc(smem_u32(sB + stage * S::B_BYTES + rank * (S::B_BYTES / 2)), &maps.b[p], fb,
+                                       kb * TC_BK, (int32_t)(rt * BN + rank * (BN / 2)), (uint16_t)0x3);
+                    else
+                        tma_load_2d(smem_u32(sB + stage * S::B_BYTES), &maps.b[p], fb, kb * TC_BK, (int32_t)(rt * BN));
                     ++issued;
                     if (++stage == S::STAGES) {
                         stage = 0;
@@ -358,8 +406,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             // Drain: the last fill of every stage has landed before the CTA
             // exits (fill n used stage n % S in phase (n / S) & 1).
-            for (int64_t n = issued - 1; n >= 0 && n >= issued - S::STAGES; --n)
+            for (int64_t n = issued - 1; n >= 0 && n >= issued - S::STAGES; --n) {
                 mbar_drain(smem_u32(&ctl->full[n % S::STAGES]), (uint32_t)((n / S::STAGES) & 1), args.status, 2);
+                // paired: both MMAs' releases of this stage (the peer's arrive
+                // remotely) have landed before the CTA exits
+                if (PAIR)
+                    mbar_drain(smem_u32(&ctl->empty[n % S::STAGES]), (uint32_t)((n / S::STAGES) & 1), args.status, 7);
+            }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
@@ -373,7 +426,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int64_t u = u_begin; u < u_end && ok; ++u) {
                 int p;
                 int64_t qt, rt;
-                decode_unit(args, u, p, qt, rt);
+                decode_unit<PAIR>(args, u, rank, p, qt, rt);
                 const int n_kb = args.panel[p].n_kb;
                 ok = mbar_wait(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, abort_flag, args.status, 3);
                 if (!ok) break;
@@ -388,7 +441,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int kk = 0; kk < TC_BK / 32; ++kk)  // K = 32 FP8 per MMA: +32 bytes = +2 in the address field
                         tc_mma_f8(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
-                    tc_commit(smem_u32(&ctl->empty[stage]));
+                    if (PAIR)
+                        tc_commit_mc(smem_u32(&ctl->empty[stage]), (uint16_t)0x3);
+                    else
+                        tc_commit(smem_u32(&ctl->empty[stage]));
                     if (++stage == S::STAGES) {
                         stage = 0;
                         phase ^= 1u;
@@ -426,7 +482,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int64_t u = u_begin; u < u_end; ++u) {
             int p;
             int64_t qt, rt;
-            decode_unit(args, u, p, qt, rt);
+            decode_unit<PAIR>(args, u, rank, p, qt, rt);
             const int64_t g = args.panel[p].tile_base + qt;
             if (g != g_prev) {
                 if (args.epi == EPI_TOPK && g_prev >= 0) {
@@ -530,6 +586,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();  // neither CTA leaves while the other may still address it
     tc_fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(S::TMEM_COLS)
@@ -695,6 +752,37 @@ cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s
     return cudaGetLastError();
 }
 
+// Largest number of 2-CTA clusters of the paired kernel that can be resident
+// at once (0 if clusters are unavailable).
+int tensor_pair_clusters(int device) {
+    size_t smem = tensor_smem<256>(EPI_TOPK);
+    if (cudaFuncSetAttribute(tensor_kernel<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3(sms & ~1);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, tensor_kernel<256, true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 int tensor_grid_target(int device) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -736,21 +824,42 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
     a.partial = L.partial;
     a.status = L.status;
     cudaError_t e;
+    if (L.pair) {
+        if (bn != 256) return cudaErrorInvalidValue;
+        size_t smem = tensor_smem<256>(L.epi);
+        e = cudaFuncSetAttribute(tensor_kernel<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof cfg);
+        cfg.gridDim = dim3(2 * L.grid);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, tensor_kernel<256, true>, maps, a);
+    }
     if (bn == 128) {
         size_t smem = tensor_smem<128>(L.epi);
-        e = cudaFuncSetAttribute(tensor_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(tensor_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        tensor_kernel<128><<<L.grid, TC_THREADS, smem, s>>>(maps, a);
+        tensor_kernel<128, false><<<L.grid, TC_THREADS, smem, s>>>(maps, a);
     } else {
         size_t smem = tensor_smem<256>(L.epi);
-        e = cudaFuncSetAttribute(tensor_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(tensor_kernel<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        tensor_kernel<256><<<L.grid, TC_THREADS, smem, s>>>(maps, a);
+        tensor_kernel<256, false><<<L.grid, TC_THREADS, smem, s>>>(maps, a);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_tensor(int epi, const CUtensorMap &map_a, const CUtensorMap &map_b, int64_t n_refs, int64_t n_q,
+cudaError_t launch_tensor(int epi, int pair, const CUtensorMap &map_a, const CUtensorMap &map_b, int64_t n_refs,
+                          int64_t n_q,
                           int32_t kpad, const float *qconst, uint32_t threshold, int32_t k, void *out,
                           int64_t ld_out, int64_t capacity, int64_t *hit_q, int64_t *hit_r, uint32_t *hit_score,
                           unsigned long long *hit_count, uint64_t *partial, const Partition &part, uint32_t *status,
@@ -758,6 +867,7 @@ cudaError_t launch_tensor(int epi, const CUtensorMap &map_a, const CUtensorMap &
     TcLaunch L;
     memset(&L, 0, sizeof L);
     L.n_panels = 1;
+    L.pair = pair;
     L.map_a[0] = map_a;
     L.map_b[0] = map_b;
     L.n_refs[0] = n_refs;

@@ -97,3 +97,35 @@ def test_tensor_form_needs_operand_copy(ts):
     db2 = ts.load_refs_alleles(torch.from_numpy(R).cuda(), 64)
     assert db2.info()["flags"] == B.REFS_TENSOR
     db2.close()
+
+
+@pytest.mark.parametrize("n_q,n_refs", [(600, 7000), (1024, 20000), (513, 3000)])
+def test_paired_launch_parity(ts, n_q, n_refs):
+    """Enough query tiles for the paired (2-CTA cluster, multicast) launch,
+    including an odd tile count (a padding tile in the last pair)."""
+    import gen
+    n_loci, seed = 1536, 77 + n_q
+    thr = gen.maf_thresholds(seed, n_loci)
+    R = gen.allele_rows(seed, gen.STREAM_DB, np.arange(n_refs), thr)
+    rec = gen.concat_recipes(gen.recipe_individuals(n_q // 2, n_refs, n_loci, seed, n_planted=50),
+                             gen.recipe_mixtures(n_q - n_q // 2, n_refs, n_loci, seed, 2, 5))
+    Q = oracle.mix(gen.source_alleles(rec, thr), rec.offsets)
+    db = ts.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci)
+    q = torch.empty((n_q, words64(n_loci)), dtype=torch.int64, device="cuda")
+    B.fastid_pack(ts.ctx, torch.from_numpy(Q).cuda(), n_loci, q)
+    modes = torch.from_numpy(rec.modes).cuda()
+    mis, une = oracle.scores(R, Q)
+    exp = oracle.select(mis, une, rec.modes)
+    sc, ix = ts.topk(db, q, modes, 32, 300)
+    es, ei = oracle.topk(exp, 32, 300)
+    assert np.array_equal(sc.cpu().numpy().view(np.uint32), es)
+    assert np.array_equal(ix.cpu().numpy(), ei)
+    full = ts.scores(db, q, modes, torch.int32)
+    assert np.array_equal(full.cpu().numpy().view(np.uint32), exp)
+    hq, hr, hs, hc = ts.hits(db, q, modes, 20, 1 << 20)
+    oq, orr, osc = oracle.hits(exp, 20)
+    n = int(hc.item())
+    assert n == oq.size and np.array_equal(hq[:n].cpu().numpy(), oq) and np.array_equal(hr[:n].cpu().numpy(), orr)
+    torch.cuda.synchronize()
+    assert B.fastid_sync_status(ts.ctx) == B.OK
+    db.close()
