@@ -40,11 +40,11 @@ constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK;  // 16 KB
 constexpr uint64_t WAIT_NS = 2000000000ull;     // 2 s per wait
 
 // Kernel variants: references per tile (the MMA's N) and pipeline depth.
-//   BN = 256: 32 KB reference stage, 3 stages, 2 x 256 TMEM columns
-//   BN = 128: 16 KB reference stage, 5 stages, 2 x 128 TMEM columns
+//   BN = 256: 32 KB reference stage, 4 stages, 2 x 256 TMEM columns
+//   BN = 128: 16 KB reference stage, 6 stages, 2 x 128 TMEM columns
 template <int BN>
 struct TcShape {
-    static constexpr int STAGES = BN == 256 ? 3 : 5;
+    static constexpr int STAGES = BN == 256 ? 4 : 6;
     static constexpr uint32_t B_BYTES = (uint32_t)BN * TC_BK;
     static constexpr uint32_t TMEM_COLS = BN == 256 ? 512 : 256;
 };
