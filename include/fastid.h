@@ -260,7 +260,8 @@ typedef struct {
 enum {
     FASTID_VARIANT_AUTO = 0,        /* the library's default (N256)            */
     FASTID_VARIANT_TENSOR_N256 = 1, /* 128 x 256 tiles, 4-stage pipeline       */
-    FASTID_VARIANT_TENSOR_N128 = 2  /* 128 x 128 tiles, 6-stage pipeline       */
+    FASTID_VARIANT_TENSOR_N128 = 2, /* 128 x 128 tiles, 6-stage pipeline       */
+    FASTID_VARIANT_TENSOR_PAIR = 3  /* 2-CTA clusters on tile pairs sharing reference stages */
 };
 
 fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs, int32_t n_panels,

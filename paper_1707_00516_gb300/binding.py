@@ -27,7 +27,7 @@ MAX_K = 32
 MAX_LOCI = 65536
 NO_THRESHOLD = 0xFFFFFFFF
 NOALLOC_SCRATCH_BYTES = 16 << 20
-VARIANT_AUTO, VARIANT_TENSOR_N256, VARIANT_TENSOR_N128 = 0, 1, 2
+VARIANT_AUTO, VARIANT_TENSOR_N256, VARIANT_TENSOR_N128, VARIANT_TENSOR_PAIR = 0, 1, 2, 3
 
 _lib = None
 _lock = threading.Lock()

@@ -415,53 +415,63 @@ fastid_status pick_form(fastid_ctx *ctx, const fastid_refdb *db, int *tensor) {
 
 // Tensor-form front half: e4m3 query operand + c_q in scratch, its TMA map,
 // and the partition over (128-query tile, 256-reference tile) units.
-struct TensorPrep {
-    CUtensorMap map_a;
-    float *qconst;
-    Partition part;  // over work groups: CTAs, or 2-CTA clusters when paired
-    int pair;
-};
-
 // Paired launches (2-CTA clusters sharing reference stages) once there are
 // enough query tiles that padding to an even count costs little.
 constexpr int PAIR_MIN_TILES = 4;
 
+// Tensor-form front half of a call: schedule, scratch (e4m3 query operand,
+// c_q, and `extra` bytes computed from the schedule), operand encoding and
+// the launch description for one panel.
+struct TensorPrep {
+    TcLaunch L;
+    int64_t n_ctas;
+};
+
+enum ExtraKind { EXTRA_NONE, EXTRA_TOPK, EXTRA_HITS };
+
 fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q, int64_t ld_q, int64_t n_q,
-                             const uint8_t *modes, cudaStream_t s, Scratch &scr, size_t (*extra_fn)(const Partition &, void *),
-                             void *extra_arg, size_t *extra_off, TensorPrep *tp) {
+                             const uint8_t *modes, cudaStream_t s, Scratch &scr, ExtraKind ek, int64_t karg,
+                             size_t *extra_off, TensorPrep *tp) {
+    TcLaunch &L = tp->L;
+    memset(&L, 0, sizeof L);
     const int64_t n_qt = round_up(n_q, tensor_tile_q()) / tensor_tile_q();
-    tp->pair = (ctx->pair_clusters > 0 && n_qt >= PAIR_MIN_TILES) ? 1 : 0;
-    const int64_t n_q_pad = round_up(n_q, (int64_t)tensor_tile_q() * (tp->pair ? 2 : 1));
-    const int64_t groups = n_q_pad / tensor_tile_q() / (tp->pair ? 2 : 1);
-    tp->part = make_partition((int32_t)groups, db->n_pad / tensor_tile_r(),
-                              tp->pair ? ctx->pair_clusters : ctx->grid_tensor);
-    const size_t extra = extra_fn ? extra_fn(tp->part, extra_arg) * (tp->pair ? 2 : 1) : 0;
+    L.pair = (ctx->pair_clusters > 0 && n_qt >= PAIR_MIN_TILES) ? 1 : 0;
+    const int64_t n_q_pad = round_up(n_q, (int64_t)tensor_tile_q() * (L.pair ? 2 : 1));
+    const int64_t n_qq = n_q_pad / tensor_tile_q() / (L.pair ? 2 : 1);
+    const int64_t n_rt = db->n_pad / tensor_tile_r();
+    const int64_t n_kb = db->kpad / 128;
+    const int64_t tile_bytes = (int64_t)tensor_tile_r() * db->kpad;
+    L.n_groups = make_tensor_schedule(1, &n_qq, &n_rt, &n_kb, &tile_bytes,
+                                      L.pair ? ctx->pair_clusters : ctx->grid_tensor, L.sched, &L.max_tpx);
+    tp->n_ctas = (int64_t)L.n_groups * (L.pair ? 2 : 1);
+    size_t extra = 0;
+    if (ek == EXTRA_TOPK) extra = (size_t)tp->n_ctas * L.max_tpx * tensor_tile_q() * (size_t)karg * 8;
+    if (ek == EXTRA_HITS) extra = 256 + (size_t)(2 + hits_sort_elems(karg) * 3 / 2 + 1) * 8;
     Carver cv;
     size_t o_a = cv.take<uint8_t>((size_t)n_q_pad * db->kpad);
     size_t o_c = cv.take<float>((size_t)n_q_pad);
     *extra_off = cv.take<uint8_t>(extra);
     FASTID_CUDA(ctx, scr.alloc(cv.off));
     uint8_t *a = at<uint8_t>(scr.p, o_a);
-    tp->qconst = at<float>(scr.p, o_c);
+    float *qconst = at<float>(scr.p, o_c);
     FASTID_CUDA(ctx, launch_queries_e4m3(q, ld_q, n_q, db->n_words64, db->n_loci, modes, n_q_pad, db->kpad, a,
-                                         tp->qconst, s));
+                                         qconst, s));
     count_launches(ctx, 1);
-    FASTID_CUDA(ctx, make_operand_map(&tp->map_a, a, n_q_pad, db->kpad, tensor_tile_q()));
+    FASTID_CUDA(ctx, make_operand_map(&L.map_a[0], a, n_q_pad, db->kpad, tensor_tile_q()));
+    L.n_panels = 1;
+    L.map_b[0] = L.pair ? db->map_b_half : db->map_b;
+    L.n_refs[0] = db->n_refs;
+    L.n_q[0] = n_q;
+    L.n_rt[0] = n_rt;
+    L.kpad[0] = db->kpad;
+    L.qconst[0] = qconst;
+    L.status = ctx->dev_status;
     return FASTID_OK;
 }
 
 uint32_t clamp_threshold(uint32_t t, int32_t n_loci) {
     if (t == 0xFFFFFFFFu) return t;
     return t > (uint32_t)n_loci ? (uint32_t)n_loci : t;
-}
-
-size_t topk_extra(const Partition &p, void *karg) {
-    return (size_t)p.grid * p.max_seg * 128 * (size_t)(*static_cast<int32_t *>(karg)) * 8;
-}
-
-size_t hits_extra(const Partition &, void *carg) {
-    const int64_t P = hits_sort_elems(*static_cast<int64_t *>(carg));
-    return 256 + (size_t)(2 + P + P / 2 + 1) * 8;
 }
 
 }  // namespace
@@ -486,13 +496,15 @@ fastid_status fastid_scores(fastid_ctx *ctx, const fastid_refdb *db, const uint6
     size_t xo;
     if (tensor) {
         TensorPrep tp;
-        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, nullptr, nullptr, &xo, &tp)))
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_NONE, 0, &xo, &tp)))
             return st;
+        tp.L.epi = out_bytes == 2 ? EPI_SCORES16 : EPI_SCORES32;
+        tp.L.threshold = 0xFFFFFFFFu;
+        tp.L.k = 1;
+        tp.L.out = out_dev;
+        tp.L.ld_out = ld_out;
         MainTimer tm(ctx, s);
-        FASTID_CUDA(ctx, launch_tensor(out_bytes == 2 ? EPI_SCORES16 : EPI_SCORES32, tp.pair, tp.map_a,
-                                       tp.pair ? db->map_b_half : db->map_b, db->n_refs,
-                                       n_q, db->kpad, tp.qconst, 0xFFFFFFFFu, 1, out_dev, ld_out, 0, nullptr,
-                                       nullptr, nullptr, nullptr, nullptr, tp.part, ctx->dev_status, s));
+        FASTID_CUDA(ctx, launch_tensor_multi(256, tp.L, s));
         tm.done();
         count_launches(ctx, 1);
         return FASTID_OK;
@@ -526,18 +538,17 @@ fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_
     if (tensor) {
         TensorPrep tp;
         size_t xo;
-        int32_t kk = k;
-        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, topk_extra, &kk, &xo, &tp)))
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_TOPK, k, &xo, &tp)))
             return st;
         uint64_t *partial = at<uint64_t>(scr.p, xo);
+        tp.L.epi = EPI_TOPK;
+        tp.L.threshold = clamp_threshold(threshold, db->n_loci);
+        tp.L.k = k;
+        tp.L.partial = partial;
         MainTimer tm(ctx, s);
-        FASTID_CUDA(ctx, launch_tensor(EPI_TOPK, tp.pair, tp.map_a, tp.pair ? db->map_b_half : db->map_b, db->n_refs,
-                                       n_q, db->kpad, tp.qconst,
-                                       clamp_threshold(threshold, db->n_loci), k, nullptr, 0, 0, nullptr, nullptr,
-                                       nullptr, nullptr, partial, tp.part, ctx->dev_status, s));
+        FASTID_CUDA(ctx, launch_tensor_multi(256, tp.L, s));
         tm.done();
-        FASTID_CUDA(ctx, launch_topk_merge_tile(partial, tp.part, tensor_tile_q(), tp.pair, n_q, k, out_scores_dev,
-                                                out_idx_dev, s));
+        FASTID_CUDA(ctx, launch_merge_sched(partial, tp.L, nullptr, n_q, out_scores_dev, out_idx_dev, s));
         count_launches(ctx, 2);
         return FASTID_OK;
     }
@@ -580,17 +591,21 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
     if (tensor) {
         TensorPrep tp;
         size_t xo;
-        int64_t cap = capacity;
-        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, hits_extra, &cap, &xo, &tp)))
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_HITS, capacity, &xo, &tp)))
             return st;
         unsigned long long *count = at<unsigned long long>(scr.p, xo);
         uint64_t *sort_tmp = at<uint64_t>(scr.p, xo + 256);
         FASTID_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
+        tp.L.epi = EPI_HITS;
+        tp.L.threshold = clamp_threshold(threshold, db->n_loci);
+        tp.L.k = 1;
+        tp.L.capacity = capacity;
+        tp.L.hit_q = hit_q_dev;
+        tp.L.hit_r = hit_r_dev;
+        tp.L.hit_score = hit_score_dev;
+        tp.L.hit_count = count;
         MainTimer tm(ctx, s);
-        FASTID_CUDA(ctx, launch_tensor(EPI_HITS, tp.pair, tp.map_a, tp.pair ? db->map_b_half : db->map_b, db->n_refs,
-                                       n_q, db->kpad, tp.qconst,
-                                       clamp_threshold(threshold, db->n_loci), 1, nullptr, 0, capacity, hit_q_dev,
-                                       hit_r_dev, hit_score_dev, count, nullptr, tp.part, ctx->dev_status, s));
+        FASTID_CUDA(ctx, launch_tensor_multi(256, tp.L, s));
         tm.done();
         FASTID_CUDA(ctx, launch_hits_finish(count, capacity, hit_q_dev, hit_r_dev, hit_score_dev, hit_count_dev,
                                             sort_tmp, ctx->dev_status, s));

@@ -80,31 +80,45 @@ struct PrepJob {
     int32_t pad_;
 };
 
-// Batched form: one query's merge of per-segment lists into its output row.
+// Batched form: one query's merge of per-slot lists into its output row.
 struct MergeJob {
     uint32_t *out_s;  // [k]
     int64_t *out_i;   // [k]
-    int32_t g;        // global query-tile id
-    int32_t ql;       // row within the tile
+    int32_t panel;
+    int32_t q;        // row of the panel's query operand
+};
+
+// Tensor-form schedule of one panel.  The panel's work groups (CTAs, or
+// 2-CTA clusters when paired) form an a x b grid: tile group x owns query
+// tiles (pairs) [x tpx, (x+1) tpx), reference slice y owns reference tiles
+// [y n_rt / b, (y+1) n_rt / b).  A group walks its slice in chunks of
+// `chunk` tiles and, inside a chunk, each of its query tiles in turn, so the
+// groups of a slice read the same reference chunk at about the same time (it
+// is fetched from DRAM once and served from L2 to the others).  Each (group,
+// query tile) keeps its running top-k in a slot of the partial buffer,
+// saved after every chunk and resumed at the next.
+struct TcSched {
+    int32_t n_qq;   // query tiles, or tile pairs when paired
+    int32_t g0;     // first work group of the panel
+    int32_t a, b;   // tile groups x reference slices
+    int32_t tpx;    // query tiles (pairs) per tile group
+    int32_t chunk;  // reference tiles per chunk
 };
 
 // Host-side description of one tensor-form launch over up to TC_MAXP panels.
 struct TcLaunch {
     int32_t n_panels;
-    int32_t pair;  // 2-CTA clusters sharing reference stages; grid and units count clusters and pair-units
+    int32_t pair;  // 2-CTA clusters sharing reference stages (groups are clusters, tiles are pairs)
     CUtensorMap map_a[TC_MAXP];
     CUtensorMap map_b[TC_MAXP];
     int64_t n_refs[TC_MAXP];
     int64_t n_q[TC_MAXP];
     int64_t n_rt[TC_MAXP];
-    int64_t unit_base[TC_MAXP];
     int32_t kpad[TC_MAXP];
-    int32_t tile_base[TC_MAXP];
     const float *qconst[TC_MAXP];
-    int64_t n_units;
-    int32_t grid;
-    int32_t max_seg;
-    const int64_t *cta_units;
+    TcSched sched[TC_MAXP];
+    int32_t n_groups;  // sum of a * b over panels
+    int32_t max_tpx;   // slots per CTA
     uint32_t threshold;
     int32_t k;
     int32_t epi;
@@ -115,9 +129,15 @@ struct TcLaunch {
     int64_t *hit_r;
     uint32_t *hit_score;
     unsigned long long *hit_count;
-    uint64_t *partial;
+    uint64_t *partial;  // EPI_TOPK: [ctas * max_tpx][k][128]
     uint32_t *status;
 };
+
+// Fills sched[] for n panels and G work groups; returns the number of groups
+// used (sum of a * b) and sets *max_tpx.  unit_cost: K stages of a unit;
+// tile_bytes: bytes of one reference tile of the operand.
+int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, const int64_t *unit_cost,
+                             const int64_t *tile_bytes, int32_t G, TcSched *sched, int32_t *max_tpx);
 
 // Top-k keys: (score << 32) | ref, so that ordering keys orders by score then
 // by reference index.  An empty slot holds KEY_EMPTY.
@@ -172,17 +192,13 @@ cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_row
 cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
                                 const uint8_t *modes, int64_t n_q_pad, int32_t kpad, uint8_t *out, float *qconst,
                                 cudaStream_t s);
-cudaError_t launch_tensor(int epi, int pair, const CUtensorMap &map_a, const CUtensorMap &map_b, int64_t n_refs,
-                          int64_t n_q,
-                          int32_t kpad, const float *qconst, uint32_t threshold, int32_t k, void *out,
-                          int64_t ld_out, int64_t capacity, int64_t *hit_q, int64_t *hit_r, uint32_t *hit_score,
-                          unsigned long long *hit_count, uint64_t *partial, const Partition &part, uint32_t *status,
-                          cudaStream_t s);
+
 cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s);
 cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s);
-cudaError_t launch_merge_jobs(const uint64_t *partial, const MergeJob *jobs, int64_t n_jobs, const int32_t *g_lo,
-                              const int32_t *g_hi, const int32_t *cta_gfirst, int32_t max_seg, int32_t tile_q,
-                              int32_t k, cudaStream_t s);
+// Merge of per-slot lists for the queries of a tensor launch (jobs == nullptr:
+// one panel, query q's output is out_scores/out_idx row q).
+cudaError_t launch_merge_sched(const uint64_t *partial, const TcLaunch &L, const MergeJob *jobs, int64_t n_jobs,
+                               uint32_t *out_scores, int64_t *out_idx, cudaStream_t s);
 cudaError_t launch_hits_finish(unsigned long long *count, int64_t capacity, int64_t *hit_q,
                                int64_t *hit_r, uint32_t *hit_score, int64_t *count_out,
                                uint64_t *sort_tmp, uint32_t *status, cudaStream_t s);

@@ -11,8 +11,9 @@
 // a CUDA graph (fastid_plan_capture) and replayed (fastid_plan_replay) with
 // new query contents in the same buffers.
 //
-// Work balance: units differ in cost by their panel's K stages, so CTA c
-// takes the units whose cumulative cost falls in [c C / G, (c+1) C / G).
+// Work balance: panels get work groups in proportion to their cost (query
+// tiles x reference tiles x K stages) and each panel's groups follow the
+// aligned tile-group x reference-slice schedule (TcSched).
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -32,13 +33,12 @@ struct fastid_plan {
     int64_t n_queries = 0;
     int64_t n_jobs_prep = 0;
     int64_t n_jobs_merge = 0;
+    int64_t n_ctas = 0;
     TcLaunch launch;
     void *work = nullptr;  // one device allocation for every table and operand
     int64_t work_bytes = 0;
     PrepJob *prep = nullptr;
     MergeJob *merge = nullptr;
-    int32_t *g_lo = nullptr, *g_hi = nullptr, *cta_gfirst = nullptr;
-    int64_t *cta_units = nullptr;
     uint64_t *partial = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -82,8 +82,10 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     if (n_batches < 0 || (n_batches > 0 && !batches)) return perr(ctx, FASTID_EINVAL, "bad batch list");
     if (k < 1 || k > FASTID_MAX_K) return perr(ctx, FASTID_EINVAL, "k out of range");
     if (variant != FASTID_VARIANT_AUTO && variant != FASTID_VARIANT_TENSOR_N256 &&
-        variant != FASTID_VARIANT_TENSOR_N128)
+        variant != FASTID_VARIANT_TENSOR_N128 && variant != FASTID_VARIANT_TENSOR_PAIR)
         return perr(ctx, FASTID_EINVAL, "unknown variant");
+    if (variant == FASTID_VARIANT_TENSOR_PAIR && ctx->pair_clusters < 1)
+        return perr(ctx, FASTID_EUNSUPPORTED, "paired launches need 2-CTA clusters");
     for (int p = 0; p < n_panels; ++p) {
         if (!dbs[p]) return perr(ctx, FASTID_EINVAL, "database is NULL");
         if (dbs[p]->device != ctx->device) return perr(ctx, FASTID_EINVAL, "database belongs to another device");
@@ -110,67 +112,27 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     P->k = k;
     P->threshold = threshold;
     const int BN = P->bn;
+    const int pair = variant == FASTID_VARIANT_TENSOR_PAIR ? 1 : 0;
+    const int64_t tq = (int64_t)TC_TILE_Q * (pair ? 2 : 1);  // operand rows per tile (pair)
 
     // Rows of each panel's operand: its batches' queries, in batch order.
     std::vector<int64_t> rows(n_panels, 0);
     for (int b = 0; b < n_batches; ++b) rows[batches[b].panel] += batches[b].n_q;
-    std::vector<int64_t> rows_pad(n_panels), n_qt(n_panels), n_rt(n_panels), unit_base(n_panels + 1),
-        cost_base(n_panels + 1), tile_base(n_panels + 1);
-    unit_base[0] = cost_base[0] = tile_base[0] = 0;
+    std::vector<int64_t> rows_pad(n_panels), n_qq(n_panels), n_rt(n_panels), n_kb(n_panels), tile_bytes(n_panels);
     for (int p = 0; p < n_panels; ++p) {
-        rows_pad[p] = rup(std::max<int64_t>(rows[p], 1), TC_TILE_Q);
-        n_qt[p] = rows[p] > 0 ? rows_pad[p] / TC_TILE_Q : 0;
+        rows_pad[p] = rup(std::max<int64_t>(rows[p], 1), tq);
+        n_qq[p] = rows[p] > 0 ? rows_pad[p] / tq : 0;
         n_rt[p] = dbs[p]->n_pad / BN;
-        unit_base[p + 1] = unit_base[p] + n_qt[p] * n_rt[p];
-        cost_base[p + 1] = cost_base[p] + n_qt[p] * n_rt[p] * (dbs[p]->kpad / 128);
-        tile_base[p + 1] = tile_base[p] + n_qt[p];
+        n_kb[p] = dbs[p]->kpad / 128;
+        tile_bytes[p] = (int64_t)BN * dbs[p]->kpad;
         P->n_queries += rows[p];
     }
-    const int64_t U = unit_base[n_panels], C = cost_base[n_panels];
-    const int64_t n_tiles = tile_base[n_panels];
-    int64_t G = std::min<int64_t>(ctx->grid_tensor, std::max<int64_t>(U, 1));
-
-    // Cost-balanced unit ranges.
-    std::vector<int64_t> cta(G + 1);
-    for (int64_t c = 0; c <= G; ++c) {
-        const int64_t T = (c * C) / G;
-        int p = 0;
-        while (p + 1 < n_panels && cost_base[p + 1] <= T) ++p;
-        const int64_t w = dbs[p]->kpad / 128;
-        int64_t u = unit_base[p] + (T - cost_base[p] + w - 1) / w;
-        cta[c] = std::min(u, U);
-    }
-    cta[0] = 0;
-    cta[G] = U;
-    // Drop empty ranges (a costly panel can leave some): every launched CTA
-    // then holds at least one unit, and the CTAs covering a query tile are
-    // consecutive, which the merge relies on.
-    {
-        std::vector<int64_t> packed_cta;
-        for (int64_t c = 0; c < G; ++c)
-            if (cta[c + 1] > cta[c]) packed_cta.push_back(cta[c]);
-        packed_cta.push_back(U);
-        cta.swap(packed_cta);
-        G = (int64_t)cta.size() - 1;
-    }
-    auto tile_of = [&](int64_t u) -> int64_t {
-        int p = 0;
-        while (p + 1 < n_panels && unit_base[p + 1] <= u) ++p;
-        return tile_base[p] + (u - unit_base[p]) / n_rt[p];
-    };
-    std::vector<int32_t> gfirst(G, 0), glo(std::max<int64_t>(n_tiles, 1), INT32_MAX),
-        ghi(std::max<int64_t>(n_tiles, 1), -1);
-    int32_t max_seg = 1;
-    for (int64_t c = 0; c < G; ++c) {
-        if (cta[c + 1] <= cta[c]) continue;
-        const int64_t g0 = tile_of(cta[c]), g1 = tile_of(cta[c + 1] - 1);
-        gfirst[c] = (int32_t)g0;
-        max_seg = std::max<int32_t>(max_seg, (int32_t)(g1 - g0 + 1));
-        for (int64_t g = g0; g <= g1; ++g) {
-            glo[g] = std::min<int32_t>(glo[g], (int32_t)c);
-            ghi[g] = std::max<int32_t>(ghi[g], (int32_t)c);
-        }
-    }
+    TcLaunch &L = P->launch;
+    memset(&L, 0, sizeof L);
+    L.pair = pair;
+    L.n_groups = make_tensor_schedule(n_panels, n_qq.data(), n_rt.data(), n_kb.data(), tile_bytes.data(),
+                                      pair ? ctx->pair_clusters : ctx->grid_tensor, L.sched, &L.max_tpx);
+    P->n_ctas = (int64_t)L.n_groups * (pair ? 2 : 1);
 
     // Workspace layout.
     size_t off = 0;
@@ -189,11 +151,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     }
     const size_t o_prep = take((size_t)n_prep * sizeof(PrepJob));
     const size_t o_merge = take((size_t)std::max<int64_t>(P->n_queries, 1) * sizeof(MergeJob));
-    const size_t o_glo = take((size_t)std::max<int64_t>(n_tiles, 1) * sizeof(int32_t));
-    const size_t o_ghi = take((size_t)std::max<int64_t>(n_tiles, 1) * sizeof(int32_t));
-    const size_t o_gf = take((size_t)G * sizeof(int32_t));
-    const size_t o_cta = take((size_t)(G + 1) * sizeof(int64_t));
-    const size_t o_part = take((size_t)G * max_seg * TC_TILE_Q * k * sizeof(uint64_t));
+    const size_t o_part = take((size_t)std::max<int64_t>(P->n_ctas, 1) * L.max_tpx * TC_TILE_Q * k * sizeof(uint64_t));
     e = cudaMalloc(&P->work, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -203,10 +161,6 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     uint8_t *W = static_cast<uint8_t *>(P->work);
     P->prep = reinterpret_cast<PrepJob *>(W + o_prep);
     P->merge = reinterpret_cast<MergeJob *>(W + o_merge);
-    P->g_lo = reinterpret_cast<int32_t *>(W + o_glo);
-    P->g_hi = reinterpret_cast<int32_t *>(W + o_ghi);
-    P->cta_gfirst = reinterpret_cast<int32_t *>(W + o_gf);
-    P->cta_units = reinterpret_cast<int64_t *>(W + o_cta);
     P->partial = reinterpret_cast<uint64_t *>(W + o_part);
 
     // Host tables.
@@ -240,8 +194,8 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
                 MergeJob m;
                 m.out_s = B.out_scores_dev + i * k;
                 m.out_i = B.out_idx_dev + i * k;
-                m.g = (int32_t)(tile_base[p] + r / TC_TILE_Q);
-                m.ql = (int32_t)(r % TC_TILE_Q);
+                m.panel = p;
+                m.q = (int32_t)r;
                 merge.push_back(m);
             }
         }
@@ -251,25 +205,17 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     e = cudaMemcpy(P->prep, prep.data(), prep.size() * sizeof(PrepJob), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !merge.empty())
         e = cudaMemcpy(P->merge, merge.data(), merge.size() * sizeof(MergeJob), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && n_tiles > 0)
-        e = cudaMemcpy(P->g_lo, glo.data(), n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && n_tiles > 0)
-        e = cudaMemcpy(P->g_hi, ghi.data(), n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->cta_gfirst, gfirst.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->cta_units, cta.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_plan(P);
         return pcuda(ctx, e, "plan tables");
     }
 
     // Launch description.
-    TcLaunch &L = P->launch;
-    memset(&L, 0, sizeof L);
     L.n_panels = n_panels;
     for (int p = 0; p < n_panels; ++p) {
         e = make_operand_map(&L.map_a[p], W + o_a[p], rows_pad[p], dbs[p]->kpad, TC_TILE_Q);
         if (e == cudaSuccess)
-            e = make_operand_map(&L.map_b[p], dbs[p]->fp8, dbs[p]->n_pad, dbs[p]->kpad, BN);
+            e = make_operand_map(&L.map_b[p], dbs[p]->fp8, dbs[p]->n_pad, dbs[p]->kpad, pair ? BN / 2 : BN);
         if (e != cudaSuccess) {
             free_plan(P);
             return pcuda(ctx, e, "tensor maps");
@@ -277,21 +223,15 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
         L.n_refs[p] = dbs[p]->n_refs;
         L.n_q[p] = rows[p];
         L.n_rt[p] = n_rt[p];
-        L.unit_base[p] = unit_base[p];
         L.kpad[p] = dbs[p]->kpad;
-        L.tile_base[p] = (int32_t)tile_base[p];
         L.qconst[p] = reinterpret_cast<const float *>(W + o_qc[p]);
     }
-    L.n_units = U;
-    L.grid = (int32_t)G;
-    L.max_seg = max_seg;
-    L.cta_units = P->cta_units;
-    L.threshold = threshold;
     L.k = k;
     L.epi = EPI_TOPK;
     L.partial = P->partial;
     L.status = ctx->dev_status;
     // Scores never exceed a panel's loci count; clamp so T + 1 stays exact in FP32.
+    L.threshold = threshold;
     if (threshold != 0xFFFFFFFFu) {
         int32_t nmax = 0;
         for (int p = 0; p < n_panels; ++p) nmax = std::max(nmax, dbs[p]->n_loci);
@@ -312,8 +252,7 @@ fastid_status fastid_plan_run(fastid_plan *plan, fastid_stream stream) {
     if (e != cudaSuccess) return pcuda(ctx, e, "batched operand preparation");
     e = launch_tensor_multi(plan->bn, plan->launch, s);
     if (e != cudaSuccess) return pcuda(ctx, e, "batched compare launch");
-    e = launch_merge_jobs(plan->partial, plan->merge, plan->n_jobs_merge, plan->g_lo, plan->g_hi, plan->cta_gfirst,
-                          plan->launch.max_seg, TC_TILE_Q, plan->k, s);
+    e = launch_merge_sched(plan->partial, plan->launch, plan->merge, plan->n_jobs_merge, nullptr, nullptr, s);
     if (e != cudaSuccess) return pcuda(ctx, e, "batched merge");
     ctx->launches += 3;
     return FASTID_OK;
@@ -373,9 +312,16 @@ fastid_status fastid_plan_info(const fastid_plan *plan, int64_t *n_queries, int6
                                int32_t *variant, int64_t *workspace_bytes) {
     if (!plan) return FASTID_EINVAL;
     if (n_queries) *n_queries = plan->n_queries;
-    if (n_units) *n_units = plan->launch.n_units;
-    if (grid) *grid = plan->launch.grid;
-    if (variant) *variant = plan->bn == 128 ? FASTID_VARIANT_TENSOR_N128 : FASTID_VARIANT_TENSOR_N256;
+    if (n_units) {
+        int64_t u = 0;
+        for (int p = 0; p < plan->launch.n_panels; ++p)
+            u += (int64_t)plan->launch.sched[p].n_qq * plan->launch.n_rt[p];
+        *n_units = u;
+    }
+    if (grid) *grid = (int32_t)plan->n_ctas;
+    if (variant)
+        *variant = plan->launch.pair ? FASTID_VARIANT_TENSOR_PAIR
+                                     : (plan->bn == 128 ? FASTID_VARIANT_TENSOR_N128 : FASTID_VARIANT_TENSOR_N256);
     if (workspace_bytes) *workspace_bytes = plan->work_bytes;
     return FASTID_OK;
 }

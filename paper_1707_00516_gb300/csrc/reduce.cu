@@ -66,21 +66,45 @@ __global__ void topk_merge_kernel(const uint64_t *__restrict__ partial, Partitio
     }
 }
 
-// Batched form: one warp per job; segments of tile g are the CTAs
-// g_lo[g] .. g_hi[g], CTA c holding tile g as its (g - cta_gfirst[c])-th segment.
-__global__ void topk_merge_jobs_kernel(const uint64_t *__restrict__ partial, const MergeJob *__restrict__ jobs,
-                                       int64_t n_jobs, const int32_t *__restrict__ g_lo,
-                                       const int32_t *__restrict__ g_hi, const int32_t *__restrict__ cta_gfirst,
-                                       int32_t max_seg, int32_t tile_q, int32_t k) {
+// Tensor launches: one warp per query; its tile's lists sit in one slot of
+// every reference slice's group of its tile group (see TcSched).  Slot
+// layout [slot][k][128].
+struct MergeSched {
+    int32_t n_panels;
+    int32_t pair;
+    int32_t max_tpx;
+    int32_t k;
+    TcSched sc[TC_MAXP];
+};
+
+__global__ void topk_merge_sched_kernel(const uint64_t *__restrict__ partial, const MergeSched M,
+                                        const MergeJob *__restrict__ jobs, int64_t n_jobs,
+                                        uint32_t *__restrict__ out_s, int64_t *__restrict__ out_i) {
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= n_jobs) return;
-    const MergeJob jb = jobs[j];
+    const int k = M.k;
+    MergeJob jb;
+    if (jobs) {
+        jb = jobs[j];
+    } else {
+        jb.out_s = out_s + j * k;
+        jb.out_i = out_i + j * k;
+        jb.panel = 0;
+        jb.q = (int32_t)j;
+    }
+    const TcSched &sc = M.sc[jb.panel];
+    const int64_t qt = jb.q / TC_TILE_Q, ql = jb.q - qt * TC_TILE_Q;
+    const int64_t qq = M.pair ? qt >> 1 : qt;
+    const int64_t rank = M.pair ? qt & 1 : 0;
+    const int64_t x = qq / sc.tpx, li = qq - x * sc.tpx;
     uint64_t acc = KEY_EMPTY;
-    for (int32_t c = g_lo[jb.g]; c <= g_hi[jb.g]; ++c) {
-        const int64_t slot = (int64_t)c * max_seg + (jb.g - cta_gfirst[c]);
-        uint64_t b = lane < k ? partial[(slot * tile_q + jb.ql) * k + lane] : KEY_EMPTY;
-        acc = warp_merge32(acc, b, lane);
+    for (int64_t y = 0; y < sc.b; ++y) {
+        const int64_t wg = sc.g0 + x * sc.b + y;
+        const int64_t cta = M.pair ? 2 * wg + rank : wg;
+        const int64_t slot = cta * M.max_tpx + li;
+        uint64_t v = lane < k ? partial[(slot * k + lane) * TC_TILE_Q + ql] : KEY_EMPTY;
+        acc = warp_merge32(acc, v, lane);
     }
     if (lane < k) {
         jb.out_s[lane] = acc == KEY_EMPTY ? 0xFFFFFFFFu : (uint32_t)(acc >> 32);
@@ -239,14 +263,18 @@ cudaError_t launch_topk_merge_tile(const uint64_t *partial, const Partition &par
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge_jobs(const uint64_t *partial, const MergeJob *jobs, int64_t n_jobs, const int32_t *g_lo,
-                              const int32_t *g_hi, const int32_t *cta_gfirst, int32_t max_seg, int32_t tile_q,
-                              int32_t k, cudaStream_t s) {
+cudaError_t launch_merge_sched(const uint64_t *partial, const TcLaunch &L, const MergeJob *jobs, int64_t n_jobs,
+                               uint32_t *out_scores, int64_t *out_idx, cudaStream_t s) {
     if (n_jobs == 0) return cudaSuccess;
+    MergeSched M;
+    M.n_panels = L.n_panels;
+    M.pair = L.pair;
+    M.max_tpx = L.max_tpx;
+    M.k = L.k;
+    for (int p = 0; p < TC_MAXP; ++p) M.sc[p] = L.sched[p];
     const int wpb = 8;
     int64_t blocks = (n_jobs + wpb - 1) / wpb;
-    topk_merge_jobs_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, jobs, n_jobs, g_lo, g_hi, cta_gfirst,
-                                                                 max_seg, tile_q, k);
+    topk_merge_sched_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, M, jobs, n_jobs, out_scores, out_idx);
     return cudaGetLastError();
 }
 

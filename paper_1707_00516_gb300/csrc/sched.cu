@@ -12,6 +12,10 @@ namespace {
 // (about a third of the 129 MB L2).
 constexpr int64_t L2_CHUNK_BUDGET = 48ll << 20;
 
+// Balance a schedule with one query tile per group may lose before a
+// multi-tile one (with list save / resume) is preferred.
+constexpr double TPX1_SLACK = 1.08;
+
 }  // namespace
 
 int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, const int64_t *unit_cost,
@@ -59,8 +63,11 @@ int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, co
         sc.tpx = 1;
         sc.chunk = 1;
         if (cost[p] <= 0.0) continue;
-        // a x b grid minimising the busiest group's reference tiles.
+        // a x b grid minimising the busiest group's reference tiles; one query
+        // tile per group (nothing to save and resume) wins unless it costs
+        // more than TPX1_SLACK in balance.
         int64_t best_ms = -1, best_a = 1, best_b = 1, best_t = 1;
+        int64_t one_ms = -1, one_a = 1, one_b = 1;
         for (int64_t a = 1; a <= std::min<int64_t>(n_qq[p], gp[p]); ++a) {
             const int64_t tpx = (n_qq[p] + a - 1) / a;
             const int64_t a_eff = (n_qq[p] + tpx - 1) / tpx;
@@ -73,6 +80,17 @@ int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, co
                 best_b = b;
                 best_t = tpx;
             }
+            if (tpx == 1 && (one_ms < 0 || ms < one_ms)) {
+                one_ms = ms;
+                one_a = a_eff;
+                one_b = b;
+            }
+        }
+        if (one_ms > 0 && (double)one_ms <= (double)best_ms * TPX1_SLACK) {
+            best_ms = one_ms;
+            best_a = one_a;
+            best_b = one_b;
+            best_t = 1;
         }
         sc.a = (int32_t)best_a;
         sc.b = (int32_t)best_b;

@@ -49,32 +49,26 @@ struct TcShape {
     static constexpr uint32_t TMEM_COLS = BN == 256 ? 512 : 256;
 };
 
-// One database ("panel") of a launch.  A launch walks the global list of
-// units (panel, query tile, reference tile), panel-major, then query-tile
-// major; panel p's units start at unit_base.
+// One database ("panel") of a launch, with its schedule (TcSched).
 struct PanelDesc {
     int64_t n_refs;
-    int64_t n_q;          // real query rows (the operand is padded to 128)
+    int64_t n_q;          // real query rows (the operand is padded to whole tiles)
     int64_t n_rt;         // reference tiles
-    int64_t unit_base;
     int32_t n_kb;         // K stages of 128 loci
-    int32_t tile_base;    // global id of the panel's first query tile
+    TcSched sc;
     const float *qconst;  // c_q per padded query row
 };
 
 struct TcMaps {
     CUtensorMap a[TC_MAXP];  // query operand of each panel (boxes 128 loci x 128 queries)
-    CUtensorMap b[TC_MAXP];  // reference operand of each panel (boxes 128 loci x BN refs)
+    CUtensorMap b[TC_MAXP];  // reference operand of each panel (boxes 128 loci x BN refs, or BN/2 when paired)
 };
 
 struct TensorArgs {
     int32_t n_panels;
     PanelDesc panel[TC_MAXP];
-    int64_t n_units;
-    int32_t grid;
-    int32_t max_seg;
-    const int64_t *cta_units;  // [grid + 1] unit ranges, or null: CTA c takes [c U / G, (c+1) U / G)
-    uint32_t threshold;        // already clamped to <= N
+    int32_t max_tpx;       // top-k slots per CTA
+    uint32_t threshold;    // already clamped to <= N
     int32_t k;
     int32_t epi;
     void *out;  // EPI_SCORES*: panel 0's [n_q][ld_out]
@@ -84,7 +78,7 @@ struct TensorArgs {
     int64_t *hit_r;
     uint32_t *hit_score;
     unsigned long long *hit_count;
-    uint64_t *partial;  // EPI_TOPK: [grid * max_seg][128][k]
+    uint64_t *partial;  // EPI_TOPK: [ctas * max_tpx][k][128]
     uint32_t *status;
 };
 
@@ -294,24 +288,69 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, uint32
     }
 }
 
-// Unit u of the launch -> panel p, query tile qt, reference tile rt.  In
-// paired launches a unit covers two query tiles (one per CTA of the cluster)
-// and the CTA of cluster rank `rank` takes tile 2 qp + rank.
-template <bool PAIR>
-__device__ __forceinline__ void decode_unit(const TensorArgs &a, int64_t u, int rank, int &p, int64_t &qt,
-                                            int64_t &rt) {
-    p = 0;
+// The work of one group (see TcSched): panel p, reference tiles
+// [r_lo, r_hi) walked in chunks, query tiles (pairs) [q_lo, q_hi).  p < 0:
+// no work.
+struct GroupWork {
+    int p;
+    int64_t r_lo, r_hi;
+    int32_t q_lo, q_hi, chunk;
+};
+
+__device__ __forceinline__ GroupWork group_work(const TensorArgs &a, int64_t wg) {
+    GroupWork w;
+    w.p = -1;
+    w.r_lo = w.r_hi = 0;
+    w.q_lo = w.q_hi = 0;
+    w.chunk = 1;
 #pragma unroll 1
-    while (p + 1 < a.n_panels && u >= a.panel[p + 1].unit_base) ++p;
-    const int64_t local = u - a.panel[p].unit_base;
-    const int64_t qq = local / a.panel[p].n_rt;
-    rt = local - qq * a.panel[p].n_rt;
-    qt = PAIR ? 2 * qq + rank : qq;
+    for (int p = 0; p < a.n_panels; ++p) {
+        const TcSched &sc = a.panel[p].sc;
+        const int64_t rel = wg - sc.g0;
+        if (sc.n_qq > 0 && rel >= 0 && rel < (int64_t)sc.a * sc.b) {
+            const int64_t x = rel / sc.b, y = rel - x * sc.b;
+            const int64_t n_rt = a.panel[p].n_rt;
+            w.p = p;
+            w.r_lo = y * n_rt / sc.b;
+            w.r_hi = (y + 1) * n_rt / sc.b;
+            w.q_lo = (int32_t)(x * sc.tpx);
+            w.q_hi = (int32_t)min((int64_t)sc.n_qq, (x + 1) * sc.tpx);
+            w.chunk = sc.chunk;
+        }
+    }
+    return w;
 }
 
-// PAIR: 2-CTA clusters; both CTAs walk the same reference tiles for two
-// adjacent query tiles, and each multicasts half of every reference stage
-// into both CTAs' shared memory (BN = 256 only).
+// Save / resume one thread's top-k list.  Slot layout [slot][k][128]: entry i
+// of the 128 rows is contiguous, so a warp's accesses coalesce.  Keys
+// ascending, empty entries KEY_EMPTY.
+__device__ __forceinline__ void list_save(uint64_t *slot_row, const int32_t (&ls)[TC_KMAX],
+                                          const uint32_t (&lr)[TC_KMAX], int k) {
+#pragma unroll
+    for (int i = 0; i < TC_KMAX; ++i)
+        if (i >= TC_KMAX - k)
+            slot_row[(int64_t)(i - (TC_KMAX - k)) * TC_BM] =
+                ls[i] == NET_EMPTY ? KEY_EMPTY : make_key((uint32_t)ls[i], lr[i]);
+}
+
+__device__ __forceinline__ void list_load(const uint64_t *slot_row, int32_t (&ls)[TC_KMAX], uint32_t (&lr)[TC_KMAX],
+                                          int k) {
+#pragma unroll
+    for (int i = 0; i < TC_KMAX; ++i) {
+        if (i >= TC_KMAX - k) {
+            const uint64_t key = slot_row[(int64_t)(i - (TC_KMAX - k)) * TC_BM];
+            ls[i] = key == KEY_EMPTY ? NET_EMPTY : (int32_t)(key >> 32);
+            lr[i] = (uint32_t)key;
+        } else {
+            ls[i] = NET_HOLD;
+            lr[i] = 0xFFFFFFFFu;
+        }
+    }
+}
+
+// PAIR: 2-CTA clusters; both CTAs walk the same reference tiles for the two
+// query tiles of a pair (rank r takes tile 2 qq + r), and each multicasts half
+// of every reference stage into both CTAs' shared memory (BN = 256 only).
 template <int BN, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tensor_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TensorArgs args) {
@@ -331,17 +370,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const int64_t c = blockIdx.x;                     // this CTA: owner of partial-list slots
+    const int64_t c = blockIdx.x;                     // this CTA: owner of top-k slots
     const int rank = PAIR ? (int)cluster_rank() : 0;
     const int64_t wg = PAIR ? (c >> 1) : c;            // work group: cluster or CTA
-    int64_t u_begin, u_end;
-    if (args.cta_units) {
-        u_begin = args.cta_units[wg];
-        u_end = args.cta_units[wg + 1];
-    } else {
-        u_begin = (wg * args.n_units) / args.grid;
-        u_end = ((wg + 1) * args.n_units) / args.grid;
-    }
+    const GroupWork W = group_work(args, wg);
     volatile int *abort_flag = &ctl->abort_flag;
 
     if (tid == 0) {
@@ -369,38 +401,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (PAIR) cluster_sync();  // the peer's barriers exist before any multicast targets them
     tc_fence_after();
     const uint32_t tmem_base = ctl->tmem_base;
+    const int p = W.p;
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
-        if (lane == 0) {
-            for (int p = 0; p < args.n_panels; ++p) {
-                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[p])) : "memory");
-                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[p])) : "memory");
-            }
+        if (lane == 0 && p >= 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[p])) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[p])) : "memory");
+            const int n_kb = args.panel[p].n_kb;
             int stage = 0;
             uint32_t phase = 0;
             int64_t issued = 0;
             bool ok = true;
-            for (int64_t u = u_begin; u < u_end && ok; ++u) {
-                int p;
-                int64_t qt, rt;
-                decode_unit<PAIR>(args, u, rank, p, qt, rt);
-                const int n_kb = args.panel[p].n_kb;
-                for (int kb = 0; kb < n_kb; ++kb) {
-                    ok = mbar_wait(smem_u32(&ctl->empty[stage]), phase ^ 1u, abort_flag, args.status, 1);
-                    if (!ok) break;
-                    const uint32_t fb = smem_u32(&ctl->full[stage]);
-                    mbar_expect_tx(fb, TC_A_BYTES + S::B_BYTES);
-                    tma_load_2d(smem_u32(sA + stage * TC_A_BYTES), &maps.a[p], fb, kb * TC_BK, (int32_t)(qt * TC_BM));
-                    if (PAIR)
-                        tma_load_2d_mc(smem_u32(sB + stage * S::B_BYTES + rank * (S::B_BYTES / 2)), &maps.b[p], fb,
-                                       kb * TC_BK, (int32_t)(rt * BN + rank * (BN / 2)), (uint16_t)0x3);
-                    else
-                        tma_load_2d(smem_u32(sB + stage * S::B_BYTES), &maps.b[p], fb, kb * TC_BK, (int32_t)(rt * BN));
-                    ++issued;
-                    if (++stage == S::STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
+            for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
+                const int64_t re = min(rc + W.chunk, W.r_hi);
+                for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
+                    const int64_t qt = PAIR ? 2 * (int64_t)qq + rank : qq;
+                    for (int64_t rt = rc; rt < re && ok; ++rt) {
+                        for (int kb = 0; kb < n_kb; ++kb) {
+                            ok = mbar_wait(smem_u32(&ctl->empty[stage]), phase ^ 1u, abort_flag, args.status, 1);
+                            if (!ok) break;
+                            const uint32_t fb = smem_u32(&ctl->full[stage]);
+                            mbar_expect_tx(fb, TC_A_BYTES + S::B_BYTES);
+                            tma_load_2d(smem_u32(sA + stage * TC_A_BYTES), &maps.a[p], fb, kb * TC_BK,
+                                        (int32_t)(qt * TC_BM));
+                            if (PAIR)
+                                tma_load_2d_mc(smem_u32(sB + stage * S::B_BYTES + rank * (S::B_BYTES / 2)),
+                                               &maps.b[p], fb, kb * TC_BK, (int32_t)(rt * BN + rank * (BN / 2)),
+                                               (uint16_t)0x3);
+                            else
+                                tma_load_2d(smem_u32(sB + stage * S::B_BYTES), &maps.b[p], fb, kb * TC_BK,
+                                            (int32_t)(rt * BN));
+                            ++issued;
+                            if (++stage == S::STAGES) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
                     }
                 }
             }
@@ -416,171 +453,161 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
-        if (lane == 0) {
+        if (lane == 0 && p >= 0) {
             constexpr uint32_t idesc = idesc_f8(TC_BM, BN);
+            const int n_kb = args.panel[p].n_kb;
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (int64_t u = u_begin; u < u_end && ok; ++u) {
-                int p;
-                int64_t qt, rt;
-                decode_unit<PAIR>(args, u, rank, p, qt, rt);
-                const int n_kb = args.panel[p].n_kb;
-                ok = mbar_wait(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, abort_flag, args.status, 3);
-                if (!ok) break;
-                tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-                for (int kb = 0; kb < n_kb; ++kb) {
-                    ok = mbar_wait(smem_u32(&ctl->full[stage]), phase, abort_flag, args.status, 4);
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint64_t ad = sw128_desc(smem_u32(sA + stage * TC_A_BYTES));
-                    const uint64_t bd = sw128_desc(smem_u32(sB + stage * S::B_BYTES));
+            for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
+                const int64_t re = min(rc + W.chunk, W.r_hi);
+                for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
+                    for (int64_t rt = rc; rt < re && ok; ++rt) {
+                        ok = mbar_wait(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, abort_flag, args.status, 3);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+                        for (int kb = 0; kb < n_kb; ++kb) {
+                            ok = mbar_wait(smem_u32(&ctl->full[stage]), phase, abort_flag, args.status, 4);
+                            if (!ok) break;
+                            tc_fence_after();
+                            const uint64_t ad = sw128_desc(smem_u32(sA + stage * TC_A_BYTES));
+                            const uint64_t bd = sw128_desc(smem_u32(sB + stage * S::B_BYTES));
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 32; ++kk)  // K = 32 FP8 per MMA: +32 bytes = +2 in the address field
-                        tc_mma_f8(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
-                    if (PAIR)
-                        tc_commit_mc(smem_u32(&ctl->empty[stage]), (uint16_t)0x3);
-                    else
-                        tc_commit(smem_u32(&ctl->empty[stage]));
-                    if (++stage == S::STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
+                            for (int kk = 0; kk < TC_BK / 32; ++kk)  // K = 32 FP8 per MMA: +32 bytes = +2 in the address field
+                                tc_mma_f8(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
+                            if (PAIR)
+                                tc_commit_mc(smem_u32(&ctl->empty[stage]), (uint16_t)0x3);
+                            else
+                                tc_commit(smem_u32(&ctl->empty[stage]));
+                            if (++stage == S::STAGES) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                        if (!ok) break;
+                        tc_commit(smem_u32(&ctl->tfull[acc]));
+                        if (++acc == 2) {
+                            acc = 0;
+                            acc_phase ^= 1u;
+                        }
                     }
-                }
-                if (!ok) break;
-                tc_commit(smem_u32(&ctl->tfull[acc]));
-                if (++acc == 2) {
-                    acc = 0;
-                    acc_phase ^= 1u;
                 }
             }
             // Drain: a commit completes after every MMA this thread issued.
             tc_commit(smem_u32(&ctl->done));
             mbar_drain(smem_u32(&ctl->done), 0, args.status, 5);
         }
-    } else {
+    } else if (p >= 0) {
         // ---------------- epilogue: warps 2..5 ----------------
         const int quad = warp & 3;            // TMEM lane quadrant this warp may access
         const int row = quad * 32 + lane;     // query row within the tile
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         const float tplus1 = args.threshold == 0xFFFFFFFFu ? __int_as_float(0x7f800000) : (float)args.threshold + 1.0f;
         const int k = args.k;
+        const int64_t n_refs = args.panel[p].n_refs;
+        const bool topk = args.epi == EPI_TOPK;
         int acc = 0;
         uint32_t acc_phase = 0;
-        int64_t g_prev = -1;  // global query-tile id of the current segment
-        int seg = 0;
         int32_t ls[TC_KMAX];  // this thread's top-k scores (see net_insert)
         uint32_t lr[TC_KMAX]; // and their references
-        float cq = 0.f;    // c_q
-        float cut = 0.f;   // D must be < cut to be a candidate
-        float cut0 = 0.f;  // cut while the list is not full
-        bool qvalid = false;
-        int64_t q = 0, n_refs = 0;
-        for (int64_t u = u_begin; u < u_end; ++u) {
-            int p;
-            int64_t qt, rt;
-            decode_unit<PAIR>(args, u, rank, p, qt, rt);
-            const int64_t g = args.panel[p].tile_base + qt;
-            if (g != g_prev) {
-                if (args.epi == EPI_TOPK && g_prev >= 0) {
-                    uint64_t *dst = args.partial + ((c * args.max_seg + seg) * TC_BM + row) * (int64_t)k;
+        bool ok = true;
+        for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
+            const int64_t re = min(rc + W.chunk, W.r_hi);
+            for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
+                const int64_t qt = PAIR ? 2 * (int64_t)qq + rank : qq;
+                const int64_t q = qt * TC_BM + row;
+                const bool qvalid = q < args.panel[p].n_q;
+                const float cq = args.panel[p].qconst[q];
+                const float cut0 = qvalid ? tplus1 - cq : -__int_as_float(0x7f800000);
+                uint64_t *slot = args.partial + (c * args.max_tpx + (qq - W.q_lo)) * (int64_t)k * TC_BM + row;
+                if (topk && rc > W.r_lo) {
+                    list_load(slot, ls, lr, k);
+                } else {
 #pragma unroll
-                    for (int i = 0; i < TC_KMAX; ++i)
-                        if (i >= TC_KMAX - k)
-                            dst[i - (TC_KMAX - k)] = ls[i] == NET_EMPTY ? KEY_EMPTY : make_key((uint32_t)ls[i], lr[i]);
-                    ++seg;
+                    for (int i = 0; i < TC_KMAX; ++i) {
+                        ls[i] = i < TC_KMAX - k ? NET_HOLD : NET_EMPTY;
+                        lr[i] = 0xFFFFFFFFu;
+                    }
                 }
-                g_prev = g;
-                q = qt * TC_BM + row;
-                qvalid = q < args.panel[p].n_q;
-                n_refs = args.panel[p].n_refs;
-                cq = args.panel[p].qconst[q];
-#pragma unroll
-                for (int i = 0; i < TC_KMAX; ++i) {
-                    ls[i] = i < TC_KMAX - k ? NET_HOLD : NET_EMPTY;
-                    lr[i] = 0xFFFFFFFFu;
-                }
-                cut0 = qvalid ? tplus1 - cq : -__int_as_float(0x7f800000);
-                cut = cut0;
-            }
-            const bool got = mbar_wait(smem_u32(&ctl->tfull[acc]), acc_phase, abort_flag, args.status, 6);
-            __syncwarp();
-            if (!__all_sync(0xffffffffu, got)) break;
-            tc_fence_after();
-            const int64_t r0 = rt * BN;
-            const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * BN);
+                float cut = ls[TC_KMAX - 1] == NET_EMPTY ? cut0 : (float)ls[TC_KMAX - 1] - cq;
+                for (int64_t rt = rc; rt < re; ++rt) {
+                    const bool got = mbar_wait(smem_u32(&ctl->tfull[acc]), acc_phase, abort_flag, args.status, 6);
+                    __syncwarp();
+                    if (!__all_sync(0xffffffffu, got)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int64_t r0 = rt * BN;
+                    const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * BN);
 #pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ++ch) {
-                uint32_t v[32];
-                __syncwarp();  // tcgen05.ld is warp-collective: reconverge first
-                tmem_ld32(taddr + ch * 32, v);
-                if (ch == BN / 32 - 1) {
-                    tc_fence_before();
-                    mbar_arrive(smem_u32(&ctl->tempty[acc]));
-                }
-                const int64_t rc = r0 + ch * 32;
-                if (args.epi == EPI_SCORES16 || args.epi == EPI_SCORES32) {
-                    if (qvalid) {
+                    for (int ch = 0; ch < BN / 32; ++ch) {
+                        uint32_t v[32];
+                        __syncwarp();  // tcgen05.ld is warp-collective: reconverge first
+                        tmem_ld32(taddr + ch * 32, v);
+                        if (ch == BN / 32 - 1) {
+                            tc_fence_before();
+                            mbar_arrive(smem_u32(&ctl->tempty[acc]));
+                        }
+                        const int64_t rch = r0 + ch * 32;
+                        if (args.epi == EPI_SCORES16 || args.epi == EPI_SCORES32) {
+                            if (qvalid) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int64_t r = rc + j;
-                            if (r < n_refs) {
-                                const uint32_t sc = (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq);
-                                if (args.epi == EPI_SCORES16)
-                                    reinterpret_cast<uint16_t *>(args.out)[q * args.ld_out + r] = (uint16_t)sc;
-                                else
-                                    reinterpret_cast<uint32_t *>(args.out)[q * args.ld_out + r] = sc;
+                                for (int j = 0; j < 32; ++j) {
+                                    const int64_t r = rch + j;
+                                    if (r < n_refs) {
+                                        const uint32_t sc = (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq);
+                                        if (args.epi == EPI_SCORES16)
+                                            reinterpret_cast<uint16_t *>(args.out)[q * args.ld_out + r] = (uint16_t)sc;
+                                        else
+                                            reinterpret_cast<uint32_t *>(args.out)[q * args.ld_out + r] = sc;
+                                    }
+                                }
                             }
+                            continue;
+                        }
+                        uint32_t m = 0;  // columns of this chunk that pass the filter
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) m |= (uint32_t)(__uint_as_float(v[j]) < cut) << j;
+                        if (rch + 32 > n_refs) m &= rch >= n_refs ? 0u : ((1u << (n_refs - rch)) - 1u);
+                        if (!__any_sync(0xffffffffu, m != 0u)) continue;
+                        if (args.epi == EPI_HITS) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (m & (1u << j))
+                                    append_hit(args.hit_count, args.capacity, args.hit_q, args.hit_r, args.hit_score,
+                                               q, rch + j, (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq));
+                            continue;
+                        }
+                        // rare path: stage the chunk, then insert candidates in lock-step
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) stage_v[j * TC_BM + row] = __uint_as_float(v[j]);
+                        while (__any_sync(0xffffffffu, m != 0u)) {
+                            int32_t xs = NET_EMPTY;
+                            uint32_t xr = 0u;
+                            if (m != 0u) {
+                                const int j = __ffs(m) - 1;
+                                m &= m - 1u;
+                                const float d = stage_v[j * TC_BM + row];
+                                if (d < cut) {
+                                    xs = (int32_t)(d + cq);
+                                    xr = (uint32_t)(rch + j);
+                                }
+                            }
+                            net_insert(ls, lr, xs, xr);
+                            cut = ls[TC_KMAX - 1] == NET_EMPTY ? cut0 : (float)ls[TC_KMAX - 1] - cq;
                         }
                     }
-                    continue;
-                }
-                uint32_t m = 0;  // columns of this chunk that pass the filter
-#pragma unroll
-                for (int j = 0; j < 32; ++j) m |= (uint32_t)(__uint_as_float(v[j]) < cut) << j;
-                if (rc + 32 > n_refs) m &= rc >= n_refs ? 0u : ((1u << (n_refs - rc)) - 1u);
-                if (!__any_sync(0xffffffffu, m != 0u)) continue;
-                if (args.epi == EPI_HITS) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (m & (1u << j))
-                            append_hit(args.hit_count, args.capacity, args.hit_q, args.hit_r, args.hit_score, q,
-                                       rc + j, (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq));
-                    continue;
-                }
-                // rare path: stage the chunk, then insert candidates in lock-step
-#pragma unroll
-                for (int j = 0; j < 32; ++j) stage_v[j * TC_BM + row] = __uint_as_float(v[j]);
-                while (__any_sync(0xffffffffu, m != 0u)) {
-                    int32_t xs = NET_EMPTY;
-                    uint32_t xr = 0u;
-                    if (m != 0u) {
-                        const int j = __ffs(m) - 1;
-                        m &= m - 1u;
-                        const float d = stage_v[j * TC_BM + row];
-                        if (d < cut) {
-                            xs = (int32_t)(d + cq);
-                            xr = (uint32_t)(rc + j);
-                        }
+                    if (++acc == 2) {
+                        acc = 0;
+                        acc_phase ^= 1u;
                     }
-                    net_insert(ls, lr, xs, xr);
-                    cut = ls[TC_KMAX - 1] == NET_EMPTY ? cut0 : (float)ls[TC_KMAX - 1] - cq;
                 }
+                if (topk && ok) list_save(slot, ls, lr, k);
             }
-            if (++acc == 2) {
-                acc = 0;
-                acc_phase ^= 1u;
-            }
-        }
-        if (args.epi == EPI_TOPK && g_prev >= 0 && !*abort_flag) {
-            uint64_t *dst = args.partial + ((c * args.max_seg + seg) * TC_BM + row) * (int64_t)k;
-#pragma unroll
-            for (int i = 0; i < TC_KMAX; ++i)
-                if (i >= TC_KMAX - k)
-                    dst[i - (TC_KMAX - k)] = ls[i] == NET_EMPTY ? KEY_EMPTY : make_key((uint32_t)ls[i], lr[i]);
         }
     }
 
@@ -795,6 +822,7 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
     memset(&maps, 0, sizeof maps);
     memset(&a, 0, sizeof a);
     if (L.n_panels < 1 || L.n_panels > TC_MAXP) return cudaErrorInvalidValue;
+    if (L.n_groups < 1) return cudaSuccess;
     a.n_panels = L.n_panels;
     for (int p = 0; p < L.n_panels; ++p) {
         maps.a[p] = L.map_a[p];
@@ -802,15 +830,11 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
         a.panel[p].n_refs = L.n_refs[p];
         a.panel[p].n_q = L.n_q[p];
         a.panel[p].n_rt = L.n_rt[p];
-        a.panel[p].unit_base = L.unit_base[p];
         a.panel[p].n_kb = L.kpad[p] / TC_BK;
-        a.panel[p].tile_base = L.tile_base[p];
+        a.panel[p].sc = L.sched[p];
         a.panel[p].qconst = L.qconst[p];
     }
-    a.n_units = L.n_units;
-    a.grid = L.grid;
-    a.max_seg = L.max_seg;
-    a.cta_units = L.cta_units;
+    a.max_tpx = L.max_tpx;
     a.threshold = L.threshold;
     a.k = L.k;
     a.epi = L.epi;
@@ -831,7 +855,7 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg;
         memset(&cfg, 0, sizeof cfg);
-        cfg.gridDim = dim3(2 * L.grid);
+        cfg.gridDim = dim3(2 * L.n_groups);
         cfg.blockDim = dim3(TC_THREADS);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = s;
@@ -848,52 +872,14 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
         size_t smem = tensor_smem<128>(L.epi);
         e = cudaFuncSetAttribute(tensor_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        tensor_kernel<128, false><<<L.grid, TC_THREADS, smem, s>>>(maps, a);
+        tensor_kernel<128, false><<<L.n_groups, TC_THREADS, smem, s>>>(maps, a);
     } else {
         size_t smem = tensor_smem<256>(L.epi);
         e = cudaFuncSetAttribute(tensor_kernel<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        tensor_kernel<256, false><<<L.grid, TC_THREADS, smem, s>>>(maps, a);
+        tensor_kernel<256, false><<<L.n_groups, TC_THREADS, smem, s>>>(maps, a);
     }
     return cudaGetLastError();
-}
-
-cudaError_t launch_tensor(int epi, int pair, const CUtensorMap &map_a, const CUtensorMap &map_b, int64_t n_refs,
-                          int64_t n_q,
-                          int32_t kpad, const float *qconst, uint32_t threshold, int32_t k, void *out,
-                          int64_t ld_out, int64_t capacity, int64_t *hit_q, int64_t *hit_r, uint32_t *hit_score,
-                          unsigned long long *hit_count, uint64_t *partial, const Partition &part, uint32_t *status,
-                          cudaStream_t s) {
-    TcLaunch L;
-    memset(&L, 0, sizeof L);
-    L.n_panels = 1;
-    L.pair = pair;
-    L.map_a[0] = map_a;
-    L.map_b[0] = map_b;
-    L.n_refs[0] = n_refs;
-    L.n_q[0] = n_q;
-    L.n_rt[0] = part.n_rt;
-    L.unit_base[0] = 0;
-    L.kpad[0] = kpad;
-    L.tile_base[0] = 0;
-    L.qconst[0] = qconst;
-    L.n_units = part.n_units;
-    L.grid = part.grid;
-    L.max_seg = part.max_seg;
-    L.cta_units = nullptr;
-    L.threshold = threshold;
-    L.k = k;
-    L.epi = epi;
-    L.out = out;
-    L.ld_out = ld_out;
-    L.capacity = capacity;
-    L.hit_q = hit_q;
-    L.hit_r = hit_r;
-    L.hit_score = hit_score;
-    L.hit_count = hit_count;
-    L.partial = partial;
-    L.status = status;
-    return launch_tensor_multi(256, L, s);
 }
 
 }  // namespace fastid

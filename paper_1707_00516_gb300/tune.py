@@ -16,7 +16,7 @@ import torch
 
 from . import binding as B
 
-CANDIDATES = (B.VARIANT_TENSOR_N256, B.VARIANT_TENSOR_N128)
+CANDIDATES = (B.VARIANT_TENSOR_N256, B.VARIANT_TENSOR_N128, B.VARIANT_TENSOR_PAIR)
 
 
 def _bucket(n: int) -> int:
