@@ -439,13 +439,13 @@ fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint
     const int64_t n_q_pad = round_up(n_q, (int64_t)tensor_tile_q() * (L.pair ? 2 : 1));
     const int64_t n_qq = n_q_pad / tensor_tile_q() / (L.pair ? 2 : 1);
     const int64_t n_rt = db->n_pad / tensor_tile_r();
-    const int64_t n_kb = db->kpad / 128;
     const int64_t tile_bytes = (int64_t)tensor_tile_r() * db->kpad;
-    L.n_groups = make_tensor_schedule(1, &n_qq, &n_rt, &n_kb, &tile_bytes,
-                                      L.pair ? ctx->pair_clusters : ctx->grid_tensor, L.sched, &L.max_tpx);
+    L.n_groups = make_tensor_schedule(1, &n_qq, &n_rt, &tile_bytes, L.pair ? ctx->pair_clusters : ctx->grid_tensor,
+                                      L.pair ? 2 : 1, L.sched, L.order, &L.n_slots);
+    if (L.n_groups < 0) return fail(ctx, FASTID_EINVAL, "too many query tiles (top-k slots)");
     tp->n_ctas = (int64_t)L.n_groups * (L.pair ? 2 : 1);
     size_t extra = 0;
-    if (ek == EXTRA_TOPK) extra = (size_t)tp->n_ctas * L.max_tpx * tensor_tile_q() * (size_t)karg * 8;
+    if (ek == EXTRA_TOPK) extra = (size_t)L.n_slots * tensor_tile_q() * (size_t)karg * 8;
     if (ek == EXTRA_HITS) extra = 256 + (size_t)(2 + hits_sort_elems(karg) * 3 / 2 + 1) * 8;
     Carver cv;
     size_t o_a = cv.take<uint8_t>((size_t)n_q_pad * db->kpad);

@@ -94,12 +94,17 @@ struct MergeJob {
 // [y n_rt / b, (y+1) n_rt / b).  A group walks its slice in chunks of
 // `chunk` tiles and, inside a chunk, each of its query tiles in turn, so the
 // groups of a slice read the same reference chunk at about the same time (it
-// is fetched from DRAM once and served from L2 to the others).  Each (group,
-// query tile) keeps its running top-k in a slot of the partial buffer,
-// saved after every chunk and resumed at the next.
+// is fetched from DRAM once and served from L2 to the others).  Each (CTA,
+// query tile) keeps its running top-k in a slot of the partial buffer, saved
+// after every chunk and resumed at the next; the panel's slots start at
+// slot0 and CTA c's tile i is slot slot0 + c tpx + i.
+// Panels run one after another: every panel's grid is laid over the same
+// work groups (group g of panel p is group g of the launch), and each group
+// walks its share of every panel in the launch's panel order (largest first),
+// so the L2 serves one panel's working set at a time.
 struct TcSched {
     int32_t n_qq;   // query tiles, or tile pairs when paired
-    int32_t g0;     // first work group of the panel
+    int32_t slot0;  // first top-k slot of the panel
     int32_t a, b;   // tile groups x reference slices
     int32_t tpx;    // query tiles (pairs) per tile group
     int32_t chunk;  // reference tiles per chunk
@@ -117,8 +122,9 @@ struct TcLaunch {
     int32_t kpad[TC_MAXP];
     const float *qconst[TC_MAXP];
     TcSched sched[TC_MAXP];
-    int32_t n_groups;  // sum of a * b over panels
-    int32_t max_tpx;   // slots per CTA
+    int32_t order[TC_MAXP];  // panel order of every group's walk
+    int32_t n_groups;  // work groups of the launch: max of a * b over panels
+    int32_t n_slots;   // top-k slots over all panels
     uint32_t threshold;
     int32_t k;
     int32_t epi;
@@ -129,15 +135,20 @@ struct TcLaunch {
     int64_t *hit_r;
     uint32_t *hit_score;
     unsigned long long *hit_count;
-    uint64_t *partial;  // EPI_TOPK: [ctas * max_tpx][k][128]
+    uint64_t *partial;  // EPI_TOPK: [n_slots][k][128]
     uint32_t *status;
+    // Panel-entry counters, one per position of the panel order (zero before
+    // the launch), or nullptr: see the rendezvous in the tensor kernel.
+    unsigned int *arrive;
 };
 
-// Fills sched[] for n panels and G work groups; returns the number of groups
-// used (sum of a * b) and sets *max_tpx.  unit_cost: K stages of a unit;
-// tile_bytes: bytes of one reference tile of the operand.
-int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, const int64_t *unit_cost,
-                             const int64_t *tile_bytes, int32_t G, TcSched *sched, int32_t *max_tpx);
+// Fills sched[] and order[] for n panels, each over (up to) G work groups of
+// `ctas_per_group` CTAs; returns the number of groups the launch needs (max
+// of a * b; -1: too many top-k slots) and sets *n_slots.  tile_bytes: bytes
+// of one reference tile of the operand.
+int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, const int64_t *tile_bytes,
+                             int32_t G, int32_t ctas_per_group, TcSched *sched, int32_t *order,
+                             int32_t *n_slots);
 
 // Top-k keys: (score << 32) | ref, so that ordering keys orders by score then
 // by reference index.  An empty slot holds KEY_EMPTY.

@@ -40,6 +40,7 @@ struct fastid_plan {
     PrepJob *prep = nullptr;
     MergeJob *merge = nullptr;
     uint64_t *partial = nullptr;
+    unsigned int *arrive = nullptr;  // panel-entry counters of the compare launch
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
 };
@@ -118,20 +119,24 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     // Rows of each panel's operand: its batches' queries, in batch order.
     std::vector<int64_t> rows(n_panels, 0);
     for (int b = 0; b < n_batches; ++b) rows[batches[b].panel] += batches[b].n_q;
-    std::vector<int64_t> rows_pad(n_panels), n_qq(n_panels), n_rt(n_panels), n_kb(n_panels), tile_bytes(n_panels);
+    std::vector<int64_t> rows_pad(n_panels), n_qq(n_panels), n_rt(n_panels), tile_bytes(n_panels);
     for (int p = 0; p < n_panels; ++p) {
         rows_pad[p] = rup(std::max<int64_t>(rows[p], 1), tq);
         n_qq[p] = rows[p] > 0 ? rows_pad[p] / tq : 0;
         n_rt[p] = dbs[p]->n_pad / BN;
-        n_kb[p] = dbs[p]->kpad / 128;
         tile_bytes[p] = (int64_t)BN * dbs[p]->kpad;
         P->n_queries += rows[p];
     }
     TcLaunch &L = P->launch;
     memset(&L, 0, sizeof L);
     L.pair = pair;
-    L.n_groups = make_tensor_schedule(n_panels, n_qq.data(), n_rt.data(), n_kb.data(), tile_bytes.data(),
-                                      pair ? ctx->pair_clusters : ctx->grid_tensor, L.sched, &L.max_tpx);
+    L.n_groups = make_tensor_schedule(n_panels, n_qq.data(), n_rt.data(), tile_bytes.data(),
+                                      pair ? ctx->pair_clusters : ctx->grid_tensor, pair ? 2 : 1, L.sched,
+                                      L.order, &L.n_slots);
+    if (L.n_groups < 0) {
+        free_plan(P);
+        return perr(ctx, FASTID_EINVAL, "plan too large (top-k slots)");
+    }
     P->n_ctas = (int64_t)L.n_groups * (pair ? 2 : 1);
 
     // Workspace layout.
@@ -151,7 +156,8 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     }
     const size_t o_prep = take((size_t)n_prep * sizeof(PrepJob));
     const size_t o_merge = take((size_t)std::max<int64_t>(P->n_queries, 1) * sizeof(MergeJob));
-    const size_t o_part = take((size_t)std::max<int64_t>(P->n_ctas, 1) * L.max_tpx * TC_TILE_Q * k * sizeof(uint64_t));
+    const size_t o_part = take((size_t)std::max<int32_t>(L.n_slots, 1) * TC_TILE_Q * k * sizeof(uint64_t));
+    const size_t o_arrive = take(TC_MAXP * sizeof(unsigned int));
     e = cudaMalloc(&P->work, off);
     if (e != cudaSuccess) {
         free_plan(P);
@@ -162,6 +168,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     P->prep = reinterpret_cast<PrepJob *>(W + o_prep);
     P->merge = reinterpret_cast<MergeJob *>(W + o_merge);
     P->partial = reinterpret_cast<uint64_t *>(W + o_part);
+    P->arrive = reinterpret_cast<unsigned int *>(W + o_arrive);
 
     // Host tables.
     std::vector<PrepJob> prep(n_prep);
@@ -230,6 +237,9 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     L.epi = EPI_TOPK;
     L.partial = P->partial;
     L.status = ctx->dev_status;
+    int busy = 0;
+    for (int p = 0; p < n_panels; ++p) busy += n_qq[p] > 0;
+    L.arrive = busy > 1 ? P->arrive : nullptr;
     // Scores never exceed a panel's loci count; clamp so T + 1 stays exact in FP32.
     L.threshold = threshold;
     if (threshold != 0xFFFFFFFFu) {
@@ -250,6 +260,10 @@ fastid_status fastid_plan_run(fastid_plan *plan, fastid_stream stream) {
     if (plan->n_queries == 0) return FASTID_OK;
     e = launch_prep_jobs(plan->prep, plan->n_jobs_prep, s);
     if (e != cudaSuccess) return pcuda(ctx, e, "batched operand preparation");
+    if (plan->launch.arrive) {
+        e = cudaMemsetAsync(plan->launch.arrive, 0, TC_MAXP * sizeof(unsigned int), s);
+        if (e != cudaSuccess) return pcuda(ctx, e, "panel counters");
+    }
     e = launch_tensor_multi(plan->bn, plan->launch, s);
     if (e != cudaSuccess) return pcuda(ctx, e, "batched compare launch");
     e = launch_merge_sched(plan->partial, plan->launch, plan->merge, plan->n_jobs_merge, nullptr, nullptr, s);

@@ -72,7 +72,6 @@ __global__ void topk_merge_kernel(const uint64_t *__restrict__ partial, Partitio
 struct MergeSched {
     int32_t n_panels;
     int32_t pair;
-    int32_t max_tpx;
     int32_t k;
     TcSched sc[TC_MAXP];
 };
@@ -100,9 +99,9 @@ __global__ void topk_merge_sched_kernel(const uint64_t *__restrict__ partial, co
     const int64_t x = qq / sc.tpx, li = qq - x * sc.tpx;
     uint64_t acc = KEY_EMPTY;
     for (int64_t y = 0; y < sc.b; ++y) {
-        const int64_t wg = sc.g0 + x * sc.b + y;
+        const int64_t wg = x * sc.b + y;
         const int64_t cta = M.pair ? 2 * wg + rank : wg;
-        const int64_t slot = cta * M.max_tpx + li;
+        const int64_t slot = (int64_t)sc.slot0 + cta * sc.tpx + li;
         uint64_t v = lane < k ? partial[(slot * k + lane) * TC_TILE_Q + ql] : KEY_EMPTY;
         acc = warp_merge32(acc, v, lane);
     }
@@ -269,7 +268,6 @@ cudaError_t launch_merge_sched(const uint64_t *partial, const TcLaunch &L, const
     MergeSched M;
     M.n_panels = L.n_panels;
     M.pair = L.pair;
-    M.max_tpx = L.max_tpx;
     M.k = L.k;
     for (int p = 0; p < TC_MAXP; ++p) M.sc[p] = L.sched[p];
     const int wpb = 8;

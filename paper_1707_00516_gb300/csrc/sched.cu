@@ -1,5 +1,6 @@
 // Host-side work schedule of a tensor-form launch (see TcSched in common.cuh).
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "common.cuh"
@@ -12,85 +13,47 @@ namespace {
 // (about a third of the 129 MB L2).
 constexpr int64_t L2_CHUNK_BUDGET = 48ll << 20;
 
-// Balance a schedule with one query tile per group may lose before a
-// multi-tile one (with list save / resume) is preferred.
-constexpr double TPX1_SLACK = 1.08;
+// Relative cost of a reference tile for a group with several query tiles
+// (chunks re-read from L2, top-k lists saved and resumed, no prefetch) over
+// one with a single query tile, which streams its slice once with the next
+// tile prefetched: 1 + TPX_PENALTY + SLICE_PENALTY * b.  Fit to sweeps of
+// a x b grids on GB300 at N = 512 .. 16384 (4M references, 15 .. 21 query
+// tile pairs, and 2048 queries x 20M references).
+constexpr double TPX_PENALTY = 0.08;
+constexpr double SLICE_PENALTY = 0.005;
 
 }  // namespace
 
-int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, const int64_t *unit_cost,
-                             const int64_t *tile_bytes, int32_t G, TcSched *sched, int32_t *max_tpx) {
-    std::vector<double> cost(n, 0.0);
-    double total = 0.0;
-    for (int p = 0; p < n; ++p) {
-        cost[p] = (double)n_qq[p] * (double)n_rt[p] * (double)unit_cost[p];
-        total += cost[p];
-    }
-    // Groups per panel, proportional to cost (at least one per busy panel).
-    std::vector<int64_t> gp(n, 0);
-    int64_t used = 0;
-    for (int p = 0; p < n; ++p) {
-        if (cost[p] <= 0.0) continue;
-        gp[p] = std::max<int64_t>(1, (int64_t)((double)G * cost[p] / total));
-        used += gp[p];
-    }
-    while (used > G) {  // shrink the largest share
-        int q = -1;
-        for (int p = 0; p < n; ++p)
-            if (gp[p] > 1 && (q < 0 || gp[p] > gp[q])) q = p;
-        if (q < 0) break;
-        --gp[q];
-        --used;
-    }
-    while (used < G && total > 0.0) {  // grow the most loaded panel
-        int q = -1;
-        double worst = -1.0;
-        for (int p = 0; p < n; ++p)
-            if (cost[p] > 0.0 && cost[p] / (double)gp[p] > worst) {
-                worst = cost[p] / (double)gp[p];
-                q = p;
-            }
-        ++gp[q];
-        ++used;
-    }
-
-    int32_t g0 = 0, mt = 1;
+int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, const int64_t *tile_bytes,
+                             int32_t G, int32_t ctas_per_group, TcSched *sched, int32_t *order,
+                             int32_t *n_slots) {
+    int64_t slots = 0;
+    int32_t groups = 0;
     for (int p = 0; p < n; ++p) {
         TcSched &sc = sched[p];
         sc.n_qq = (int32_t)n_qq[p];
-        sc.g0 = g0;
+        sc.slot0 = (int32_t)slots;
         sc.a = sc.b = 0;
         sc.tpx = 1;
         sc.chunk = 1;
-        if (cost[p] <= 0.0) continue;
-        // a x b grid minimising the busiest group's reference tiles; one query
-        // tile per group (nothing to save and resume) wins unless it costs
-        // more than TPX1_SLACK in balance.
-        int64_t best_ms = -1, best_a = 1, best_b = 1, best_t = 1;
-        int64_t one_ms = -1, one_a = 1, one_b = 1;
-        for (int64_t a = 1; a <= std::min<int64_t>(n_qq[p], gp[p]); ++a) {
+        if (n_qq[p] <= 0 || n_rt[p] <= 0) continue;
+        // a x b grid minimising the busiest group's cost: its reference
+        // tiles, weighted as above when it holds several query tiles.
+        double best = -1.0;
+        int64_t best_a = 1, best_b = 1, best_t = 1;
+        for (int64_t a = 1; a <= std::min<int64_t>(n_qq[p], G); ++a) {
             const int64_t tpx = (n_qq[p] + a - 1) / a;
             const int64_t a_eff = (n_qq[p] + tpx - 1) / tpx;
-            const int64_t b = std::min<int64_t>(gp[p] / a_eff, n_rt[p]);
+            const int64_t b = std::min<int64_t>(G / a_eff, n_rt[p]);
             if (b < 1) continue;
-            const int64_t ms = tpx * ((n_rt[p] + b - 1) / b);
-            if (best_ms < 0 || ms < best_ms || (ms == best_ms && tpx < best_t)) {
-                best_ms = ms;
+            const double tiles = (double)(tpx * ((n_rt[p] + b - 1) / b));
+            const double cost = tpx == 1 ? tiles : tiles * (1.0 + TPX_PENALTY + SLICE_PENALTY * (double)b);
+            if (best < 0.0 || cost < best) {
+                best = cost;
                 best_a = a_eff;
                 best_b = b;
                 best_t = tpx;
             }
-            if (tpx == 1 && (one_ms < 0 || ms < one_ms)) {
-                one_ms = ms;
-                one_a = a_eff;
-                one_b = b;
-            }
-        }
-        if (one_ms > 0 && (double)one_ms <= (double)best_ms * TPX1_SLACK) {
-            best_ms = one_ms;
-            best_a = one_a;
-            best_b = one_b;
-            best_t = 1;
         }
         sc.a = (int32_t)best_a;
         sc.b = (int32_t)best_b;
@@ -99,15 +62,24 @@ int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, co
         if (best_t == 1) {
             sc.chunk = (int32_t)std::max<int64_t>(1, slice);  // one segment per slice: nothing to resume
         } else {
-            const int64_t budget = L2_CHUNK_BUDGET * gp[p] / std::max<int64_t>(1, G);
-            const int64_t c = budget / std::max<int64_t>(1, best_b * tile_bytes[p]);
+            const int64_t c = L2_CHUNK_BUDGET / std::max<int64_t>(1, best_b * tile_bytes[p]);
             sc.chunk = (int32_t)std::min<int64_t>(std::max<int64_t>(2, c), std::max<int64_t>(1, slice));
         }
-        g0 += sc.a * sc.b;
-        mt = std::max(mt, sc.tpx);
+        groups = std::max<int32_t>(groups, sc.a * sc.b);
+        slots += (int64_t)sc.a * sc.b * ctas_per_group * sc.tpx;
+        if (slots > INT32_MAX) return -1;
     }
-    *max_tpx = mt;
-    return g0;
+    // Largest panel first: every group enters it together, so the groups of
+    // a slice stay in step and share its tiles through L2; the small panels
+    // at the end absorb the drift.
+    std::vector<double> work(n);
+    for (int p = 0; p < n; ++p) {
+        work[p] = (double)std::max<int64_t>(n_qq[p], 0) * (double)std::max<int64_t>(n_rt[p], 0) * (double)tile_bytes[p];
+        order[p] = p;
+    }
+    std::stable_sort(order, order + n, [&](int32_t x, int32_t y) { return work[x] > work[y]; });
+    *n_slots = (int32_t)slots;
+    return groups;
 }
 
 }  // namespace fastid

@@ -38,6 +38,7 @@ constexpr int TC_BK = 128;            // loci (bytes) per stage
 constexpr int TC_THREADS = 192;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK;  // 16 KB
 constexpr uint64_t WAIT_NS = 2000000000ull;     // 2 s per wait
+constexpr uint64_t RENDEZVOUS_NS = 50000000ull;  // 50 ms per panel entry, then go on alone
 
 // Kernel variants: references per tile (the MMA's N) and pipeline depth.
 //   BN = 256: 32 KB reference stage, 4 stages, 2 x 256 TMEM columns
@@ -67,7 +68,7 @@ struct TcMaps {
 struct TensorArgs {
     int32_t n_panels;
     PanelDesc panel[TC_MAXP];
-    int32_t max_tpx;       // top-k slots per CTA
+    int32_t order[TC_MAXP];  // panels in the order every group walks them
     uint32_t threshold;    // already clamped to <= N
     int32_t k;
     int32_t epi;
@@ -78,8 +79,9 @@ struct TensorArgs {
     int64_t *hit_r;
     uint32_t *hit_score;
     unsigned long long *hit_count;
-    uint64_t *partial;  // EPI_TOPK: [ctas * max_tpx][k][128]
+    uint64_t *partial;  // EPI_TOPK: [slots][k][128], see TcSched
     uint32_t *status;
+    unsigned int *arrive;  // panel-entry counters (see the producer), or nullptr
 };
 
 // ---- PTX wrappers --------------------------------------------------------
@@ -153,6 +155,13 @@ __device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *
         "[%0], [%1, {%2, %3}], [%4], %5;"
         ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(ctamask)
         : "memory");
+}
+
+// L2 prefetch of one box (no shared-memory destination, no completion).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int32_t x, int32_t y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y)
+                 : "memory");
 }
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -288,35 +297,49 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, uint32
     }
 }
 
-// The work of one group (see TcSched): panel p, reference tiles
-// [r_lo, r_hi) walked in chunks, query tiles (pairs) [q_lo, q_hi).  p < 0:
-// no work.
+// Panel-entry rendezvous.  Groups that share a reference slice read its
+// tiles through L2 only while they walk it in step; entering a panel at
+// different times (the previous panel's drift) breaks that.  So each CTA's
+// producer counts itself in at every panel after the first and, if it has
+// work there, waits for the whole grid before loading the panel's tiles.
+// It is a hint, not a barrier the results depend on: the wait gives up
+// after RENDEZVOUS_NS (a CTA that is not resident, or one that aborted) and
+// the producer goes on alone.
+__device__ __forceinline__ void panel_rendezvous(unsigned int *ctr, bool wait) {
+    atomicAdd(ctr, 1u);
+    if (!wait) return;
+    const unsigned int n = gridDim.x;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        unsigned int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= n || globaltimer() - t0 > RENDEZVOUS_NS) return;
+        __nanosleep(200);
+    }
+}
+
+// The work of one group (see TcSched) in panel p: reference tiles
+// [r_lo, r_hi) walked in chunks, query tiles (pairs) [q_lo, q_hi).  Empty
+// (q_lo == q_hi) when the panel's grid has no group wg.
 struct GroupWork {
-    int p;
     int64_t r_lo, r_hi;
     int32_t q_lo, q_hi, chunk;
 };
 
-__device__ __forceinline__ GroupWork group_work(const TensorArgs &a, int64_t wg) {
+__device__ __forceinline__ GroupWork group_work(const TensorArgs &a, int64_t wg, int p) {
     GroupWork w;
-    w.p = -1;
     w.r_lo = w.r_hi = 0;
     w.q_lo = w.q_hi = 0;
     w.chunk = 1;
-#pragma unroll 1
-    for (int p = 0; p < a.n_panels; ++p) {
-        const TcSched &sc = a.panel[p].sc;
-        const int64_t rel = wg - sc.g0;
-        if (sc.n_qq > 0 && rel >= 0 && rel < (int64_t)sc.a * sc.b) {
-            const int64_t x = rel / sc.b, y = rel - x * sc.b;
-            const int64_t n_rt = a.panel[p].n_rt;
-            w.p = p;
-            w.r_lo = y * n_rt / sc.b;
-            w.r_hi = (y + 1) * n_rt / sc.b;
-            w.q_lo = (int32_t)(x * sc.tpx);
-            w.q_hi = (int32_t)min((int64_t)sc.n_qq, (x + 1) * sc.tpx);
-            w.chunk = sc.chunk;
-        }
+    const TcSched &sc = a.panel[p].sc;
+    if (sc.n_qq > 0 && wg < (int64_t)sc.a * sc.b) {
+        const int64_t x = wg / sc.b, y = wg - x * sc.b;
+        const int64_t n_rt = a.panel[p].n_rt;
+        w.r_lo = y * n_rt / sc.b;
+        w.r_hi = (y + 1) * n_rt / sc.b;
+        w.q_lo = (int32_t)(x * sc.tpx);
+        w.q_hi = (int32_t)min((int64_t)sc.n_qq, (x + 1) * sc.tpx);
+        w.chunk = sc.chunk;
     }
     return w;
 }
@@ -373,7 +396,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int64_t c = blockIdx.x;                     // this CTA: owner of top-k slots
     const int rank = PAIR ? (int)cluster_rank() : 0;
     const int64_t wg = PAIR ? (c >> 1) : c;            // work group: cluster or CTA
-    const GroupWork W = group_work(args, wg);
     volatile int *abort_flag = &ctl->abort_flag;
 
     if (tid == 0) {
@@ -401,41 +423,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (PAIR) cluster_sync();  // the peer's barriers exist before any multicast targets them
     tc_fence_after();
     const uint32_t tmem_base = ctl->tmem_base;
-    const int p = W.p;
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
-        if (lane == 0 && p >= 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[p])) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[p])) : "memory");
-            const int n_kb = args.panel[p].n_kb;
+        if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
             int64_t issued = 0;
             bool ok = true;
-            for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
-                const int64_t re = min(rc + W.chunk, W.r_hi);
-                for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
-                    const int64_t qt = PAIR ? 2 * (int64_t)qq + rank : qq;
-                    for (int64_t rt = rc; rt < re && ok; ++rt) {
-                        for (int kb = 0; kb < n_kb; ++kb) {
-                            ok = mbar_wait(smem_u32(&ctl->empty[stage]), phase ^ 1u, abort_flag, args.status, 1);
-                            if (!ok) break;
-                            const uint32_t fb = smem_u32(&ctl->full[stage]);
-                            mbar_expect_tx(fb, TC_A_BYTES + S::B_BYTES);
-                            tma_load_2d(smem_u32(sA + stage * TC_A_BYTES), &maps.a[p], fb, kb * TC_BK,
-                                        (int32_t)(qt * TC_BM));
-                            if (PAIR)
-                                tma_load_2d_mc(smem_u32(sB + stage * S::B_BYTES + rank * (S::B_BYTES / 2)),
-                                               &maps.b[p], fb, kb * TC_BK, (int32_t)(rt * BN + rank * (BN / 2)),
-                                               (uint16_t)0x3);
-                            else
-                                tma_load_2d(smem_u32(sB + stage * S::B_BYTES), &maps.b[p], fb, kb * TC_BK,
-                                            (int32_t)(rt * BN));
-                            ++issued;
-                            if (++stage == S::STAGES) {
-                                stage = 0;
-                                phase ^= 1u;
+            for (int pi = 0; pi < args.n_panels && ok; ++pi) {
+                const int p = args.order[pi];
+                const GroupWork W = group_work(args, wg, p);
+                if (pi > 0 && args.arrive) panel_rendezvous(args.arrive + pi, W.q_lo < W.q_hi);
+                if (W.q_lo >= W.q_hi) continue;
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[p])) : "memory");
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[p])) : "memory");
+                const int n_kb = args.panel[p].n_kb;
+                for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
+                    const int64_t re = min(rc + W.chunk, W.r_hi);
+                    for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
+                        const int64_t qt = PAIR ? 2 * (int64_t)qq + rank : qq;
+                        for (int64_t rt = rc; rt < re && ok; ++rt) {
+                            for (int kb = 0; kb < n_kb; ++kb) {
+                                ok = mbar_wait(smem_u32(&ctl->empty[stage]), phase ^ 1u, abort_flag, args.status, 1);
+                                if (!ok) break;
+                                const uint32_t fb = smem_u32(&ctl->full[stage]);
+                                mbar_expect_tx(fb, TC_A_BYTES + S::B_BYTES);
+                                tma_load_2d(smem_u32(sA + stage * TC_A_BYTES), &maps.a[p], fb, kb * TC_BK,
+                                            (int32_t)(qt * TC_BM));
+                                if (PAIR)
+                                    tma_load_2d_mc(smem_u32(sB + stage * S::B_BYTES + rank * (S::B_BYTES / 2)),
+                                                   &maps.b[p], fb, kb * TC_BK, (int32_t)(rt * BN + rank * (BN / 2)),
+                                                   (uint16_t)0x3);
+                                else
+                                    tma_load_2d(smem_u32(sB + stage * S::B_BYTES), &maps.b[p], fb, kb * TC_BK,
+                                                (int32_t)(rt * BN));
+                                // A group with one query tile streams its slice once: fetch the
+                                // next reference tile into L2 while this one is consumed, so the
+                                // group that reaches a tile first does not wait on DRAM.
+                                if (W.q_hi - W.q_lo == 1 && rt + 1 < W.r_hi)
+                                    tma_prefetch_2d(&maps.b[p], kb * TC_BK,
+                                                    (int32_t)((rt + 1) * BN + (PAIR ? rank * (BN / 2) : 0)));
+                                ++issued;
+                                if (++stage == S::STAGES) {
+                                    stage = 0;
+                                    phase ^= 1u;
+                                }
                             }
                         }
                     }
@@ -453,45 +486,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
-        if (lane == 0 && p >= 0) {
+        if (lane == 0) {
             constexpr uint32_t idesc = idesc_f8(TC_BM, BN);
-            const int n_kb = args.panel[p].n_kb;
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
-                const int64_t re = min(rc + W.chunk, W.r_hi);
-                for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
-                    for (int64_t rt = rc; rt < re && ok; ++rt) {
-                        ok = mbar_wait(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, abort_flag, args.status, 3);
-                        if (!ok) break;
-                        tc_fence_after();
-                        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-                        for (int kb = 0; kb < n_kb; ++kb) {
-                            ok = mbar_wait(smem_u32(&ctl->full[stage]), phase, abort_flag, args.status, 4);
+            for (int pi = 0; pi < args.n_panels && ok; ++pi) {
+                const int p = args.order[pi];
+                const GroupWork W = group_work(args, wg, p);
+                if (W.q_lo >= W.q_hi) continue;
+                const int n_kb = args.panel[p].n_kb;
+                for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
+                    const int64_t re = min(rc + W.chunk, W.r_hi);
+                    for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
+                        for (int64_t rt = rc; rt < re && ok; ++rt) {
+                            ok = mbar_wait(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, abort_flag, args.status, 3);
                             if (!ok) break;
                             tc_fence_after();
-                            const uint64_t ad = sw128_desc(smem_u32(sA + stage * TC_A_BYTES));
-                            const uint64_t bd = sw128_desc(smem_u32(sB + stage * S::B_BYTES));
+                            const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+                            for (int kb = 0; kb < n_kb; ++kb) {
+                                ok = mbar_wait(smem_u32(&ctl->full[stage]), phase, abort_flag, args.status, 4);
+                                if (!ok) break;
+                                tc_fence_after();
+                                const uint64_t ad = sw128_desc(smem_u32(sA + stage * TC_A_BYTES));
+                                const uint64_t bd = sw128_desc(smem_u32(sB + stage * S::B_BYTES));
 #pragma unroll
-                            for (int kk = 0; kk < TC_BK / 32; ++kk)  // K = 32 FP8 per MMA: +32 bytes = +2 in the address field
-                                tc_mma_f8(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
-                            if (PAIR)
-                                tc_commit_mc(smem_u32(&ctl->empty[stage]), (uint16_t)0x3);
-                            else
-                                tc_commit(smem_u32(&ctl->empty[stage]));
-                            if (++stage == S::STAGES) {
-                                stage = 0;
-                                phase ^= 1u;
+                                for (int kk = 0; kk < TC_BK / 32; ++kk)  // K = 32 FP8 per MMA: +32 bytes = +2 in the address field
+                                    tc_mma_f8(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
+                                if (PAIR)
+                                    tc_commit_mc(smem_u32(&ctl->empty[stage]), (uint16_t)0x3);
+                                else
+                                    tc_commit(smem_u32(&ctl->empty[stage]));
+                                if (++stage == S::STAGES) {
+                                    stage = 0;
+                                    phase ^= 1u;
+                                }
                             }
-                        }
-                        if (!ok) break;
-                        tc_commit(smem_u32(&ctl->tfull[acc]));
-                        if (++acc == 2) {
-                            acc = 0;
-                            acc_phase ^= 1u;
+                            if (!ok) break;
+                            tc_commit(smem_u32(&ctl->tfull[acc]));
+                            if (++acc == 2) {
+                                acc = 0;
+                                acc_phase ^= 1u;
+                            }
                         }
                     }
                 }
@@ -500,113 +538,132 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_commit(smem_u32(&ctl->done));
             mbar_drain(smem_u32(&ctl->done), 0, args.status, 5);
         }
-    } else if (p >= 0) {
+    } else {
         // ---------------- epilogue: warps 2..5 ----------------
         const int quad = warp & 3;            // TMEM lane quadrant this warp may access
         const int row = quad * 32 + lane;     // query row within the tile
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         const float tplus1 = args.threshold == 0xFFFFFFFFu ? __int_as_float(0x7f800000) : (float)args.threshold + 1.0f;
         const int k = args.k;
-        const int64_t n_refs = args.panel[p].n_refs;
         const bool topk = args.epi == EPI_TOPK;
         int acc = 0;
         uint32_t acc_phase = 0;
         int32_t ls[TC_KMAX];  // this thread's top-k scores (see net_insert)
         uint32_t lr[TC_KMAX]; // and their references
         bool ok = true;
-        for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
-            const int64_t re = min(rc + W.chunk, W.r_hi);
-            for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
-                const int64_t qt = PAIR ? 2 * (int64_t)qq + rank : qq;
-                const int64_t q = qt * TC_BM + row;
-                const bool qvalid = q < args.panel[p].n_q;
-                const float cq = args.panel[p].qconst[q];
-                const float cut0 = qvalid ? tplus1 - cq : -__int_as_float(0x7f800000);
-                uint64_t *slot = args.partial + (c * args.max_tpx + (qq - W.q_lo)) * (int64_t)k * TC_BM + row;
-                if (topk && rc > W.r_lo) {
-                    list_load(slot, ls, lr, k);
-                } else {
+        for (int pi = 0; pi < args.n_panels && ok; ++pi) {
+            const int p = args.order[pi];
+            const GroupWork W = group_work(args, wg, p);
+            if (W.q_lo >= W.q_hi) continue;
+            const PanelDesc &P = args.panel[p];
+            const int64_t n_refs = P.n_refs;
+            for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
+                const int64_t re = min(rc + W.chunk, W.r_hi);
+                for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
+                    const int64_t qt = PAIR ? 2 * (int64_t)qq + rank : qq;
+                    const int64_t q = qt * TC_BM + row;
+                    const bool qvalid = q < P.n_q;
+                    const float cq = P.qconst[q];
+                    const float cut0 = qvalid ? tplus1 - cq : -__int_as_float(0x7f800000);
+                    uint64_t *slot = args.partial +
+                                     ((int64_t)P.sc.slot0 + c * P.sc.tpx + (qq - W.q_lo)) * (int64_t)k * TC_BM + row;
+                    if (topk && rc > W.r_lo) {
+                        list_load(slot, ls, lr, k);
+                    } else {
 #pragma unroll
-                    for (int i = 0; i < TC_KMAX; ++i) {
-                        ls[i] = i < TC_KMAX - k ? NET_HOLD : NET_EMPTY;
-                        lr[i] = 0xFFFFFFFFu;
-                    }
-                }
-                float cut = ls[TC_KMAX - 1] == NET_EMPTY ? cut0 : (float)ls[TC_KMAX - 1] - cq;
-                for (int64_t rt = rc; rt < re; ++rt) {
-                    const bool got = mbar_wait(smem_u32(&ctl->tfull[acc]), acc_phase, abort_flag, args.status, 6);
-                    __syncwarp();
-                    if (!__all_sync(0xffffffffu, got)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const int64_t r0 = rt * BN;
-                    const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * BN);
-#pragma unroll 1
-                    for (int ch = 0; ch < BN / 32; ++ch) {
-                        uint32_t v[32];
-                        __syncwarp();  // tcgen05.ld is warp-collective: reconverge first
-                        tmem_ld32(taddr + ch * 32, v);
-                        if (ch == BN / 32 - 1) {
-                            tc_fence_before();
-                            mbar_arrive(smem_u32(&ctl->tempty[acc]));
+                        for (int i = 0; i < TC_KMAX; ++i) {
+                            ls[i] = i < TC_KMAX - k ? NET_HOLD : NET_EMPTY;
+                            lr[i] = 0xFFFFFFFFu;
                         }
-                        const int64_t rch = r0 + ch * 32;
-                        if (args.epi == EPI_SCORES16 || args.epi == EPI_SCORES32) {
-                            if (qvalid) {
+                    }
+                    float cut = ls[TC_KMAX - 1] == NET_EMPTY ? cut0 : (float)ls[TC_KMAX - 1] - cq;
+                    for (int64_t rt = rc; rt < re; ++rt) {
+                        const bool got = mbar_wait(smem_u32(&ctl->tfull[acc]), acc_phase, abort_flag, args.status, 6);
+                        __syncwarp();
+                        if (!__all_sync(0xffffffffu, got)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const int64_t r0 = rt * BN;
+                        const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * BN);
+#pragma unroll 1
+                        for (int ch = 0; ch < BN / 32; ++ch) {
+                            uint32_t v[32];
+                            __syncwarp();  // tcgen05.ld is warp-collective: reconverge first
+                            tmem_ld32(taddr + ch * 32, v);
+                            if (ch == BN / 32 - 1) {
+                                tc_fence_before();
+                                mbar_arrive(smem_u32(&ctl->tempty[acc]));
+                            }
+                            const int64_t rch = r0 + ch * 32;
+                            if (args.epi == EPI_SCORES16 || args.epi == EPI_SCORES32) {
+                                if (qvalid) {
 #pragma unroll
-                                for (int j = 0; j < 32; ++j) {
-                                    const int64_t r = rch + j;
-                                    if (r < n_refs) {
-                                        const uint32_t sc = (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq);
-                                        if (args.epi == EPI_SCORES16)
-                                            reinterpret_cast<uint16_t *>(args.out)[q * args.ld_out + r] = (uint16_t)sc;
-                                        else
-                                            reinterpret_cast<uint32_t *>(args.out)[q * args.ld_out + r] = sc;
+                                    for (int j = 0; j < 32; ++j) {
+                                        const int64_t r = rch + j;
+                                        if (r < n_refs) {
+                                            const uint32_t sc = (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq);
+                                            if (args.epi == EPI_SCORES16)
+                                                reinterpret_cast<uint16_t *>(args.out)[q * args.ld_out + r] =
+                                                    (uint16_t)sc;
+                                            else
+                                                reinterpret_cast<uint32_t *>(args.out)[q * args.ld_out + r] = sc;
+                                        }
                                     }
                                 }
+                                continue;
                             }
-                            continue;
-                        }
-                        uint32_t m = 0;  // columns of this chunk that pass the filter
+                            // Common case first: nothing in the chunk beats the cut
+                            // (the chunk's minimum, by a tree of fminf).
+                            float mn[16];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) m |= (uint32_t)(__uint_as_float(v[j]) < cut) << j;
-                        if (rch + 32 > n_refs) m &= rch >= n_refs ? 0u : ((1u << (n_refs - rch)) - 1u);
-                        if (!__any_sync(0xffffffffu, m != 0u)) continue;
-                        if (args.epi == EPI_HITS) {
+                            for (int j = 0; j < 16; ++j) mn[j] = fminf(__uint_as_float(v[j]), __uint_as_float(v[j + 16]));
 #pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if (m & (1u << j))
-                                    append_hit(args.hit_count, args.capacity, args.hit_q, args.hit_r, args.hit_score,
-                                               q, rch + j, (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq));
-                            continue;
-                        }
-                        // rare path: stage the chunk, then insert candidates in lock-step
+                            for (int w = 8; w > 0; w >>= 1)
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) stage_v[j * TC_BM + row] = __uint_as_float(v[j]);
-                        while (__any_sync(0xffffffffu, m != 0u)) {
-                            int32_t xs = NET_EMPTY;
-                            uint32_t xr = 0u;
-                            if (m != 0u) {
-                                const int j = __ffs(m) - 1;
-                                m &= m - 1u;
-                                const float d = stage_v[j * TC_BM + row];
-                                if (d < cut) {
-                                    xs = (int32_t)(d + cq);
-                                    xr = (uint32_t)(rch + j);
+                                for (int j = 0; j < w; ++j) mn[j] = fminf(mn[j], mn[j + w]);
+                            if (!__any_sync(0xffffffffu, mn[0] < cut)) continue;
+                            uint32_t m = 0;  // columns of this chunk that pass the filter
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) m |= (uint32_t)(__uint_as_float(v[j]) < cut) << j;
+                            if (rch + 32 > n_refs) m &= rch >= n_refs ? 0u : ((1u << (n_refs - rch)) - 1u);
+                            if (!__any_sync(0xffffffffu, m != 0u)) continue;
+                            if (args.epi == EPI_HITS) {
+#pragma unroll
+                                for (int j = 0; j < 32; ++j)
+                                    if (m & (1u << j))
+                                        append_hit(args.hit_count, args.capacity, args.hit_q, args.hit_r,
+                                                   args.hit_score, q, rch + j,
+                                                   (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq));
+                                continue;
+                            }
+                            // rare path: stage the chunk, then insert candidates in lock-step
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) stage_v[j * TC_BM + row] = __uint_as_float(v[j]);
+                            while (__any_sync(0xffffffffu, m != 0u)) {
+                                int32_t xs = NET_EMPTY;
+                                uint32_t xr = 0u;
+                                if (m != 0u) {
+                                    const int j = __ffs(m) - 1;
+                                    m &= m - 1u;
+                                    const float d = stage_v[j * TC_BM + row];
+                                    if (d < cut) {
+                                        xs = (int32_t)(d + cq);
+                                        xr = (uint32_t)(rch + j);
+                                    }
                                 }
+                                net_insert(ls, lr, xs, xr);
+                                cut = ls[TC_KMAX - 1] == NET_EMPTY ? cut0 : (float)ls[TC_KMAX - 1] - cq;
                             }
-                            net_insert(ls, lr, xs, xr);
-                            cut = ls[TC_KMAX - 1] == NET_EMPTY ? cut0 : (float)ls[TC_KMAX - 1] - cq;
+                        }
+                        if (++acc == 2) {
+                            acc = 0;
+                            acc_phase ^= 1u;
                         }
                     }
-                    if (++acc == 2) {
-                        acc = 0;
-                        acc_phase ^= 1u;
-                    }
+                    if (topk && ok) list_save(slot, ls, lr, k);
                 }
-                if (topk && ok) list_save(slot, ls, lr, k);
             }
         }
     }
@@ -833,8 +890,8 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
         a.panel[p].n_kb = L.kpad[p] / TC_BK;
         a.panel[p].sc = L.sched[p];
         a.panel[p].qconst = L.qconst[p];
+        a.order[p] = L.order[p];
     }
-    a.max_tpx = L.max_tpx;
     a.threshold = L.threshold;
     a.k = L.k;
     a.epi = L.epi;
@@ -847,6 +904,7 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
     a.hit_count = L.hit_count;
     a.partial = L.partial;
     a.status = L.status;
+    a.arrive = L.arrive;
     cudaError_t e;
     if (L.pair) {
         if (bn != 256) return cudaErrorInvalidValue;
