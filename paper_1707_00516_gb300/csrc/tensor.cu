@@ -243,17 +243,18 @@ __host__ __device__ constexpr uint32_t idesc_f8(int m, int n) {
 // the earlier entry has the lower index).  Inserting (xs, xr) is a fixed
 // compare-select network, so all lanes of a warp insert in lock-step; a lane
 // with nothing to insert passes xs = INT32_MAX, which changes nothing.
-// For a runtime k <= 32 the first 32 - k slots hold INT32_MIN place-holders
-// that nothing displaces, so the k kept entries sit in slots 32-k .. 31 and
-// the k-th smallest is always slot 31 (static register indices only).
+// The network has KM slots (16 or 32, chosen per launch from k).  For a
+// runtime k <= KM the first KM - k slots hold INT32_MIN place-holders that
+// nothing displaces, so the k kept entries sit in slots KM-k .. KM-1 and the
+// k-th smallest is always slot KM-1 (static register indices only).
 constexpr int TC_KMAX = 32;
 constexpr int32_t NET_EMPTY = 0x7fffffff;
 constexpr int32_t NET_HOLD = (int32_t)0x80000000;
 
-__device__ __forceinline__ void net_insert(int32_t (&ls)[TC_KMAX], uint32_t (&lr)[TC_KMAX], int32_t xs,
-                                           uint32_t xr) {
+template <int KM>
+__device__ __forceinline__ void net_insert(int32_t (&ls)[KM], uint32_t (&lr)[KM], int32_t xs, uint32_t xr) {
 #pragma unroll
-    for (int i = TC_KMAX - 1; i > 0; --i) {
+    for (int i = KM - 1; i > 0; --i) {
         const bool shift = xs < ls[i - 1];
         const bool here = xs < ls[i];
         ls[i] = shift ? ls[i - 1] : (here ? xs : ls[i]);
@@ -347,21 +348,22 @@ __device__ __forceinline__ GroupWork group_work(const TensorArgs &a, int64_t wg,
 // Save / resume one thread's top-k list.  Slot layout [slot][k][128]: entry i
 // of the 128 rows is contiguous, so a warp's accesses coalesce.  Keys
 // ascending, empty entries KEY_EMPTY.
-__device__ __forceinline__ void list_save(uint64_t *slot_row, const int32_t (&ls)[TC_KMAX],
-                                          const uint32_t (&lr)[TC_KMAX], int k) {
+template <int KM>
+__device__ __forceinline__ void list_save(uint64_t *slot_row, const int32_t (&ls)[KM], const uint32_t (&lr)[KM],
+                                          int k) {
 #pragma unroll
-    for (int i = 0; i < TC_KMAX; ++i)
-        if (i >= TC_KMAX - k)
-            slot_row[(int64_t)(i - (TC_KMAX - k)) * TC_BM] =
+    for (int i = 0; i < KM; ++i)
+        if (i >= KM - k)
+            slot_row[(int64_t)(i - (KM - k)) * TC_BM] =
                 ls[i] == NET_EMPTY ? KEY_EMPTY : make_key((uint32_t)ls[i], lr[i]);
 }
 
-__device__ __forceinline__ void list_load(const uint64_t *slot_row, int32_t (&ls)[TC_KMAX], uint32_t (&lr)[TC_KMAX],
-                                          int k) {
+template <int KM>
+__device__ __forceinline__ void list_load(const uint64_t *slot_row, int32_t (&ls)[KM], uint32_t (&lr)[KM], int k) {
 #pragma unroll
-    for (int i = 0; i < TC_KMAX; ++i) {
-        if (i >= TC_KMAX - k) {
-            const uint64_t key = slot_row[(int64_t)(i - (TC_KMAX - k)) * TC_BM];
+    for (int i = 0; i < KM; ++i) {
+        if (i >= KM - k) {
+            const uint64_t key = slot_row[(int64_t)(i - (KM - k)) * TC_BM];
             ls[i] = key == KEY_EMPTY ? NET_EMPTY : (int32_t)(key >> 32);
             lr[i] = (uint32_t)key;
         } else {
@@ -374,7 +376,7 @@ __device__ __forceinline__ void list_load(const uint64_t *slot_row, int32_t (&ls
 // PAIR: 2-CTA clusters; both CTAs walk the same reference tiles for the two
 // query tiles of a pair (rank r takes tile 2 qq + r), and each multicasts half
 // of every reference stage into both CTAs' shared memory (BN = 256 only).
-template <int BN, bool PAIR>
+template <int BN, bool PAIR, int KM>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tensor_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TensorArgs args) {
     using S = TcShape<BN>;
@@ -548,8 +550,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const bool topk = args.epi == EPI_TOPK;
         int acc = 0;
         uint32_t acc_phase = 0;
-        int32_t ls[TC_KMAX];  // this thread's top-k scores (see net_insert)
-        uint32_t lr[TC_KMAX]; // and their references
+        int32_t ls[KM];   // this thread's top-k scores (see net_insert)
+        uint32_t lr[KM];  // and their references
         bool ok = true;
         for (int pi = 0; pi < args.n_panels && ok; ++pi) {
             const int p = args.order[pi];
@@ -571,12 +573,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         list_load(slot, ls, lr, k);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < TC_KMAX; ++i) {
-                            ls[i] = i < TC_KMAX - k ? NET_HOLD : NET_EMPTY;
+                        for (int i = 0; i < KM; ++i) {
+                            ls[i] = i < KM - k ? NET_HOLD : NET_EMPTY;
                             lr[i] = 0xFFFFFFFFu;
                         }
                     }
-                    float cut = ls[TC_KMAX - 1] == NET_EMPTY ? cut0 : (float)ls[TC_KMAX - 1] - cq;
+                    float cut = ls[KM - 1] == NET_EMPTY ? cut0 : (float)ls[KM - 1] - cq;
                     for (int64_t rt = rc; rt < re; ++rt) {
                         const bool got = mbar_wait(smem_u32(&ctl->tfull[acc]), acc_phase, abort_flag, args.status, 6);
                         __syncwarp();
@@ -654,7 +656,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                     }
                                 }
                                 net_insert(ls, lr, xs, xr);
-                                cut = ls[TC_KMAX - 1] == NET_EMPTY ? cut0 : (float)ls[TC_KMAX - 1] - cq;
+                                cut = ls[KM - 1] == NET_EMPTY ? cut0 : (float)ls[KM - 1] - cq;
                             }
                         }
                         if (++acc == 2) {
@@ -840,8 +842,8 @@ cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s
 // at once (0 if clusters are unavailable).
 int tensor_pair_clusters(int device) {
     size_t smem = tensor_smem<256>(EPI_TOPK);
-    if (cudaFuncSetAttribute(tensor_kernel<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
+    if (cudaFuncSetAttribute(tensor_kernel<256, true, TC_KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -860,7 +862,7 @@ int tensor_pair_clusters(int device) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tensor_kernel<256, true>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, tensor_kernel<256, true, TC_KMAX>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -872,6 +874,34 @@ int tensor_grid_target(int device) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     return sms;
 }
+
+namespace {
+
+// One launch of tensor_kernel<BN, PAIR, KM> over n_groups work groups (2-CTA
+// clusters when paired).
+template <int BN, bool PAIR, int KM>
+cudaError_t launch_variant(const TcMaps &maps, const TensorArgs &a, int32_t n_groups, int epi, cudaStream_t s) {
+    const size_t smem = tensor_smem<BN>(epi);
+    cudaError_t e =
+        cudaFuncSetAttribute(tensor_kernel<BN, PAIR, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((PAIR ? 2 : 1) * n_groups);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = PAIR ? 2 : 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = PAIR ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, tensor_kernel<BN, PAIR, KM>, maps, a);
+}
+
+}  // namespace
 
 cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
     TcMaps maps;
@@ -905,39 +935,15 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
     a.partial = L.partial;
     a.status = L.status;
     a.arrive = L.arrive;
-    cudaError_t e;
-    if (L.pair) {
-        if (bn != 256) return cudaErrorInvalidValue;
-        size_t smem = tensor_smem<256>(L.epi);
-        e = cudaFuncSetAttribute(tensor_kernel<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        cudaLaunchConfig_t cfg;
-        memset(&cfg, 0, sizeof cfg);
-        cfg.gridDim = dim3(2 * L.n_groups);
-        cfg.blockDim = dim3(TC_THREADS);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, tensor_kernel<256, true>, maps, a);
-    }
-    if (bn == 128) {
-        size_t smem = tensor_smem<128>(L.epi);
-        e = cudaFuncSetAttribute(tensor_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        tensor_kernel<128, false><<<L.n_groups, TC_THREADS, smem, s>>>(maps, a);
-    } else {
-        size_t smem = tensor_smem<256>(L.epi);
-        e = cudaFuncSetAttribute(tensor_kernel<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        tensor_kernel<256, false><<<L.n_groups, TC_THREADS, smem, s>>>(maps, a);
-    }
-    return cudaGetLastError();
+    if (L.pair && bn != 256) return cudaErrorInvalidValue;
+    // 16-slot lists when k allows (half the insert network, 32 fewer registers)
+    const bool k16 = L.epi != EPI_TOPK || L.k <= 16;
+    if (L.pair) return k16 ? launch_variant<256, true, 16>(maps, a, L.n_groups, L.epi, s)
+                           : launch_variant<256, true, 32>(maps, a, L.n_groups, L.epi, s);
+    if (bn == 128) return k16 ? launch_variant<128, false, 16>(maps, a, L.n_groups, L.epi, s)
+                              : launch_variant<128, false, 32>(maps, a, L.n_groups, L.epi, s);
+    return k16 ? launch_variant<256, false, 16>(maps, a, L.n_groups, L.epi, s)
+               : launch_variant<256, false, 32>(maps, a, L.n_groups, L.epi, s);
 }
 
 }  // namespace fastid

@@ -72,8 +72,8 @@ def _check(panels, batches, k, T):
         assert np.array_equal(ix.cpu().numpy(), ei)
 
 
-@pytest.mark.parametrize("variant", [B.VARIANT_TENSOR_N256, B.VARIANT_TENSOR_N128])
-@pytest.mark.parametrize("k,T", [(16, B.NO_THRESHOLD), (32, 40)])
+@pytest.mark.parametrize("variant", [B.VARIANT_TENSOR_N256, B.VARIANT_TENSOR_N128, B.VARIANT_TENSOR_PAIR])
+@pytest.mark.parametrize("k,T", [(16, B.NO_THRESHOLD), (32, 40), (17, B.NO_THRESHOLD), (3, 25)])
 def test_plan_run_matches_oracle(setup, variant, k, T):
     s, panels = setup
     sizes = [1, 0, 7, 130, 300, 2, 129, 57, 256]

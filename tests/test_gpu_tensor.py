@@ -99,10 +99,12 @@ def test_tensor_form_needs_operand_copy(ts):
     db2.close()
 
 
-@pytest.mark.parametrize("n_q,n_refs", [(600, 7000), (1024, 20000), (513, 3000)])
-def test_paired_launch_parity(ts, n_q, n_refs):
+@pytest.mark.parametrize("n_q,n_refs,k", [(600, 7000, 32), (1024, 20000, 32), (513, 3000, 32), (600, 7000, 16),
+                                         (513, 3000, 9)])
+def test_paired_launch_parity(ts, n_q, n_refs, k):
     """Enough query tiles for the paired (2-CTA cluster, multicast) launch,
-    including an odd tile count (a padding tile in the last pair)."""
+    including an odd tile count (a padding tile in the last pair), with the
+    32-slot (k > 16) and 16-slot top-k lists."""
     import gen
     n_loci, seed = 1536, 77 + n_q
     thr = gen.maf_thresholds(seed, n_loci)
@@ -116,8 +118,8 @@ def test_paired_launch_parity(ts, n_q, n_refs):
     modes = torch.from_numpy(rec.modes).cuda()
     mis, une = oracle.scores(R, Q)
     exp = oracle.select(mis, une, rec.modes)
-    sc, ix = ts.topk(db, q, modes, 32, 300)
-    es, ei = oracle.topk(exp, 32, 300)
+    sc, ix = ts.topk(db, q, modes, k, 300)
+    es, ei = oracle.topk(exp, k, 300)
     assert np.array_equal(sc.cpu().numpy().view(np.uint32), es)
     assert np.array_equal(ix.cpu().numpy(), ei)
     full = ts.scores(db, q, modes, torch.int32)
