@@ -341,12 +341,14 @@ def time_form(args, s, db, form_name, step_fn, pairs_per_step, n_loci, world, de
 
     peaks, peak_src = load_peaks()
     main_s = prof["main_ms"] / max(1, prof["main_launches"]) / 1e3
+    # compare launches per step (several when references stream in blocks)
+    main_per_step = max(1, prof["main_launches"]) / args.steps
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if form_name == "plain":
         words32 = 2 * ((n_loci + 63) // 64)
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak = POPC_PER_CLK_PER_SM * n_sms * sm_max * 1e6 / 1e12
-        achieved = pairs_per_step * words32 / main_s / 1e12
+        achieved = pairs_per_step * words32 / (main_s * main_per_step) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpopc/s",
                 "kernel": "plain_kernel<EPI_TOPK>",
                 "peak_source": f"{POPC_PER_CLK_PER_SM} POPC/clk/SM x {n_sms} SMs x {sm_max:.0f} MHz "
@@ -354,7 +356,7 @@ def time_form(args, s, db, form_name, step_fn, pairs_per_step, n_loci, world, de
     else:
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         peak = bf16 * FP8_OVER_BF16
-        achieved = 2.0 * pairs_per_step * n_loci / main_s / 1e12
+        achieved = 2.0 * pairs_per_step * n_loci / (main_s * main_per_step) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "kernel": "tensor_kernel (tcgen05 kind::f8f6f4, EPI_TOPK)",
                 "peak_source": f"bf16 dense burst {bf16:.1f} TFLOP/s ({peak_src}) x {FP8_OVER_BF16:g} "
@@ -438,6 +440,84 @@ def run_gpu(args, w):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_streamed(args, w):
+    """The workload with its references in pinned HOST memory, streamed
+    through the device in blocks by fastid_topk_streamed (tensor form)."""
+    import torch
+    from paper_1707_00516_gb300 import binding as B
+    from paper_1707_00516_gb300.build import build
+    from paper_1707_00516_gb300.search import Searcher, words64
+    world, rank = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gen.build_gpu()
+    build()
+    s = Searcher(local, B.FORM_TENSOR)
+    seed = gen.config_seed(w["cfg"])
+    n_refs, n_loci, k, T = w["n_refs"], w["n_loci"], w["k"], w["threshold"]
+    thr = gen.maf_thresholds(seed, n_loci)
+    thr_dev = torch.from_numpy(thr.view(np.int32)).to(dev)
+    host = torch.empty((n_refs, words64(n_loci)), dtype=torch.int64, pin_memory=True)
+    chunk = min(1 << 20, n_refs)
+    alle = torch.empty((chunk, n_loci), dtype=torch.uint8, device=dev)
+    packed = torch.empty((chunk, words64(n_loci)), dtype=torch.int64, device=dev)
+    for r0 in range(0, n_refs, chunk):
+        n = min(chunk, n_refs - r0)
+        gen.allele_rows_device(seed, gen.STREAM_DB, thr_dev, alle[:n], row0=r0)
+        B.fastid_pack(s.ctx, alle[:n], n_loci, packed[:n])
+        host[r0:r0 + n].copy_(packed[:n])
+    del alle, packed
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    recipe = recipe_for(args.config, n_refs=n_refs)
+    q, modes = device_queries(s, seed, recipe, thr_dev, n_loci)
+    n_q = q.size(0)
+    sc = torch.empty((n_q, k), dtype=torch.int32, device=dev)
+    ix = torch.empty((n_q, k), dtype=torch.int64, device=dev)
+    block = args.streamed
+
+    def step():
+        B.fastid_topk_streamed(s.ctx, host, n_loci, B.REFS_TENSOR, block, q, modes, k, T, sc, ix)
+
+    r = time_form(args, s, None, "tensor", step, n_q * n_refs, n_loci, world, dev)
+    # end to end: packed queries in from pinned memory, results out, each step
+    hq = q.cpu().pin_memory()
+    hm = modes.cpu().pin_memory()
+    hs = torch.empty((n_q, k), dtype=torch.int32, pin_memory=True)
+    hi = torch.empty((n_q, k), dtype=torch.int64, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q.copy_(hq, non_blocking=True)
+        modes.copy_(hm, non_blocking=True)
+        step()
+        hs.copy_(sc, non_blocking=True)
+        hi.copy_(ix, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    n_blocks, done, nxt = 0, 0, max(min(block, n_refs, 256), min(block, n_refs) // 8)
+    while done < n_refs:  # the library's block sizes: from block / 8, doubling
+        done += min(nxt, n_refs - done)
+        nxt = min(min(block, n_refs), 2 * nxt)
+        n_blocks += 1
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "e4m3xe4m3->f32", "data": "synthetic",
+            "config": {"workload": w["workload"] + f"_refs_streamed_from_pinned_host_block{block}",
+                       "n_queries": n_q, "n_refs": n_refs, "n_loci": n_loci, "k": k, "threshold": T,
+                       "blocks_per_step": n_blocks, "host_bytes_per_step": int(host.numel() * 8),
+                       "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (references copied from host every step)"},
+            "e2e": {"value": n_q * n_refs * args.steps * world / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(hq.numel() * 8 + hm.numel() + host.numel() * 8),
+                    "d2h_bytes_per_step": int(hs.numel() * 4 + hi.numel() * 8)},
+            "gpu_launches": r["gpu_launches"], "roofline": r["roofline"], "clocks": r["clocks"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.ctx.close()
 
 
 def device_queries(s, seed: int, recipe, thr_dev, n_loci: int):
@@ -645,6 +725,9 @@ def main(argv=None):
     ap.add_argument("--warmup-seconds", type=float, default=3.0, help="c5: warm-up serving time")
     ap.add_argument("--max-wave", type=int, default=4096, help="c5: queries per wave")
     ap.add_argument("--hbm-budget", type=int, default=4 << 30, help="c5: bytes of HBM for in-flight waves")
+    ap.add_argument("--streamed", type=int, default=0, metavar="BLOCK",
+                    help="c1-c3: keep the references in pinned host memory and stream them in blocks of BLOCK "
+                         "references (fastid_topk_streamed)")
 
     args = ap.parse_args(argv)
     w = dict(WORKLOADS[args.config])
@@ -657,6 +740,8 @@ def main(argv=None):
         run_c4(args, w)
     elif args.config == "c5":
         run_c5(args, w)
+    elif args.streamed:
+        run_streamed(args, w)
     else:
         run_gpu(args, w)
 

@@ -223,6 +223,42 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
                              int64_t *hit_r_dev, uint32_t *hit_score_dev, int64_t *hit_count_dev,
                              fastid_stream stream);
 
+/*
+ * fastid_topk over a reference set that stays in HOST memory: the known
+ * profiles are copied to the device block by block, each block is compared
+ * against all queries and its top-k is folded into the running result.  This
+ * is the blocked transfer of Sec. III-C ("Comparing Large Numbers of DNA
+ * Mixtures": all unknowns resident, known profiles sent in blocks), for
+ * databases larger than device memory; unlike the paper's scheme, block
+ * i + 1's host-to-device copy runs on a second stream while block i is
+ * compared, and only the k-lists (never the score block) stay on the device.
+ * Results are identical to fastid_topk on the same references loaded whole.
+ *  refs_host   uint64 [n_refs][ld_words] packed references in host memory,
+ *              bits at loci >= n_loci zero.  Page-locked memory (cudaHostAlloc
+ *              or cudaHostRegister) lets the copies overlap the comparisons;
+ *              pageable memory works but serialises them.  It must stay valid
+ *              and unchanged until the stream has passed this call.
+ *  n_refs      1 .. 2^31 - 1;  flags: 0 or FASTID_REFS_TENSOR (expand each
+ *              block to the FP8 operand and use the tensor form under
+ *              FASTID_FORM_AUTO), as in fastid_load_refs.
+ *  block_refs  largest block (>= 1; the first blocks are smaller, from
+ *              block_refs / 8 doubling, so that the first comparison starts
+ *              early).  Two blocks are on the device at once, each holding
+ *              ceil(n_loci / 64) x 8 bytes per reference as copied plus, for
+ *              the tensor form, its FP8 operand (n_loci rounded up to 128
+ *              bytes per reference) or, for the plain form, padded rows and
+ *              popcounts.
+ *  The other arguments are those of fastid_topk.  Stream-ordered: the call
+ *  enqueues the copies and kernels and returns without waiting for them.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+fastid_status fastid_topk_streamed(fastid_ctx *ctx, const uint64_t *refs_host, int64_t n_refs,
+                                   int32_t n_loci, int64_t ld_words, uint32_t flags,
+                                   int64_t block_refs, const uint64_t *queries_dev, int64_t ld_q,
+                                   int64_t n_q, const uint8_t *modes_dev, int32_t k,
+                                   uint32_t threshold, uint32_t *out_scores_dev,
+                                   int64_t *out_idx_dev, fastid_stream stream);
+
 /* ------------------------------------------------- batched persistent plans */
 /*
  * Many query batches of uneven size against several reference databases
@@ -233,9 +269,9 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
  * A plan fixes panels, batches, k and threshold and owns all scratch memory,
  * so fastid_plan_run allocates nothing and never synchronises: it enqueues an
  * operand-preparation kernel, the persistent compare kernel over the units
- * (panel, 128-query tile, reference tile) of all panels -- CTAs take
- * cost-balanced unit ranges -- and a merge kernel that writes each batch's
- * outputs.  fastid_plan_capture records one run into a CUDA graph;
+ * (panel, 128-query tile, reference tile) of all panels -- each panel spread
+ * over every work group, panels taken one after another, largest first --
+ * and a merge kernel that writes each batch's outputs.  fastid_plan_capture records one run into a CUDA graph;
  * fastid_plan_replay launches that graph.  Between runs the caller may change
  * the contents (not the addresses or sizes) of the batch buffers.
  *

@@ -66,6 +66,8 @@ _PROTOS = {
     "fastid_topk": (_I32, [_P, _P, _P, _I64, _I64, _P, _I32, _U32, _P, _P, _P]),
     "fastid_compare": (_I32, [_P, _P, _P, _I64, _I64, _P, _U32, _I64, _P, _P, _P, _P, _P]),
     "fastid_topk_noalloc": (_I32, [_P, _P, _P, _I64, _I64, _P, _I32, _U32, _P, _P, _P]),
+    "fastid_topk_streamed": (_I32, [_P, _P, _I64, _I32, _I64, _U32, _I64, _P, _I64, _I64, _P, _I32, _U32, _P, _P,
+                                    _P]),
     "fastid_plan_create": (_I32, [_P, _P, _I32, _P, _I32, _I32, _U32, _I32, ctypes.POINTER(_P)]),
     "fastid_plan_run": (_I32, [_P, _P]),
     "fastid_plan_capture": (_I32, [_P, _P]),
@@ -279,6 +281,27 @@ def fastid_topk(ctx: Context, db: RefDB, queries: torch.Tensor, modes: torch.Ten
         raise ValueError("modes / outputs do not match n_q x k")
     ctx.check(load_library().fastid_topk(ctx.handle, db.handle, q, _ld(queries), n_q, m, k, threshold, s, i,
                                          _stream_ptr(stream)))
+
+
+def fastid_topk_streamed(ctx: Context, refs_host: torch.Tensor, n_loci: int, flags: int, block_refs: int,
+                         queries: torch.Tensor, modes: torch.Tensor, k: int, threshold: int,
+                         out_scores: torch.Tensor, out_idx: torch.Tensor, stream=None) -> None:
+    """refs_host: int64 [n_refs][ld_words] packed references in host memory
+    (pin it for overlapped copies); it must outlive the stream's work."""
+    if not isinstance(refs_host, torch.Tensor) or refs_host.is_cuda or refs_host.dtype != torch.int64:
+        raise TypeError("refs_host must be a host int64 torch.Tensor")
+    if refs_host.dim() != 2 or refs_host.stride(1) != 1:
+        raise ValueError("refs_host must be 2-D with contiguous rows")
+    q = _dev(queries, torch.int64, "queries", 2)
+    m = _dev(modes, torch.uint8, "modes", 1)
+    s = _dev(out_scores, torch.int32, "out_scores", 2)
+    i = _dev(out_idx, torch.int64, "out_idx", 2)
+    n_q = queries.size(0)
+    if modes.numel() != n_q or tuple(out_scores.shape) != (n_q, k) or tuple(out_idx.shape) != (n_q, k):
+        raise ValueError("modes / outputs do not match n_q x k")
+    ctx.check(load_library().fastid_topk_streamed(ctx.handle, refs_host.data_ptr(), refs_host.size(0), n_loci,
+                                                  _ld(refs_host), flags, block_refs, q, _ld(queries), n_q, m, k,
+                                                  threshold, s, i, _stream_ptr(stream)))
 
 
 def fastid_compare(ctx: Context, db: RefDB, queries: torch.Tensor, modes: torch.Tensor, threshold: int,

@@ -333,7 +333,9 @@ fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int6
         db->kpad = tensor_kpad(n_loci);
         const size_t fbytes = (size_t)db->n_pad * db->kpad;
         e = cudaMalloc(&db->fp8, fbytes);
-        if (e == cudaSuccess) e = launch_refs_e4m3(db->packed, db->ld64, db->n_pad, db->kpad, db->fp8, (cudaStream_t)stream);
+        if (e == cudaSuccess)
+            e = launch_refs_e4m3(db->packed, db->ld64, db->n_pad, (int32_t)db->ld64, db->n_pad, db->kpad, db->fp8,
+                                 ctx->grid_tensor * 32, (cudaStream_t)stream);
         if (e == cudaSuccess) e = make_operand_map(&db->map_b, db->fp8, db->n_pad, db->kpad, tensor_tile_r());
         if (e == cudaSuccess)
             e = make_operand_map(&db->map_b_half, db->fp8, db->n_pad, db->kpad, tensor_tile_r() / 2);

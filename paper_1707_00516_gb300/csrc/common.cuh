@@ -198,8 +198,10 @@ int tensor_tile_r();
 int tensor_kpad(int32_t n_loci);
 int tensor_grid_target(int device);
 int tensor_pair_clusters(int device);
-cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_rows, int32_t kpad, uint8_t *out,
-                             cudaStream_t s);
+// FP8 reference operand [n_rows][kpad] from packed rows (n_src rows of n_words
+// words exist at stride ld64; zero elsewhere), on at most max_blocks CTAs.
+cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_src, int32_t n_words, int64_t n_rows,
+                             int32_t kpad, uint8_t *out, int max_blocks, cudaStream_t s);
 cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
                                 const uint8_t *modes, int64_t n_q_pad, int32_t kpad, uint8_t *out, float *qconst,
                                 cudaStream_t s);
@@ -210,6 +212,10 @@ cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s
 // one panel, query q's output is out_scores/out_idx row q).
 cudaError_t launch_merge_sched(const uint64_t *partial, const TcLaunch &L, const MergeJob *jobs, int64_t n_jobs,
                                uint32_t *out_scores, int64_t *out_idx, cudaStream_t s);
+// Fold one streamed block's [n_q][k] lists (indices + offset) into the
+// running [n_q][k] lists.
+cudaError_t launch_topk_fold(uint32_t *run_s, int64_t *run_i, const uint32_t *blk_s, const int64_t *blk_i,
+                             int64_t offset, int64_t n_q, int32_t k, cudaStream_t s);
 cudaError_t launch_hits_finish(unsigned long long *count, int64_t capacity, int64_t *hit_q,
                                int64_t *hit_r, uint32_t *hit_score, int64_t *count_out,
                                uint64_t *sort_tmp, uint32_t *status, cudaStream_t s);

@@ -111,6 +111,30 @@ __global__ void topk_merge_sched_kernel(const uint64_t *__restrict__ partial, co
     }
 }
 
+// Streamed reference blocks: fold one block's lists (reference indices
+// relative to the block, offset added here) into the running lists, one warp
+// per query.  Both lists are ascending (score, reference) keys; a bitonic
+// merge keeps the k smallest.
+__global__ void topk_fold_kernel(uint32_t *__restrict__ run_s, int64_t *__restrict__ run_i,
+                                 const uint32_t *__restrict__ blk_s, const int64_t *__restrict__ blk_i,
+                                 int64_t offset, int64_t n_q, int32_t k) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= n_q) return;
+    uint64_t a = KEY_EMPTY, b = KEY_EMPTY;
+    if (lane < k) {
+        const int64_t ia = run_i[q * k + lane];
+        const int64_t ib = blk_i[q * k + lane];
+        if (ia >= 0) a = make_key(run_s[q * k + lane], (uint32_t)ia);
+        if (ib >= 0) b = make_key(blk_s[q * k + lane], (uint32_t)(ib + offset));
+    }
+    const uint64_t v = warp_merge32(a, b, lane);
+    if (lane < k) {
+        run_s[q * k + lane] = v == KEY_EMPTY ? 0xFFFFFFFFu : (uint32_t)(v >> 32);
+        run_i[q * k + lane] = v == KEY_EMPTY ? -1ll : (int64_t)(uint32_t)v;
+    }
+}
+
 // ---- hit list finish ----------------------------------------------------
 // sort_tmp layout: [0] = live count n (as u64), [1] = next power of two of n,
 // then keys[P], then vals (u32)[P].
@@ -273,6 +297,15 @@ cudaError_t launch_merge_sched(const uint64_t *partial, const TcLaunch &L, const
     const int wpb = 8;
     int64_t blocks = (n_jobs + wpb - 1) / wpb;
     topk_merge_sched_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, M, jobs, n_jobs, out_scores, out_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_topk_fold(uint32_t *run_s, int64_t *run_i, const uint32_t *blk_s, const int64_t *blk_i,
+                             int64_t offset, int64_t n_q, int32_t k, cudaStream_t s) {
+    if (n_q == 0) return cudaSuccess;
+    const int wpb = 8;
+    topk_fold_kernel<<<(unsigned)((n_q + wpb - 1) / wpb), wpb * 32, 0, s>>>(run_s, run_i, blk_s, blk_i, offset,
+                                                                             n_q, k);
     return cudaGetLastError();
 }
 

@@ -688,23 +688,27 @@ __device__ __forceinline__ uint32_t bits4_to_e4m3(uint32_t x) {
     return b * 0x38u;
 }
 
-// Reference operand: byte l of row r = R_rl ? 0x38 : 0 for l < kpad (the
-// packed rows are zero past N).  One thread per 16 output bytes.
-__global__ void refs_e4m3_kernel(const uint64_t *__restrict__ packed, int64_t ld64, int64_t n_rows, int32_t kpad,
-                                 uint8_t *__restrict__ out) {
+// Reference operand: byte l of row r = R_rl ? 0x38 : 0 for l < kpad, from
+// packed rows at stride ld64 of which the first n_src rows and n_words words
+// exist (zero elsewhere: padding rows and loci).  One thread per 16 output
+// bytes; streaming loads and stores (each byte is touched once, and the
+// operand is larger than L2), so that a concurrent comparison keeps its L2.
+__global__ void refs_e4m3_kernel(const uint64_t *__restrict__ packed, int64_t ld64, int64_t n_src, int32_t n_words,
+                                 int64_t n_rows, int32_t kpad, uint8_t *__restrict__ out) {
     const int64_t per_row = kpad / 16;
     const int64_t total = n_rows * per_row;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = t / per_row, c = t - r * per_row;
         const int64_t l0 = c * 16;
-        const uint64_t w = packed[r * ld64 + (l0 >> 6)];
+        const int32_t wi = (int32_t)(l0 >> 6);
+        const uint64_t w = (r < n_src && wi < n_words) ? __ldcs(packed + r * ld64 + wi) : 0ull;
         const uint32_t bits = (uint32_t)(w >> (l0 & 63)) & 0xFFFFu;
         uint4 o;
         o.x = bits4_to_e4m3(bits);
         o.y = bits4_to_e4m3(bits >> 4);
         o.z = bits4_to_e4m3(bits >> 8);
         o.w = bits4_to_e4m3(bits >> 12);
-        reinterpret_cast<uint4 *>(out + r * (int64_t)kpad)[c] = o;
+        __stcs(reinterpret_cast<uint4 *>(out + r * (int64_t)kpad) + c, o);
     }
 }
 
@@ -811,12 +815,13 @@ int tensor_tile_q() { return TC_BM; }
 int tensor_tile_r() { return 256; }
 int tensor_kpad(int32_t n_loci) { return (n_loci + TC_BK - 1) / TC_BK * TC_BK; }
 
-cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_rows, int32_t kpad, uint8_t *out,
-                             cudaStream_t s) {
+cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_src, int32_t n_words, int64_t n_rows,
+                             int32_t kpad, uint8_t *out, int max_blocks, cudaStream_t s) {
     int64_t total = n_rows * (kpad / 16);
     int64_t blocks = (total + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    refs_e4m3_kernel<<<(unsigned)blocks, 256, 0, s>>>(packed, ld64, n_rows, kpad, out);
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) return cudaSuccess;
+    refs_e4m3_kernel<<<(unsigned)blocks, 256, 0, s>>>(packed, ld64, n_src, n_words, n_rows, kpad, out);
     return cudaGetLastError();
 }
 

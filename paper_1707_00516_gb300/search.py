@@ -66,6 +66,17 @@ class Searcher:
         B.fastid_topk(self.ctx, db, queries, modes, k, threshold, sc, ix)
         return sc, ix
 
+    def topk_streamed(self, refs_host: torch.Tensor, n_loci: int, queries: torch.Tensor, modes: torch.Tensor,
+                      k: int, threshold: int = B.NO_THRESHOLD, block_refs: int = 1 << 22,
+                      flags: int = B.REFS_TENSOR):
+        """Top-k against packed references kept in host memory (int64
+        [n_refs][words]; pinned for overlapped copies), streamed in blocks."""
+        n_q = queries.shape[0]
+        sc = torch.empty((n_q, k), dtype=torch.int32, device=self.device)
+        ix = torch.empty((n_q, k), dtype=torch.int64, device=self.device)
+        B.fastid_topk_streamed(self.ctx, refs_host, n_loci, flags, block_refs, queries, modes, k, threshold, sc, ix)
+        return sc, ix
+
     def hits(self, db: B.RefDB, queries: torch.Tensor, modes: torch.Tensor, threshold: int, capacity: int):
         hq = torch.empty(capacity, dtype=torch.int64, device=self.device)
         hr = torch.empty(capacity, dtype=torch.int64, device=self.device)
