@@ -108,6 +108,7 @@ struct TcSched {
     int32_t a, b;   // tile groups x reference slices
     int32_t tpx;    // query tiles (pairs) per tile group
     int32_t chunk;  // reference tiles per chunk
+    int32_t pf;     // 1: prefetch the next reference tile into L2 (tpx == 1 only)
 };
 
 // Host-side description of one tensor-form launch over up to TC_MAXP panels.

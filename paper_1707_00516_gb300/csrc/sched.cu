@@ -13,6 +13,14 @@ namespace {
 // (about a third of the 129 MB L2).
 constexpr int64_t L2_CHUNK_BUDGET = 48ll << 20;
 
+// L2 prefetch of the next reference tile (single-tile groups): only where a
+// slice is shared by several groups -- the first to reach a tile would
+// otherwise wait on DRAM -- and all slices' prefetched tiles fit in a quarter
+// of L2.  A lone group per slice gains nothing, and one tile ahead for each of
+// 76-152 slices overflows L2: measured on 20M references at N = 2048, 64-256
+// queries took 10-18 ms with the prefetch against 5.8-8.7 ms without.
+constexpr int64_t PREFETCH_BUDGET = 32ll << 20;
+
 // Relative cost of a reference tile for a group with several query tiles
 // (chunks re-read from L2, top-k lists saved and resumed, no prefetch) over
 // one with a single query tile, which streams its slice once with the next
@@ -36,6 +44,7 @@ int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, co
         sc.a = sc.b = 0;
         sc.tpx = 1;
         sc.chunk = 1;
+        sc.pf = 0;
         if (n_qq[p] <= 0 || n_rt[p] <= 0) continue;
         // a x b grid minimising the busiest group's cost: its reference
         // tiles, weighted as above when it holds several query tiles.
@@ -61,6 +70,7 @@ int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, co
         const int64_t slice = (n_rt[p] + best_b - 1) / best_b;
         if (best_t == 1) {
             sc.chunk = (int32_t)std::max<int64_t>(1, slice);  // one segment per slice: nothing to resume
+            sc.pf = best_a >= 2 && best_b * tile_bytes[p] <= PREFETCH_BUDGET;
         } else {
             const int64_t c = L2_CHUNK_BUDGET / std::max<int64_t>(1, best_b * tile_bytes[p]);
             sc.chunk = (int32_t)std::min<int64_t>(std::max<int64_t>(2, c), std::max<int64_t>(1, slice));

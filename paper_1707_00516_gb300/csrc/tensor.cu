@@ -441,6 +441,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[p])) : "memory");
                 asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[p])) : "memory");
                 const int n_kb = args.panel[p].n_kb;
+                const bool pf = args.panel[p].sc.pf != 0 && W.q_hi - W.q_lo == 1;
                 for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
                     const int64_t re = min(rc + W.chunk, W.r_hi);
                     for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
@@ -462,8 +463,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                                 (int32_t)(rt * BN));
                                 // A group with one query tile streams its slice once: fetch the
                                 // next reference tile into L2 while this one is consumed, so the
-                                // group that reaches a tile first does not wait on DRAM.
-                                if (W.q_hi - W.q_lo == 1 && rt + 1 < W.r_hi)
+                                // group that reaches a tile first does not wait on DRAM (where
+                                // the schedule enables it, see TcSched::pf).
+                                if (pf && rt + 1 < W.r_hi)
                                     tma_prefetch_2d(&maps.b[p], kb * TC_BK,
                                                     (int32_t)((rt + 1) * BN + (PAIR ? rank * (BN / 2) : 0)));
                                 ++issued;
