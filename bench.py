@@ -655,7 +655,7 @@ def run_c5(args, w):
     gen.build_gpu()
     build()
     dev = torch.device("cuda", 0)
-    s = Searcher(0, B.FORM_TENSOR)
+    s = Searcher(0, B.FORM_AUTO)  # FP8 operand for large waves, packed rows for small ones
     seed = gen.config_seed(w["cfg"])
     n_refs, n_loci, k = w["n_refs"], w["n_loci"], w["k"]
     db, thr = build_db(s, seed, n_refs, n_loci, B.REFS_TENSOR)

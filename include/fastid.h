@@ -69,10 +69,18 @@ enum { FASTID_MODE_MISMATCH = 0, FASTID_MODE_UNEXPLAINED = 1 };
 
 /* Compute form used by the comparison calls. */
 enum {
-    FASTID_FORM_AUTO = 0,   /* tensor form when the database holds its operand copy, else plain */
-    FASTID_FORM_PLAIN = 1,  /* packed words, AND + POPC on the integer pipes            */
-    FASTID_FORM_TENSOR = 2  /* 0/1 and +-1 operands in FP8 e4m3 on tcgen05, FP32 accum  */
+    FASTID_FORM_AUTO = 0,          /* see below                                              */
+    FASTID_FORM_PLAIN = 1,         /* packed words, AND + POPC on the integer pipes          */
+    FASTID_FORM_TENSOR = 2,        /* 0/1 and +-1 operands in FP8 e4m3 on tcgen05, FP32 accum,
+                                      the reference operand read from the database's FP8 copy
+                                      (FASTID_REFS_TENSOR), else from its packed rows      */
+    FASTID_FORM_TENSOR_PACKED = 3  /* the tensor form with the reference operand always read
+                                      as packed bits and expanded to FP8 on chip (1/8 of the
+                                      bytes; no FP8 copy needed)                          */
 };
+/* FASTID_FORM_AUTO: the tensor form; its reference operand is the FP8 copy when
+ * the database has one and the call has more than 512 queries, else the packed
+ * rows. */
 
 /* fastid_load_refs flags */
 enum {

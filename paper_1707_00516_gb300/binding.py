@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libfastid.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EUNSUPPORTED, EDEVICE = range(8)
 MODE_MISMATCH, MODE_UNEXPLAINED = 0, 1
-FORM_AUTO, FORM_PLAIN, FORM_TENSOR = 0, 1, 2
+FORM_AUTO, FORM_PLAIN, FORM_TENSOR, FORM_TENSOR_PACKED = 0, 1, 2, 3
 REFS_TENSOR = 1
 MAX_K = 32
 MAX_LOCI = 65536

@@ -237,7 +237,8 @@ const char *fastid_last_error(const fastid_ctx *ctx) { return ctx ? ctx->last_er
 
 fastid_status fastid_set_form(fastid_ctx *ctx, int32_t form) {
     if (!ctx) return FASTID_EINVAL;
-    if (form != FASTID_FORM_AUTO && form != FASTID_FORM_PLAIN && form != FASTID_FORM_TENSOR)
+    if (form != FASTID_FORM_AUTO && form != FASTID_FORM_PLAIN && form != FASTID_FORM_TENSOR &&
+        form != FASTID_FORM_TENSOR_PACKED)
         return fail(ctx, FASTID_EINVAL, "unknown form %d", form);
     ctx->form = form;
     return FASTID_OK;
@@ -329,8 +330,16 @@ fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int6
         return cuda_fail(ctx, e, "copy rows");
     }
     count_launches(ctx, 1);
+    db->kpad = tensor_kpad(n_loci);
+    e = make_packed_map(&db->map_p, db->packed, db->n_pad, db->ld64);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaFree(db->packed);
+        cudaFree(db->norms);
+        delete db;
+        return cuda_fail(ctx, e, "packed operand map");
+    }
     if (flags & FASTID_REFS_TENSOR) {
-        db->kpad = tensor_kpad(n_loci);
         const size_t fbytes = (size_t)db->n_pad * db->kpad;
         e = cudaMalloc(&db->fp8, fbytes);
         if (e == cudaSuccess)
@@ -401,17 +410,9 @@ fastid_status prepare(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q
     return FASTID_OK;
 }
 
-// Chooses the form for a call: *tensor = 1 for the tensor form.
-fastid_status pick_form(fastid_ctx *ctx, const fastid_refdb *db, int *tensor) {
-    *tensor = 0;
-    if (ctx->form == FASTID_FORM_TENSOR) {
-        if (!db->fp8)
-            return fail(ctx, FASTID_EUNSUPPORTED,
-                        "tensor form requested but the database was loaded without FASTID_REFS_TENSOR");
-        *tensor = 1;
-    } else if (ctx->form == FASTID_FORM_AUTO && db->fp8) {
-        *tensor = 1;
-    }
+// 0 plain, 1 tensor form over the FP8 copy, 2 tensor form over the packed rows.
+fastid_status pick_form(fastid_ctx *ctx, const fastid_refdb *db, int64_t n_q, int *tensor) {
+    *tensor = fastid::pick_operand(ctx->form, db->fp8 != nullptr, n_q);
     return FASTID_OK;
 }
 
@@ -431,17 +432,20 @@ struct TensorPrep {
 
 enum ExtraKind { EXTRA_NONE, EXTRA_TOPK, EXTRA_HITS };
 
+// pk: reference operand read as packed rows and expanded on chip (unpaired;
+// queries encoded at half scale to match the expanded 2.0).
 fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q, int64_t ld_q, int64_t n_q,
                              const uint8_t *modes, cudaStream_t s, Scratch &scr, ExtraKind ek, int64_t karg,
-                             size_t *extra_off, TensorPrep *tp) {
+                             size_t *extra_off, TensorPrep *tp, bool pk) {
     TcLaunch &L = tp->L;
     memset(&L, 0, sizeof L);
     const int64_t n_qt = round_up(n_q, tensor_tile_q()) / tensor_tile_q();
-    L.pair = (ctx->pair_clusters > 0 && n_qt >= PAIR_MIN_TILES) ? 1 : 0;
+    L.pk = pk ? 1 : 0;
+    L.pair = (!pk && ctx->pair_clusters > 0 && n_qt >= PAIR_MIN_TILES) ? 1 : 0;
     const int64_t n_q_pad = round_up(n_q, (int64_t)tensor_tile_q() * (L.pair ? 2 : 1));
     const int64_t n_qq = n_q_pad / tensor_tile_q() / (L.pair ? 2 : 1);
     const int64_t n_rt = db->n_pad / tensor_tile_r();
-    const int64_t tile_bytes = (int64_t)tensor_tile_r() * db->kpad;
+    const int64_t tile_bytes = (int64_t)tensor_tile_r() * (pk ? db->ld64 * 8 : db->kpad);
     L.n_groups = make_tensor_schedule(1, &n_qq, &n_rt, &tile_bytes, L.pair ? ctx->pair_clusters : ctx->grid_tensor,
                                       L.pair ? 2 : 1, L.sched, L.order, &L.n_slots);
     if (L.n_groups < 0) return fail(ctx, FASTID_EINVAL, "too many query tiles (top-k slots)");
@@ -457,11 +461,11 @@ fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint
     uint8_t *a = at<uint8_t>(scr.p, o_a);
     float *qconst = at<float>(scr.p, o_c);
     FASTID_CUDA(ctx, launch_queries_e4m3(q, ld_q, n_q, db->n_words64, db->n_loci, modes, n_q_pad, db->kpad, a,
-                                         qconst, s));
+                                         qconst, pk, s));
     count_launches(ctx, 1);
     FASTID_CUDA(ctx, make_operand_map(&L.map_a[0], a, n_q_pad, db->kpad, tensor_tile_q()));
     L.n_panels = 1;
-    L.map_b[0] = L.pair ? db->map_b_half : db->map_b;
+    L.map_b[0] = pk ? db->map_p : L.pair ? db->map_b_half : db->map_b;
     L.n_refs[0] = db->n_refs;
     L.n_q[0] = n_q;
     L.n_rt[0] = n_rt;
@@ -490,7 +494,7 @@ fastid_status fastid_scores(fastid_ctx *ctx, const fastid_refdb *db, const uint6
     if (ld_out < db->n_refs) return fail(ctx, FASTID_EINVAL, "ld_out < n_refs");
     if (n_q > 0 && !out_dev) return fail(ctx, FASTID_EINVAL, "out is NULL");
     int tensor;
-    if ((st = pick_form(ctx, db, &tensor))) return st;
+    if ((st = pick_form(ctx, db, n_q, &tensor))) return st;
     if (n_q == 0) return FASTID_OK;
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -498,7 +502,8 @@ fastid_status fastid_scores(fastid_ctx *ctx, const fastid_refdb *db, const uint6
     size_t xo;
     if (tensor) {
         TensorPrep tp;
-        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_NONE, 0, &xo, &tp)))
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_NONE, 0, &xo, &tp,
+                                 tensor == 2)))
             return st;
         tp.L.epi = out_bytes == 2 ? EPI_SCORES16 : EPI_SCORES32;
         tp.L.threshold = 0xFFFFFFFFu;
@@ -532,7 +537,7 @@ fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_
     if (k < 1 || k > FASTID_MAX_K) return fail(ctx, FASTID_EINVAL, "k out of range: %d", k);
     if (n_q > 0 && (!out_scores_dev || !out_idx_dev)) return fail(ctx, FASTID_EINVAL, "output is NULL");
     int tensor;
-    if ((st = pick_form(ctx, db, &tensor))) return st;
+    if ((st = pick_form(ctx, db, n_q, &tensor))) return st;
     if (n_q == 0) return FASTID_OK;
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -540,7 +545,8 @@ fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_
     if (tensor) {
         TensorPrep tp;
         size_t xo;
-        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_TOPK, k, &xo, &tp)))
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_TOPK, k, &xo, &tp,
+                                 tensor == 2)))
             return st;
         uint64_t *partial = at<uint64_t>(scr.p, xo);
         tp.L.epi = EPI_TOPK;
@@ -582,7 +588,7 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
     if (capacity > 0 && (!hit_q_dev || !hit_r_dev || !hit_score_dev))
         return fail(ctx, FASTID_EINVAL, "hit buffers are NULL");
     int tensor;
-    if ((st = pick_form(ctx, db, &tensor))) return st;
+    if ((st = pick_form(ctx, db, n_q, &tensor))) return st;
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     if (n_q == 0) {
@@ -593,7 +599,8 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
     if (tensor) {
         TensorPrep tp;
         size_t xo;
-        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_HITS, capacity, &xo, &tp)))
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_HITS, capacity, &xo, &tp,
+                                 tensor == 2)))
             return st;
         unsigned long long *count = at<unsigned long long>(scr.p, xo);
         uint64_t *sort_tmp = at<uint64_t>(scr.p, xo + 256);
@@ -635,3 +642,20 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
 }
 
 }  // extern "C"
+
+namespace fastid {
+
+int pick_operand(int form, bool has_fp8, int64_t n_q) {
+    switch (form) {
+        case FASTID_FORM_PLAIN:
+            return 0;
+        case FASTID_FORM_TENSOR_PACKED:
+            return 2;
+        case FASTID_FORM_TENSOR:
+            return has_fp8 ? 1 : 2;
+        default:  // AUTO: a few queries read the operand about once; packed rows are 1/8 of the bytes
+            return has_fp8 && n_q > AUTO_PACKED_MAX_Q ? 1 : 2;
+    }
+}
+
+}  // namespace fastid

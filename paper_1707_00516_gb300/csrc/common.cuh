@@ -115,6 +115,7 @@ struct TcSched {
 struct TcLaunch {
     int32_t n_panels;
     int32_t pair;  // 2-CTA clusters sharing reference stages (groups are clusters, tiles are pairs)
+    int32_t pk;    // packed references expanded on chip (map_b over the packed rows; queries at half scale)
     CUtensorMap map_a[TC_MAXP];
     CUtensorMap map_b[TC_MAXP];
     int64_t n_refs[TC_MAXP];
@@ -205,7 +206,9 @@ cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_src
                              int32_t kpad, uint8_t *out, int max_blocks, cudaStream_t s);
 cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
                                 const uint8_t *modes, int64_t n_q_pad, int32_t kpad, uint8_t *out, float *qconst,
-                                cudaStream_t s);
+                                bool half, cudaStream_t s);
+// TMA map over packed rows for packed-reference (PK) launches.
+cudaError_t make_packed_map(CUtensorMap *map, const uint64_t *packed, int64_t rows, int64_t ld64);
 
 cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s);
 cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s);

@@ -37,7 +37,15 @@ struct fastid_refdb {
     int32_t kpad = 0;            // loci padded to the tensor form's K stage
     CUtensorMap map_b;           // TMA map over fp8 (boxes of K-stage x reference tile)
     CUtensorMap map_b_half;      // same, boxes of half a reference tile (paired launches)
+    CUtensorMap map_p;           // TMA map over packed (boxes of 2 words x 256 refs, packed-operand launches)
     int64_t bytes = 0;
     int device = 0;
 };
 
+namespace fastid {
+// Operand of a comparison call: 0 plain form, 1 tensor form over the FP8 copy,
+// 2 tensor form over the packed rows (expanded on chip).  AUTO takes the FP8
+// copy, when there is one, above AUTO_PACKED_MAX_Q queries.
+constexpr int64_t AUTO_PACKED_MAX_Q = 256;
+int pick_operand(int form, bool has_fp8, int64_t n_q);
+}  // namespace fastid

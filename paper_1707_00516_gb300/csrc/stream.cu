@@ -127,14 +127,17 @@ fastid_status fastid_topk_streamed(fastid_ctx *ctx, const uint64_t *refs_host, i
     const cudaStream_t s = (cudaStream_t)stream;
     const int64_t block = std::min<int64_t>(block_refs, n_refs);
     const int64_t cap = rup(block, ROW_ALIGN);
-    const bool tensor = (flags & FASTID_REFS_TENSOR) != 0;
+    // The operand the per-block comparisons will take (as fastid_topk picks
+    // it): the FP8 operand is built per block only for the tensor form over
+    // the FP8 copy; the plain form and the tensor form over packed rows read
+    // the padded rows.
+    const int op = pick_operand(ctx->form, (flags & FASTID_REFS_TENSOR) != 0, n_q);
+    const bool tensor = op == 1;
+    const bool rows = !tensor;
 
     StreamState st(ctx, s);
     if ((e = st.init()) != cudaSuccess) return scuda(ctx, e, "streams and events");
 
-    // The padded rows and norms serve only the plain form: skipped when the
-    // comparison will take the tensor form.
-    const bool rows = !tensor || ctx->form == FASTID_FORM_PLAIN;
     const int64_t ld64 = rup(n_words, 8);
     const int32_t kpad = tensor_kpad(n_loci);
     for (Slot &sl : st.slot) {
@@ -145,9 +148,11 @@ fastid_status fastid_topk_streamed(fastid_ctx *ctx, const uint64_t *refs_host, i
         db.ld64 = ld64;
         db.flags = flags;
         sl.staging = static_cast<uint64_t *>(st.take((size_t)block * n_words * 8, e));
+        db.kpad = kpad;
         if (rows) {
             db.packed = static_cast<uint64_t *>(st.take((size_t)cap * ld64 * 8, e));
             db.norms = static_cast<uint32_t *>(st.take((size_t)cap * 4, e));
+            if (e == cudaSuccess) e = make_packed_map(&db.map_p, db.packed, cap, ld64);
         }
         if (tensor) {
             db.kpad = kpad;

@@ -35,7 +35,12 @@ namespace {
 
 constexpr int TC_BM = 128;            // queries per tile
 constexpr int TC_BK = 128;            // loci (bytes) per stage
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 192;     // producer, MMA issuer, 4 epilogue warps
+// PK: warps expanding packed references, after the 6 others.  Blocks of 257 to
+// 384 threads get at most 168 registers a thread, which the 16-slot top-k
+// fits (4 expanding warps) and the 32-slot one does not (2).
+__host__ __device__ constexpr int pk_threads(int km) { return km == 16 ? 128 : 64; }
+constexpr uint32_t TC_P_BYTES = 256 * 16;  // packed reference stage: 256 rows x 128 bits
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK;  // 16 KB
 constexpr uint64_t WAIT_NS = 2000000000ull;     // 2 s per wait
 constexpr uint64_t RENDEZVOUS_NS = 50000000ull;  // 50 ms per panel entry, then go on alone
@@ -62,7 +67,9 @@ struct PanelDesc {
 
 struct TcMaps {
     CUtensorMap a[TC_MAXP];  // query operand of each panel (boxes 128 loci x 128 queries)
-    CUtensorMap b[TC_MAXP];  // reference operand of each panel (boxes 128 loci x BN refs, or BN/2 when paired)
+    // reference operand of each panel: FP8 boxes of 128 loci x BN refs (BN/2 when
+    // paired), or, for PK launches, packed boxes of 2 words x 256 refs
+    CUtensorMap b[TC_MAXP];
 };
 
 struct TensorArgs {
@@ -268,6 +275,7 @@ __device__ __forceinline__ void net_insert(int32_t (&ls)[KM], uint32_t (&lr)[KM]
 struct TcSmem {
     uint64_t full[8];
     uint64_t empty[8];
+    uint64_t bfull[8];  // PK: reference stage expanded
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint64_t done;
@@ -373,14 +381,46 @@ __device__ __forceinline__ void list_load(const uint64_t *slot_row, int32_t (&ls
     }
 }
 
+// PK launches: the reference operand arrives packed (TC_P_BYTES per stage,
+// row r at r * 16 bytes: loci 0-63 then 64-127 of the stage) and warps 6.. (pk_threads)
+// expand it into the FP8 stage the MMA reads.  A reference "1" is e4m3 2.0
+// (byte 0x40: one bit per byte, so four loci take one multiply and one mask)
+// and the query operand is encoded at half scale (+-0.5), so D is unchanged.
+// The stage layout is the TMA's 128-byte swizzle: 16-byte chunk c of row r
+// sits at r * 128 + ((c ^ (r & 7)) << 4) from a 1024-byte aligned base.
+__device__ __forceinline__ uint32_t bits4_to_two(uint32_t x) { return ((x & 0xFu) * 0x08102040u) & 0x40404040u; }
+
+template <int NT>
+__device__ __forceinline__ void expand_stage(const uint8_t *sp, uint8_t *sb, int t) {
+#pragma unroll
+    for (int rr = 0; rr < 256 / NT; ++rr) {
+        const int r = t + NT * rr;
+        const uint2 lo = *reinterpret_cast<const uint2 *>(sp + r * 16);
+        const uint2 hi = *reinterpret_cast<const uint2 *>(sp + r * 16 + 8);
+        const uint32_t w[4] = {lo.x, lo.y, hi.x, hi.y};  // 32 loci each
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t bits = w[c >> 1] >> (16 * (c & 1));  // loci 16c .. 16c+15
+            uint4 o;
+            o.x = bits4_to_two(bits);
+            o.y = bits4_to_two(bits >> 4);
+            o.z = bits4_to_two(bits >> 8);
+            o.w = bits4_to_two(bits >> 12);
+            *reinterpret_cast<uint4 *>(sb + r * 128 + ((c ^ (r & 7)) << 4)) = o;
+        }
+    }
+}
+
 // PAIR: 2-CTA clusters; both CTAs walk the same reference tiles for the two
 // query tiles of a pair (rank r takes tile 2 qq + r), and each multicasts half
 // of every reference stage into both CTAs' shared memory (BN = 256 only).
-template <int BN, bool PAIR, int KM>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// PK: packed reference operand expanded on chip (see expand_stage).
+template <int BN, bool PAIR, int KM, bool PK>
+__global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS, 1)
     tensor_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TensorArgs args) {
     using S = TcShape<BN>;
     static_assert(!PAIR || BN == 256, "paired launches use 256-reference tiles");
+    static_assert(!PK || (BN == 256 && !PAIR), "packed-reference launches use unpaired 256-reference tiles");
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned operand stages, then control block, then staging.
     const uint32_t raw = smem_u32(smem_raw);
@@ -388,7 +428,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint8_t *base = smem_raw + pad;
     uint8_t *sA = base;
     uint8_t *sB = base + S::STAGES * TC_A_BYTES;
-    TcSmem *ctl = reinterpret_cast<TcSmem *>(base + S::STAGES * (TC_A_BYTES + S::B_BYTES));
+    uint8_t *sP = base + S::STAGES * (TC_A_BYTES + S::B_BYTES);  // PK only
+    TcSmem *ctl = reinterpret_cast<TcSmem *>(sP + (PK ? S::STAGES * TC_P_BYTES : 0));
     // per-thread staging of one 32-column chunk, [32][128] floats (rare path)
     float *stage_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(ctl) + 256);
 
@@ -404,6 +445,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int s = 0; s < S::STAGES; ++s) {
             mbar_init(smem_u32(&ctl->full[s]), 1);
             mbar_init(smem_u32(&ctl->empty[s]), PAIR ? 2 : 1);  // both CTAs' MMAs release a paired stage
+            if (PK) mbar_init(smem_u32(&ctl->bfull[s]), pk_threads(KM));  // every expanding thread
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl->tfull[a]), 1);
@@ -451,10 +493,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 ok = mbar_wait(smem_u32(&ctl->empty[stage]), phase ^ 1u, abort_flag, args.status, 1);
                                 if (!ok) break;
                                 const uint32_t fb = smem_u32(&ctl->full[stage]);
-                                mbar_expect_tx(fb, TC_A_BYTES + S::B_BYTES);
+                                mbar_expect_tx(fb, TC_A_BYTES + (PK ? TC_P_BYTES : S::B_BYTES));
                                 tma_load_2d(smem_u32(sA + stage * TC_A_BYTES), &maps.a[p], fb, kb * TC_BK,
                                             (int32_t)(qt * TC_BM));
-                                if (PAIR)
+                                if (PK)  // 2 words (128 loci) x 256 references
+                                    tma_load_2d(smem_u32(sP + stage * TC_P_BYTES), &maps.b[p], fb, kb * 2,
+                                                (int32_t)(rt * BN));
+                                else if (PAIR)
                                     tma_load_2d_mc(smem_u32(sB + stage * S::B_BYTES + rank * (S::B_BYTES / 2)),
                                                    &maps.b[p], fb, kb * TC_BK, (int32_t)(rt * BN + rank * (BN / 2)),
                                                    (uint16_t)0x3);
@@ -465,7 +510,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 // next reference tile into L2 while this one is consumed, so the
                                 // group that reaches a tile first does not wait on DRAM (where
                                 // the schedule enables it, see TcSched::pf).
-                                if (pf && rt + 1 < W.r_hi)
+                                if (!PK && pf && rt + 1 < W.r_hi)
                                     tma_prefetch_2d(&maps.b[p], kb * TC_BK,
                                                     (int32_t)((rt + 1) * BN + (PAIR ? rank * (BN / 2) : 0)));
                                 ++issued;
@@ -512,6 +557,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
                             for (int kb = 0; kb < n_kb; ++kb) {
                                 ok = mbar_wait(smem_u32(&ctl->full[stage]), phase, abort_flag, args.status, 4);
+                                if (ok && PK)
+                                    ok = mbar_wait(smem_u32(&ctl->bfull[stage]), phase, abort_flag, args.status, 8);
                                 if (!ok) break;
                                 tc_fence_after();
                                 const uint64_t ad = sw128_desc(smem_u32(sA + stage * TC_A_BYTES));
@@ -541,6 +588,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // Drain: a commit completes after every MMA this thread issued.
             tc_commit(smem_u32(&ctl->done));
             mbar_drain(smem_u32(&ctl->done), 0, args.status, 5);
+        }
+    } else if (PK && warp >= 6) {
+        // ---------------- PK: reference expansion, warps 6.. ----------------
+        const int t = tid - 192;
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int pi = 0; pi < args.n_panels && ok; ++pi) {
+            const int p = args.order[pi];
+            const GroupWork W = group_work(args, wg, p);
+            if (W.q_lo >= W.q_hi) continue;
+            const int n_kb = args.panel[p].n_kb;
+            for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
+                const int64_t re = min(rc + W.chunk, W.r_hi);
+                for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
+                    for (int64_t rt = rc; rt < re && ok; ++rt) {
+                        for (int kb = 0; kb < n_kb; ++kb) {
+                            ok = mbar_wait(smem_u32(&ctl->full[stage]), phase, abort_flag, args.status, 9);
+                            if (!ok) break;
+                            expand_stage<pk_threads(KM)>(sP + stage * TC_P_BYTES, sB + stage * S::B_BYTES, t);
+                            // generic-proxy writes, read next by the tensor core (async proxy)
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            mbar_arrive(smem_u32(&ctl->bfull[stage]));
+                            if (++stage == S::STAGES) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                    }
+                }
+            }
         }
     } else {
         // ---------------- epilogue: warps 2..5 ----------------
@@ -716,9 +794,11 @@ __global__ void refs_e4m3_kernel(const uint64_t *__restrict__ packed, int64_t ld
 
 // Query operand per mode (see the header comment) and c_q for one row, by one
 // warp.  src == nullptr (a padding row) writes zeros.
+// `one` is the e4m3 byte of +1 on this operand's scale: 0x38 (1.0) against the
+// FP8 reference operand, 0x30 (0.5) against PK's expanded references (2.0).
 __device__ __forceinline__ void encode_query_row(const uint64_t *__restrict__ src, bool mis, int32_t n_words,
                                                  int32_t n_loci, int32_t kpad, uint8_t *__restrict__ dst,
-                                                 float *__restrict__ qc, int lane) {
+                                                 float *__restrict__ qc, int lane, uint32_t one = 0x38u) {
     const bool valid = src != nullptr;
     uint32_t pc = 0;
     for (int32_t c = lane; c < kpad / 16; c += 32) {
@@ -736,9 +816,9 @@ __device__ __forceinline__ void encode_query_row(const uint64_t *__restrict__ sr
             const uint32_t qb = (bits >> (4 * i)) & 0xFu;   // Q_l
             const uint32_t nb = (in_n >> (4 * i)) & 0xFu;   // l < N
             // mode 1: 1 - Q_l  -> +1 where l < N and Q_l = 0
-            // mode 0: 1 - 2Q_l -> +1 where Q_l = 0, -1 (0xB8 = 0x38 | 0x80) where Q_l = 1
-            const uint32_t plus = bits4_to_e4m3(nb & ~qb);
-            const uint32_t minus = mis ? (bits4_to_e4m3(qb) | (((qb * 0x00204081u) & 0x01010101u) * 0x80u)) : 0u;
+            // mode 0: 1 - 2Q_l -> +1 where Q_l = 0, -1 (sign bit 0x80 set) where Q_l = 1
+            const uint32_t plus = (((nb & ~qb) * 0x00204081u) & 0x01010101u) * one;
+            const uint32_t minus = mis ? ((qb * 0x00204081u) & 0x01010101u) * (one | 0x80u) : 0u;
             w[i] = plus | minus;
         }
         reinterpret_cast<uint4 *>(dst)[c] = make_uint4(w[0], w[1], w[2], w[3]);
@@ -750,13 +830,14 @@ __device__ __forceinline__ void encode_query_row(const uint64_t *__restrict__ sr
 
 __global__ void queries_e4m3_kernel(const uint64_t *__restrict__ q, int64_t ld_q, int64_t n_q, int32_t n_words,
                                     int32_t n_loci, const uint8_t *__restrict__ modes, int64_t n_q_pad,
-                                    int32_t kpad, uint8_t *__restrict__ out, float *__restrict__ qconst) {
+                                    int32_t kpad, uint8_t *__restrict__ out, float *__restrict__ qconst,
+                                    uint32_t one) {
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n_q_pad; r += warps_total) {
         const bool valid = r < n_q;
         encode_query_row(valid ? q + r * ld_q : nullptr, valid && modes[r] == FASTID_MODE_MISMATCH, n_words, n_loci,
-                         kpad, out + r * (int64_t)kpad, qconst + r, lane);
+                         kpad, out + r * (int64_t)kpad, qconst + r, lane, one);
     }
 }
 
@@ -772,9 +853,9 @@ __global__ void prep_jobs_kernel(const PrepJob *__restrict__ jobs, int64_t n_job
 }
 
 template <int BN>
-size_t tensor_smem(int epi) {
+size_t tensor_smem(int epi, bool pk = false) {
     using S = TcShape<BN>;
-    size_t s = 1024 + S::STAGES * (size_t)(TC_A_BYTES + S::B_BYTES) + 256;
+    size_t s = 1024 + S::STAGES * (size_t)(TC_A_BYTES + S::B_BYTES + (pk ? TC_P_BYTES : 0)) + 256;
     if (epi == EPI_TOPK) s += (size_t)32 * TC_BM * sizeof(float);
     return s;
 }
@@ -829,12 +910,27 @@ cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_src
 
 cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
                                 const uint8_t *modes, int64_t n_q_pad, int32_t kpad, uint8_t *out, float *qconst,
-                                cudaStream_t s) {
+                                bool half, cudaStream_t s) {
     int64_t blocks = (n_q_pad + 7) / 8;
     if (blocks > 65535) blocks = 65535;
     queries_e4m3_kernel<<<(unsigned)blocks, 256, 0, s>>>(q, ld_q, n_q, n_words, n_loci, modes, n_q_pad, kpad, out,
-                                                         qconst);
+                                                         qconst, half ? 0x30u : 0x38u);
     return cudaGetLastError();
+}
+
+// PK reference operand: the packed rows [rows][ld64] uint64 themselves, in
+// boxes of 2 words (128 loci) x 256 references, unswizzled.
+cudaError_t make_packed_map(CUtensorMap *map, const uint64_t *packed, int64_t rows, int64_t ld64) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)ld64, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld64 * 8};
+    cuuint32_t box[2] = {2, 256};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t *>(packed), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s) {
@@ -849,7 +945,7 @@ cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s
 // at once (0 if clusters are unavailable).
 int tensor_pair_clusters(int device) {
     size_t smem = tensor_smem<256>(EPI_TOPK);
-    if (cudaFuncSetAttribute(tensor_kernel<256, true, TC_KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(tensor_kernel<256, true, TC_KMAX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -869,7 +965,7 @@ int tensor_pair_clusters(int device) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tensor_kernel<256, true, TC_KMAX>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, tensor_kernel<256, true, TC_KMAX, false>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -886,16 +982,16 @@ namespace {
 
 // One launch of tensor_kernel<BN, PAIR, KM> over n_groups work groups (2-CTA
 // clusters when paired).
-template <int BN, bool PAIR, int KM>
+template <int BN, bool PAIR, int KM, bool PK = false>
 cudaError_t launch_variant(const TcMaps &maps, const TensorArgs &a, int32_t n_groups, int epi, cudaStream_t s) {
-    const size_t smem = tensor_smem<BN>(epi);
+    const size_t smem = tensor_smem<BN>(epi, PK);
     cudaError_t e =
-        cudaFuncSetAttribute(tensor_kernel<BN, PAIR, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(tensor_kernel<BN, PAIR, KM, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3((PAIR ? 2 : 1) * n_groups);
-    cfg.blockDim = dim3(TC_THREADS);
+    cfg.blockDim = dim3(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -905,7 +1001,7 @@ cudaError_t launch_variant(const TcMaps &maps, const TensorArgs &a, int32_t n_gr
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = PAIR ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, tensor_kernel<BN, PAIR, KM>, maps, a);
+    return cudaLaunchKernelEx(&cfg, tensor_kernel<BN, PAIR, KM, PK>, maps, a);
 }
 
 }  // namespace
@@ -945,6 +1041,11 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
     if (L.pair && bn != 256) return cudaErrorInvalidValue;
     // 16-slot lists when k allows (half the insert network, 32 fewer registers)
     const bool k16 = L.epi != EPI_TOPK || L.k <= 16;
+    if (L.pk) {
+        if (L.pair || bn != 256) return cudaErrorInvalidValue;
+        return k16 ? launch_variant<256, false, 16, true>(maps, a, L.n_groups, L.epi, s)
+                   : launch_variant<256, false, 32, true>(maps, a, L.n_groups, L.epi, s);
+    }
     if (L.pair) return k16 ? launch_variant<256, true, 16>(maps, a, L.n_groups, L.epi, s)
                            : launch_variant<256, true, 32>(maps, a, L.n_groups, L.epi, s);
     if (bn == 128) return k16 ? launch_variant<128, false, 16>(maps, a, L.n_groups, L.epi, s)

@@ -34,7 +34,7 @@ class Searcher:
 
     def default_flags(self) -> int:
         """Database flags the chosen form needs."""
-        return B.REFS_TENSOR if self.form == B.FORM_TENSOR else 0
+        return B.REFS_TENSOR if self.form in (B.FORM_TENSOR, B.FORM_AUTO) else 0
 
     def load_refs_alleles(self, alleles: torch.Tensor, n_loci: int, flags: int | None = None) -> B.RefDB:
         """Pack uint8 allele rows already on the device and load them."""

@@ -13,13 +13,17 @@ from paper_1707_00516_gb300 import binding as B  # noqa: E402
 from paper_1707_00516_gb300.search import Searcher, words64  # noqa: E402
 
 
-@pytest.fixture(scope="module", params=["plain", "tensor"])
+FORMS = {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "packed": B.FORM_TENSOR_PACKED}
+
+
+@pytest.fixture(scope="module", params=sorted(FORMS))
 def searcher(request):
     """One searcher per compute form; databases are loaded with the flags
-    the form needs (the tensor form's e4m3 operand copy)."""
+    the form needs (the tensor form's e4m3 operand copy; none for the plain
+    form and for the tensor form over packed rows)."""
     import __graft_entry__
     __graft_entry__.build()
-    s = Searcher(0, B.FORM_PLAIN if request.param == "plain" else B.FORM_TENSOR)
+    s = Searcher(0, FORMS[request.param])
     yield s
     s.ctx.close()
 

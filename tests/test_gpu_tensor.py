@@ -1,6 +1,7 @@
 """Tensor form (tcgen05, e4m3 operands, FP32 accumulation): exactness at the
-largest loci counts and form selection.  Scores are integers; the test is
-equality with the oracle."""
+largest loci counts and form selection, for both reference operands -- the
+database's FP8 copy and the packed rows expanded on chip.  Scores are
+integers; the test is equality with the oracle."""
 import numpy as np
 import pytest
 
@@ -13,11 +14,11 @@ from paper_1707_00516_gb300 import binding as B  # noqa: E402
 from paper_1707_00516_gb300.search import Searcher, words64  # noqa: E402
 
 
-@pytest.fixture(scope="module")
-def ts():
+@pytest.fixture(scope="module", params=["fp8", "packed"])
+def ts(request):
     import __graft_entry__
     __graft_entry__.build()
-    s = Searcher(0, B.FORM_TENSOR)
+    s = Searcher(0, B.FORM_TENSOR if request.param == "fp8" else B.FORM_TENSOR_PACKED)
     yield s
     s.ctx.close()
 
@@ -81,20 +82,24 @@ def test_uint16_scores(ts):
     assert np.array_equal(_full(ts, R, Q, modes, 1024, torch.int16), exp)
 
 
-def test_tensor_form_needs_operand_copy(ts):
-    R = np.ones((10, 64), np.uint8)
-    db = ts.load_refs_alleles(torch.from_numpy(R).cuda(), 64, flags=0)
-    q = torch.zeros((2, 1), dtype=torch.int64, device="cuda")
-    m = torch.zeros(2, dtype=torch.uint8, device="cuda")
-    sc = torch.empty((2, 4), dtype=torch.int32, device="cuda")
-    ix = torch.empty((2, 4), dtype=torch.int64, device="cuda")
-    with pytest.raises(B.FastIDError) as e:
-        B.fastid_topk(ts.ctx, db, q, m, 4, B.NO_THRESHOLD, sc, ix)
-    assert e.value.status == B.EUNSUPPORTED
-    info = db.info()
-    assert info["flags"] == 0
+def test_tensor_form_on_packed_only_database(ts):
+    """A database loaded without its FP8 copy still takes the tensor form: the
+    packed rows are expanded on chip."""
+    rng = np.random.default_rng(3)
+    R = (rng.random((700, 300)) < 0.4).astype(np.uint8)
+    Q = (rng.random((9, 300)) < 0.4).astype(np.uint8)
+    modes = np.array([0, 1] * 4 + [1], np.uint8)
+    db = ts.load_refs_alleles(torch.from_numpy(R).cuda(), 300, flags=0)
+    assert db.info()["flags"] == 0
+    q = torch.empty((9, words64(300)), dtype=torch.int64, device="cuda")
+    B.fastid_pack(ts.ctx, torch.from_numpy(Q).cuda(), 300, q)
+    sc, ix = ts.topk(db, q, torch.from_numpy(modes).cuda(), 5)
+    mis, une = oracle.scores(R, Q)
+    es, ei = oracle.topk(oracle.select(mis, une, modes), 5, B.NO_THRESHOLD)
+    assert np.array_equal(sc.cpu().numpy().view(np.uint32), es)
+    assert np.array_equal(ix.cpu().numpy(), ei)
     db.close()
-    db2 = ts.load_refs_alleles(torch.from_numpy(R).cuda(), 64)
+    db2 = ts.load_refs_alleles(torch.from_numpy(R).cuda(), 300, flags=B.REFS_TENSOR)
     assert db2.info()["flags"] == B.REFS_TENSOR
     db2.close()
 
