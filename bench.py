@@ -295,10 +295,10 @@ def kernel_source_hash(form: str) -> str:
 # (profiles/), keyed by form and workload, with the source hash it was taken
 # at.  A changed kernel reports null.
 NCU_TRAFFIC = {
-    # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 145.41 GB + dram__bytes_write.sum 9.15 MB
-    "tensor/c3": (145.41e9 + 9.15e6, "47bbfb33ef783709"),
-    # profiles/plain_kernel_c3_2048x20M.md: dram__bytes_read.sum 20.05 GB + dram__bytes_write.sum 16.9 MB
-    "plain/c3": (20.05e9 + 16.9e6, "fa746efa301e2dfc"),
+    # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 147.24 GB + dram__bytes_write.sum 9.66 MB
+    "tensor/c3": (147.24e9 + 9.66e6, "a03684f16e848ee7"),
+    # profiles/plain_kernel_c3_2048x20M.md: dram__bytes_read.sum 20.39 GB + dram__bytes_write.sum 18.2 MB
+    "plain/c3": (20.39e9 + 18.2e6, "6d92bb82b11e790f"),
 }
 
 

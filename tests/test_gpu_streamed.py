@@ -17,11 +17,16 @@ from paper_1707_00516_gb300 import binding as B  # noqa: E402
 from paper_1707_00516_gb300.search import Searcher, words64  # noqa: E402
 
 
-@pytest.fixture(scope="module", params=["plain", "tensor"])
+FORMS = {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "packed": B.FORM_TENSOR_PACKED}
+
+
+@pytest.fixture(scope="module", params=sorted(FORMS))
 def searcher(request):
+    """plain: padded rows per block; tensor: each block expanded to FP8;
+    packed: padded rows per block, expanded on chip by the compare kernel."""
     import __graft_entry__
     __graft_entry__.build()
-    s = Searcher(0, B.FORM_PLAIN if request.param == "plain" else B.FORM_TENSOR)
+    s = Searcher(0, FORMS[request.param])
     s.form_name = request.param
     yield s
     s.ctx.close()
