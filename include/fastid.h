@@ -61,7 +61,7 @@ typedef enum {
     FASTID_ECUDA = 3,        /* a CUDA runtime/driver call failed              */
     FASTID_EOVERFLOW = 4,    /* hit list longer than its capacity              */
     FASTID_ETIMEOUT = 5,     /* a bounded device-side wait ran out             */
-    FASTID_EUNSUPPORTED = 6, /* valid request this build/device cannot serve   */
+    FASTID_EUNSUPPORTED = 6, /* valid request the library or device cannot serve */
     FASTID_EDEVICE = 7       /* a device-side consistency check failed         */
 } fastid_status;
 
