@@ -484,6 +484,19 @@ def run_streamed(args, w):
     sc = torch.empty((n_q, k), dtype=torch.int32, device=dev)
     ix = torch.empty((n_q, k), dtype=torch.int64, device=dev)
     block = args.streamed
+    # host-to-device bandwidth of this machine from pinned memory (1 GiB probe)
+    probe_h = host[: (1 << 30) // host.stride(0) // 8]
+    probe_d = torch.empty_like(probe_h, device=dev)
+    probe_d.copy_(probe_h, non_blocking=True)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for _ in range(3):
+        probe_d.copy_(probe_h, non_blocking=True)
+    p1.record()
+    torch.cuda.synchronize()
+    h2d_gbps = 3 * probe_h.numel() * 8 / (p0.elapsed_time(p1) / 1e3) / 1e9
+    del probe_d
 
     def step():
         B.fastid_topk_streamed(s.ctx, host, n_loci, B.REFS_TENSOR, block, q, modes, k, T, sc, ix)
@@ -515,6 +528,7 @@ def run_streamed(args, w):
             "config": {"workload": w["workload"] + f"_refs_streamed_from_pinned_host_block{block}",
                        "n_queries": n_q, "n_refs": n_refs, "n_loci": n_loci, "k": k, "threshold": T,
                        "blocks_per_step": n_blocks, "host_bytes_per_step": int(host.numel() * 8),
+                       "h2d_gbps_pinned_probe": h2d_gbps,
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (references copied from host every step)"},
             "e2e": {"value": n_q * n_refs * args.steps * world / e2e_s, "unit": UNIT,
