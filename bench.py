@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import os
 import statistics
@@ -284,10 +285,15 @@ def run_reference(args, w):
 # ----------------------------------------------------------------------------
 
 def kernel_source_hash(form: str) -> str:
+    """Hash of the kernel's source with comments and whitespace removed, so
+    that edits to comments alone keep the recorded ncu figures valid."""
     h = hashlib.sha256()
     for f in ("plain.cu" if form == "plain" else "tensor.cu", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_1707_00516_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1707_00516_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
@@ -296,9 +302,9 @@ def kernel_source_hash(form: str) -> str:
 # at.  A changed kernel reports null.
 NCU_TRAFFIC = {
     # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 147.24 GB + dram__bytes_write.sum 9.66 MB
-    "tensor/c3": (147.24e9 + 9.66e6, "a03684f16e848ee7"),
+    "tensor/c3": (147.24e9 + 9.66e6, "9ee9bb26e99deac5"),
     # profiles/plain_kernel_c3_2048x20M.md: dram__bytes_read.sum 20.39 GB + dram__bytes_write.sum 18.2 MB
-    "plain/c3": (20.39e9 + 18.2e6, "6d92bb82b11e790f"),
+    "plain/c3": (20.39e9 + 18.2e6, "d004d3de252d4918"),
 }
 
 

@@ -19,6 +19,8 @@
 //   warp 1       TMEM allocation + MMA issue (one lane)
 //   warps 2..5   epilogue: TMEM -> registers -> score filter -> per-query
 //                top-k (thread = query), hit list or full score matrix
+//   warps 6..    packed-reference launches only (PK): expansion of the packed
+//                reference stage into the FP8 stage (see expand_stage)
 // Two accumulators (2 x 256 TMEM columns) let the epilogue of one reference
 // tile overlap the MMAs of the next.  Every mbarrier wait is bounded: on
 // timeout the thread records FASTID_ETIMEOUT in the status word and the CTA
@@ -33,8 +35,8 @@ namespace fastid {
 
 namespace {
 
-constexpr int TC_BM = 128;            // queries per tile
-constexpr int TC_BK = 128;            // loci (bytes) per stage
+constexpr int TC_BM = 128;          // queries per tile
+constexpr int TC_BK = 128;          // loci (bytes) per stage
 constexpr int TC_THREADS = 192;     // producer, MMA issuer, 4 epilogue warps
 // PK: warps expanding packed references, after the 6 others.  Blocks of 257 to
 // 384 threads get at most 168 registers a thread, which the 16-slot top-k
@@ -422,7 +424,8 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
     static_assert(!PAIR || BN == 256, "paired launches use 256-reference tiles");
     static_assert(!PK || (BN == 256 && !PAIR), "packed-reference launches use unpaired 256-reference tiles");
     extern __shared__ uint8_t smem_raw[];
-    // 1024-byte aligned operand stages, then control block, then staging.
+    // 1024-byte aligned operand stages (queries, references, and for PK the
+    // packed reference stages), then the control block, then staging.
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     uint8_t *base = smem_raw + pad;
