@@ -267,6 +267,24 @@ fastid_status fastid_topk_streamed(fastid_ctx *ctx, const uint64_t *refs_host, i
                                    uint32_t threshold, uint32_t *out_scores_dev,
                                    int64_t *out_idx_dev, fastid_stream stream);
 
+/*
+ * fastid_compare over a reference set in HOST memory: the hit list of
+ * fastid_compare (every (q, r) with score <= threshold, sorted by (q, r), r the
+ * index in refs_host), computed block by block as in fastid_topk_streamed.
+ * Each block's hits are appended to the output buffers, their reference
+ * indices made global, and the whole list is sorted once at the end.  The
+ * reference arguments are those of fastid_topk_streamed, the others those of
+ * fastid_compare (same overflow behaviour: hit_count receives the true count,
+ * and FASTID_EOVERFLOW is reported by the next fastid_sync_status).
+ */
+fastid_status fastid_compare_streamed(fastid_ctx *ctx, const uint64_t *refs_host, int64_t n_refs,
+                                      int32_t n_loci, int64_t ld_words, uint32_t flags,
+                                      int64_t block_refs, const uint64_t *queries_dev, int64_t ld_q,
+                                      int64_t n_q, const uint8_t *modes_dev, uint32_t threshold,
+                                      int64_t capacity, int64_t *hit_q_dev, int64_t *hit_r_dev,
+                                      uint32_t *hit_score_dev, int64_t *hit_count_dev,
+                                      fastid_stream stream);
+
 /* ------------------------------------------------- batched persistent plans */
 /*
  * Many query batches of uneven size against several reference databases

@@ -68,6 +68,8 @@ _PROTOS = {
     "fastid_topk_noalloc": (_I32, [_P, _P, _P, _I64, _I64, _P, _I32, _U32, _P, _P, _P]),
     "fastid_topk_streamed": (_I32, [_P, _P, _I64, _I32, _I64, _U32, _I64, _P, _I64, _I64, _P, _I32, _U32, _P, _P,
                                     _P]),
+    "fastid_compare_streamed": (_I32, [_P, _P, _I64, _I32, _I64, _U32, _I64, _P, _I64, _I64, _P, _U32, _I64, _P,
+                                       _P, _P, _P, _P]),
     "fastid_plan_create": (_I32, [_P, _P, _I32, _P, _I32, _I32, _U32, _I32, ctypes.POINTER(_P)]),
     "fastid_plan_run": (_I32, [_P, _P]),
     "fastid_plan_capture": (_I32, [_P, _P]),
@@ -302,6 +304,32 @@ def fastid_topk_streamed(ctx: Context, refs_host: torch.Tensor, n_loci: int, fla
     ctx.check(load_library().fastid_topk_streamed(ctx.handle, refs_host.data_ptr(), refs_host.size(0), n_loci,
                                                   _ld(refs_host), flags, block_refs, q, _ld(queries), n_q, m, k,
                                                   threshold, s, i, _stream_ptr(stream)))
+
+
+def fastid_compare_streamed(ctx: Context, refs_host: torch.Tensor, n_loci: int, flags: int, block_refs: int,
+                            queries: torch.Tensor, modes: torch.Tensor, threshold: int, hit_q: torch.Tensor,
+                            hit_r: torch.Tensor, hit_score: torch.Tensor, hit_count: torch.Tensor,
+                            stream=None) -> None:
+    """Hit list over packed references in host memory (see fastid_topk_streamed)."""
+    if not isinstance(refs_host, torch.Tensor) or refs_host.is_cuda or refs_host.dtype != torch.int64:
+        raise TypeError("refs_host must be a host int64 torch.Tensor")
+    if refs_host.dim() != 2 or refs_host.stride(1) != 1:
+        raise ValueError("refs_host must be 2-D with contiguous rows")
+    q = _dev(queries, torch.int64, "queries", 2)
+    m = _dev(modes, torch.uint8, "modes", 1)
+    hq = _dev(hit_q, torch.int64, "hit_q", 1)
+    hr = _dev(hit_r, torch.int64, "hit_r", 1)
+    hs = _dev(hit_score, torch.int32, "hit_score", 1)
+    hc = _dev(hit_count, torch.int64, "hit_count", 1)
+    cap = hit_q.numel()
+    if hit_r.numel() != cap or hit_score.numel() != cap:
+        raise ValueError("hit buffers differ in length")
+    n_q = queries.size(0)
+    if modes.numel() != n_q:
+        raise ValueError("modes do not match n_q")
+    ctx.check(load_library().fastid_compare_streamed(ctx.handle, refs_host.data_ptr(), refs_host.size(0), n_loci,
+                                                     _ld(refs_host), flags, block_refs, q, _ld(queries), n_q, m,
+                                                     threshold, cap, hq, hr, hs, hc, _stream_ptr(stream)))
 
 
 def fastid_compare(ctx: Context, db: RefDB, queries: torch.Tensor, modes: torch.Tensor, threshold: int,

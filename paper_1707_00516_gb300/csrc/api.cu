@@ -110,16 +110,6 @@ struct MainTimer {
 
 void count_launches(fastid_ctx *ctx, int64_t n) { ctx->launches += n; }
 
-int64_t hits_finish_launches(int64_t capacity) {
-    if (capacity == 0) return 1;
-    int64_t P = hits_sort_elems(capacity), n = 4;  // prep, keys, first smem sort, unpack
-    for (int64_t size = 2 * 2048; size <= P; size <<= 1) {
-        for (int64_t j = size >> 1; j >= 2048; j >>= 1) ++n;
-        ++n;
-    }
-    return n;
-}
-
 // Pads the queries into the plain layout and computes per-query coefficients.
 struct PreparedQueries {
     uint32_t *q32;
@@ -587,57 +577,24 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
     if (!hit_count_dev) return fail(ctx, FASTID_EINVAL, "hit_count is NULL");
     if (capacity > 0 && (!hit_q_dev || !hit_r_dev || !hit_score_dev))
         return fail(ctx, FASTID_EINVAL, "hit buffers are NULL");
-    int tensor;
-    if ((st = pick_form(ctx, db, n_q, &tensor))) return st;
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     if (n_q == 0) {
         FASTID_CUDA(ctx, cudaMemsetAsync(hit_count_dev, 0, sizeof(int64_t), s));
         return FASTID_OK;
     }
-    Scratch scr(ctx, s);
-    if (tensor) {
-        TensorPrep tp;
-        size_t xo;
-        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_HITS, capacity, &xo, &tp,
-                                 tensor == 2)))
-            return st;
-        unsigned long long *count = at<unsigned long long>(scr.p, xo);
-        uint64_t *sort_tmp = at<uint64_t>(scr.p, xo + 256);
-        FASTID_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
-        tp.L.epi = EPI_HITS;
-        tp.L.threshold = clamp_threshold(threshold, db->n_loci);
-        tp.L.k = 1;
-        tp.L.capacity = capacity;
-        tp.L.hit_q = hit_q_dev;
-        tp.L.hit_r = hit_r_dev;
-        tp.L.hit_score = hit_score_dev;
-        tp.L.hit_count = count;
-        MainTimer tm(ctx, s);
-        FASTID_CUDA(ctx, launch_tensor_multi(256, tp.L, s));
-        tm.done();
-        FASTID_CUDA(ctx, launch_hits_finish(count, capacity, hit_q_dev, hit_r_dev, hit_score_dev, hit_count_dev,
-                                            sort_tmp, ctx->dev_status, s));
-        count_launches(ctx, 1 + hits_finish_launches(capacity));
-        return FASTID_OK;
-    }
-    const int64_t P = hits_sort_elems(capacity);
-    const size_t extra = 256 + (size_t)(2 + P + P / 2 + 1) * 8;
-    PreparedQueries pq;
-    size_t xo;
-    if ((st = prepare(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, extra, &xo, &pq))) return st;
-    unsigned long long *count = at<unsigned long long>(scr.p, xo);
-    uint64_t *sort_tmp = at<uint64_t>(scr.p, xo + 256);
+    // device hit counter and the sort's scratch
+    Scratch aux(ctx, s);
+    FASTID_CUDA(ctx, aux.alloc(fastid::hits_aux_bytes(capacity)));
+    unsigned long long *count = at<unsigned long long>(aux.p, 0);
+    uint64_t *sort_tmp = at<uint64_t>(aux.p, 256);
     FASTID_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
-    Partition part = make_partition((int32_t)(pq.n_q_pad / PL_TQ), db->n_pad / PL_TR, ctx->grid_hits);
-    MainTimer tm(ctx, s);
-    FASTID_CUDA(ctx, launch_plain(EPI_HITS, (const uint32_t *)db->packed, db->norms, db->n_refs, db->ld64 * 2,
-                                  db->n_words64 * 2, pq.q32, pq.coef, n_q, threshold, 1, nullptr, 0, capacity,
-                                  hit_q_dev, hit_r_dev, hit_score_dev, count, nullptr, part, ctx->dev_status, s));
-    tm.done();
-    FASTID_CUDA(ctx, launch_hits_finish(count, capacity, hit_q_dev, hit_r_dev, hit_score_dev, hit_count_dev,
-                                        sort_tmp, ctx->dev_status, s));
-    count_launches(ctx, 1 + hits_finish_launches(capacity));
+    if ((st = fastid::compare_append(ctx, db, queries_dev, ld_q, n_q, modes_dev, threshold, capacity, hit_q_dev,
+                                     hit_r_dev, hit_score_dev, count, s)))
+        return st;
+    FASTID_CUDA(ctx, launch_hits_finish(count, capacity, hit_q_dev, hit_r_dev, hit_score_dev, hit_count_dev, sort_tmp,
+                                        ctx->dev_status, s));
+    count_launches(ctx, hits_finish_launches(capacity));
     return FASTID_OK;
 }
 
@@ -656,6 +613,61 @@ int pick_operand(int form, bool has_fp8, int64_t n_q) {
         default:  // AUTO: a few queries read the operand about once; packed rows are 1/8 of the bytes
             return has_fp8 && n_q > AUTO_PACKED_MAX_Q ? 1 : 2;
     }
+}
+
+size_t hits_aux_bytes(int64_t capacity) {
+    return 256 + (size_t)(2 + hits_sort_elems(capacity) * 3 / 2 + 1) * 8;
+}
+
+fastid_status compare_append(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev, int64_t ld_q,
+                             int64_t n_q, const uint8_t *modes_dev, uint32_t threshold, int64_t capacity,
+                             int64_t *hit_q_dev, int64_t *hit_r_dev, uint32_t *hit_score_dev,
+                             unsigned long long *count, cudaStream_t s) {
+    int tensor;
+    fastid_status st;
+    if ((st = pick_form(ctx, db, n_q, &tensor))) return st;
+    Scratch scr(ctx, s);
+    if (tensor) {
+        TensorPrep tp;
+        size_t xo;
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_NONE, 0, &xo, &tp,
+                                 tensor == 2)))
+            return st;
+        tp.L.epi = EPI_HITS;
+        tp.L.threshold = clamp_threshold(threshold, db->n_loci);
+        tp.L.k = 1;
+        tp.L.capacity = capacity;
+        tp.L.hit_q = hit_q_dev;
+        tp.L.hit_r = hit_r_dev;
+        tp.L.hit_score = hit_score_dev;
+        tp.L.hit_count = count;
+        MainTimer tm(ctx, s);
+        FASTID_CUDA(ctx, launch_tensor_multi(256, tp.L, s));
+        tm.done();
+        count_launches(ctx, 1);
+        return FASTID_OK;
+    }
+    PreparedQueries pq;
+    size_t xo;
+    if ((st = prepare(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, 0, &xo, &pq))) return st;
+    Partition part = make_partition((int32_t)(pq.n_q_pad / PL_TQ), db->n_pad / PL_TR, ctx->grid_hits);
+    MainTimer tm(ctx, s);
+    FASTID_CUDA(ctx, launch_plain(EPI_HITS, (const uint32_t *)db->packed, db->norms, db->n_refs, db->ld64 * 2,
+                                  db->n_words64 * 2, pq.q32, pq.coef, n_q, threshold, 1, nullptr, 0, capacity,
+                                  hit_q_dev, hit_r_dev, hit_score_dev, count, nullptr, part, ctx->dev_status, s));
+    tm.done();
+    count_launches(ctx, 1);
+    return FASTID_OK;
+}
+
+int64_t hits_finish_launches(int64_t capacity) {
+    if (capacity == 0) return 1;
+    int64_t P = hits_sort_elems(capacity), n = 4;  // prep, keys, first smem sort, unpack
+    for (int64_t size = 2 * 2048; size <= P; size <<= 1) {
+        for (int64_t j = size >> 1; j >= 2048; j >>= 1) ++n;
+        ++n;
+    }
+    return n;
 }
 
 }  // namespace fastid

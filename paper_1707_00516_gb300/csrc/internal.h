@@ -48,4 +48,21 @@ namespace fastid {
 // copy, when there is one, above AUTO_PACKED_MAX_Q queries.
 constexpr int64_t AUTO_PACKED_MAX_Q = 256;
 int pick_operand(int form, bool has_fp8, int64_t n_q);
+
+// The hit-list half of fastid_compare: every (q, r) with score <= threshold of
+// this call is appended at atomicAdd(count) (stored while < capacity),
+// reference indices relative to db.  No sort, no reset of the count.
+fastid_status compare_append(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev, int64_t ld_q,
+                             int64_t n_q, const uint8_t *modes_dev, uint32_t threshold, int64_t capacity,
+                             int64_t *hit_q_dev, int64_t *hit_r_dev, uint32_t *hit_score_dev,
+                             unsigned long long *count, cudaStream_t s);
+// Bytes of a hit call's counter (at 0) and sort scratch (at 256).
+size_t hits_aux_bytes(int64_t capacity);
+// Kernel launches of launch_hits_finish for this capacity.
+int64_t hits_finish_launches(int64_t capacity);
+// Streamed blocks, hit lists: snaps[b] = *count, then hits appended by block
+// b (since snaps[b - 1]) get r0 added to their reference index (2 launches,
+// or 1 when r0 == 0).  In reduce.cu.
+cudaError_t launch_hits_block_offset(const unsigned long long *count, unsigned long long *snaps, int64_t b,
+                                     int64_t capacity, int64_t *hit_r, int64_t r0, int grid, cudaStream_t s);
 }  // namespace fastid

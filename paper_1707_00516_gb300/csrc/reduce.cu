@@ -135,6 +135,23 @@ __global__ void topk_fold_kernel(uint32_t *__restrict__ run_s, int64_t *__restri
     }
 }
 
+// Streamed reference blocks, hit lists: after block b's hits are appended,
+// snaps[b] = the count; the hits appended by block b, positions
+// [snaps[b - 1], min(snaps[b], capacity)), get the block's first reference
+// index added.
+__global__ void hits_snap_kernel(const unsigned long long *__restrict__ count, unsigned long long *__restrict__ snap) {
+    *snap = *count;
+}
+
+__global__ void hits_offset_kernel(const unsigned long long *__restrict__ snaps, int64_t b, int64_t capacity,
+                                   int64_t *__restrict__ hit_r, int64_t r0) {
+    const unsigned long long lo = b > 0 ? snaps[b - 1] : 0ull;
+    const unsigned long long hi = min(snaps[b], (unsigned long long)capacity);
+    for (unsigned long long i = lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < hi;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        hit_r[i] += r0;
+}
+
 // ---- hit list finish ----------------------------------------------------
 // sort_tmp layout: [0] = live count n (as u64), [1] = next power of two of n,
 // then keys[P], then vals (u32)[P].
@@ -306,6 +323,13 @@ cudaError_t launch_topk_fold(uint32_t *run_s, int64_t *run_i, const uint32_t *bl
     const int wpb = 8;
     topk_fold_kernel<<<(unsigned)((n_q + wpb - 1) / wpb), wpb * 32, 0, s>>>(run_s, run_i, blk_s, blk_i, offset,
                                                                              n_q, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hits_block_offset(const unsigned long long *count, unsigned long long *snaps, int64_t b,
+                                     int64_t capacity, int64_t *hit_r, int64_t r0, int grid, cudaStream_t s) {
+    hits_snap_kernel<<<1, 1, 0, s>>>(count, snaps + b);
+    if (r0 != 0 && capacity > 0) hits_offset_kernel<<<grid, 256, 0, s>>>(snaps, b, capacity, hit_r, r0);
     return cudaGetLastError();
 }
 

@@ -77,6 +77,17 @@ class Searcher:
         B.fastid_topk_streamed(self.ctx, refs_host, n_loci, flags, block_refs, queries, modes, k, threshold, sc, ix)
         return sc, ix
 
+    def hits_streamed(self, refs_host: torch.Tensor, n_loci: int, queries: torch.Tensor, modes: torch.Tensor,
+                      threshold: int, capacity: int, block_refs: int = 1 << 22, flags: int = B.REFS_TENSOR):
+        """Hit list against packed references kept in host memory."""
+        hq = torch.empty(capacity, dtype=torch.int64, device=self.device)
+        hr = torch.empty(capacity, dtype=torch.int64, device=self.device)
+        hs = torch.empty(capacity, dtype=torch.int32, device=self.device)
+        hc = torch.zeros(1, dtype=torch.int64, device=self.device)
+        B.fastid_compare_streamed(self.ctx, refs_host, n_loci, flags, block_refs, queries, modes, threshold, hq, hr,
+                                  hs, hc)
+        return hq, hr, hs, hc
+
     def hits(self, db: B.RefDB, queries: torch.Tensor, modes: torch.Tensor, threshold: int, capacity: int):
         hq = torch.empty(capacity, dtype=torch.int64, device=self.device)
         hr = torch.empty(capacity, dtype=torch.int64, device=self.device)

@@ -148,3 +148,44 @@ def test_streamed_argument_errors(searcher):
                                sc[:, :0], ix[:, :0])  # k = 0
     with pytest.raises(TypeError):
         B.fastid_topk_streamed(searcher.ctx, refs.cuda(), 64, 0, 4, q, m, 4, B.NO_THRESHOLD, sc, ix)
+
+
+@pytest.mark.parametrize("block", [5000, 1777, 256])
+def test_streamed_hits_match_oracle(searcher, block):
+    """Hit lists over host-resident references: every (q, r) with score <= T,
+    sorted by (q, r), reference indices global."""
+    n_refs, n_loci, T = 5000, 333, 120
+    R, Q, modes = _case(n_refs, n_loci, 50, 40, seed=777)
+    refs = _pack_host(searcher, R, n_loci, pinned=True)
+    q = _q(searcher, Q, n_loci)
+    hq, hr, hs, hc = searcher.hits_streamed(refs, n_loci, q, torch.from_numpy(modes).cuda(), T, 1 << 20,
+                                            block_refs=block, flags=_flags(searcher))
+    torch.cuda.synchronize()
+    assert B.fastid_sync_status(searcher.ctx) == B.OK
+    mis, une = oracle.scores(R, Q)
+    oq, orr, osc = oracle.hits(oracle.select(mis, une, modes), T)
+    n = int(hc.item())
+    assert n == oq.size
+    assert np.array_equal(hq[:n].cpu().numpy(), oq) and np.array_equal(hr[:n].cpu().numpy(), orr)
+    assert np.array_equal(hs[:n].cpu().numpy().view(np.uint32), osc)
+
+
+def test_streamed_hits_overflow(searcher):
+    """More hits than capacity: the true count, a sorted valid subset, and
+    FASTID_EOVERFLOW from the next status read."""
+    n_refs, n_loci, T = 3000, 64, 40
+    R, Q, modes = _case(n_refs, n_loci, 8, 8, seed=31)
+    refs = _pack_host(searcher, R, n_loci, pinned=True)
+    q = _q(searcher, Q, n_loci)
+    mis, une = oracle.scores(R, Q)
+    oq, orr, osc = oracle.hits(oracle.select(mis, une, modes), T)
+    cap = oq.size // 3
+    assert cap > 0
+    hq, hr, hs, hc = searcher.hits_streamed(refs, n_loci, q, torch.from_numpy(modes).cuda(), T, cap, block_refs=700,
+                                            flags=_flags(searcher))
+    assert B.fastid_sync_status(searcher.ctx) == B.EOVERFLOW
+    assert int(hc.item()) == oq.size
+    got = set(zip(hq.cpu().tolist(), hr.cpu().tolist()))
+    assert len(got) == cap and got <= set(zip(oq.tolist(), orr.tolist()))
+    keys = hq.cpu().numpy() * n_refs + hr.cpu().numpy()
+    assert np.all(np.diff(keys) > 0)
