@@ -47,8 +47,8 @@ import gen  # noqa: E402
 WORKLOADS = {
     "c3": dict(workload="2048q_x_20M_refs_N2048_top32_T512", n_q=2048, n_refs=20_000_000, n_loci=2048,
                k=32, threshold=512, cfg=3),
-    "c2": dict(workload="2048mix_x_1M_refs_N4096_top16", n_q=2048, n_refs=1_000_000, n_loci=4096,
-               k=16, threshold=0xFFFFFFFF, cfg=2),
+    "c2": dict(workload="2048mix_x_1M_refs_N4096_top16_T0", n_q=2048, n_refs=1_000_000, n_loci=4096,
+               k=16, threshold=0, cfg=2),
     "c1": dict(workload="64q_x_10k_refs_N1024_top32", n_q=64, n_refs=10_000, n_loci=1024,
                k=32, threshold=0xFFFFFFFF, cfg=1),
     "c4": dict(workload="256_batches_1-512q_panels_N512-2048-8192-16384_x_4M_refs_top16", n_refs=4_000_000,

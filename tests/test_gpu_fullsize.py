@@ -1,6 +1,7 @@
 """Parity at the full workload sizes, in the launch configuration bench.py
 times: 2048 unknowns x 20,000,000 references (N = 2048, top-32, T = 512) and
-2048 mixtures x 1,000,000 references (N = 4096, top-16).
+2048 mixtures x 1,000,000 references (N = 4096, top-16 within score <= 0, and
+the hit list at score <= 0).
 
 The oracle cannot produce the whole score matrix here, so the checks are
   * every returned (query, reference) score equals the oracle's, computed one
@@ -25,7 +26,7 @@ from paper_1707_00516_gb300.search import Searcher  # noqa: E402
 
 CASES = {
     "c3": dict(n_refs=20_000_000, n_loci=2048, k=32, T=512, forms=("tensor", "plain")),
-    "c2": dict(n_refs=1_000_000, n_loci=4096, k=16, T=0xFFFFFFFF, forms=("tensor", "plain")),
+    "c2": dict(n_refs=1_000_000, n_loci=4096, k=16, T=0, forms=("tensor", "plain")),
 }
 
 
@@ -42,18 +43,26 @@ def test_fullsize_sampled_parity(name):
     recipe = bench.recipe_for(name, n_refs=n_refs)
     thr_dev = torch.from_numpy(thr.view(np.int32)).cuda()
     q, modes = bench.device_queries(s, seed, recipe, thr_dev, n_loci)
-    results = {}
+    results, hits = {}, {}
     for form in cfg["forms"]:
         B.fastid_set_form(s.ctx, B.FORM_PLAIN if form == "plain" else B.FORM_TENSOR)
         sc, ix = s.topk(db, q, modes, k, T)
         torch.cuda.synchronize()
         assert B.fastid_sync_status(s.ctx) == B.OK
         results[form] = (sc.cpu().numpy().view(np.uint32).copy(), ix.cpu().numpy().copy())
+        if T == 0:
+            hq, hr, hs, hc = s.hits(db, q, modes, 0, 1 << 22)
+            torch.cuda.synchronize()
+            assert B.fastid_sync_status(s.ctx) == B.OK
+            n = int(hc.item())
+            hits[form] = (hq[:n].cpu().numpy(), hr[:n].cpu().numpy(), hs[:n].cpu().numpy().view(np.uint32))
     db.close()
     s.ctx.close()
     sc, ix = results[cfg["forms"][0]]
     for form in cfg["forms"][1:]:
         assert np.array_equal(results[form][0], sc) and np.array_equal(results[form][1], ix), form
+        if hits:
+            assert all(np.array_equal(a, b) for a, b in zip(hits[form], hits[cfg["forms"][0]])), form
 
     # host side: the queries' alleles (oracle mix of regenerated contributors)
     Q = oracle.mix(gen.source_alleles(recipe, thr), recipe.offsets)
@@ -92,3 +101,19 @@ def test_fullsize_sampled_parity(name):
     for j in range(n_q):
         for r in recipe.planted(j):
             assert r in ix[j], (j, r)
+    # 5. the hit list at score <= 0: every hit scores 0, sorted by (q, r); it
+    #    holds every planted contributor and every sampled zero
+    if hits:
+        hq, hr, hs = hits[cfg["forms"][0]]
+        assert np.all(hs == 0)
+        assert np.all(np.diff(hq * n_refs + hr) > 0)
+        uh, ih = np.unique(hr, return_inverse=True)
+        Rh = gen.allele_rows(seed, gen.STREAM_DB, uh, thr)
+        hmis, hune = oracle.score_pairs(Rh, Q, hq, ih)
+        assert np.all(np.where(recipe.modes[hq] == gen.MODE_MISMATCH, hmis, hune) == 0)
+        hit_set = set(zip(hq.tolist(), hr.tolist()))
+        for j in range(n_q):
+            for r in recipe.planted(j):
+                assert (j, r) in hit_set, (j, r)
+        zq, zr = np.nonzero(ss == 0)
+        assert set(zip(zq.tolist(), sample[zr].tolist())) <= hit_set
