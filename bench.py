@@ -49,7 +49,7 @@ WORKLOADS = {
                k=32, threshold=512, cfg=3),
     "c2": dict(workload="2048mix_x_1M_refs_N4096_top16_T0", n_q=2048, n_refs=1_000_000, n_loci=4096,
                k=16, threshold=0, cfg=2),
-    "c1": dict(workload="64q_x_10k_refs_N1024_top32", n_q=64, n_refs=10_000, n_loci=1024,
+    "c1": dict(workload="64q_x_10k_refs_N1024_full_uint16_matrices", n_q=64, n_refs=10_000, n_loci=1024,
                k=32, threshold=0xFFFFFFFF, cfg=1),
     "c4": dict(workload="256_batches_1-512q_panels_N512-2048-8192-16384_x_4M_refs_top16", n_refs=4_000_000,
                panels=(512, 2048, 8192, 16384), n_batches=256, k=16, threshold=0xFFFFFFFF, cfg=4),
@@ -232,10 +232,11 @@ def cpu_baseline(w: dict, recipe, thr, target_s: float = 12.0):
     t = oracle_sample_step(q, modes, seed, w["n_refs"], thr, np.sort(rng.choice(w["n_refs"], S, replace=False)),
                            w["k"], w["threshold"])
     for _ in range(3):  # calibrate: small samples overstate the per-reference time
-        S = int(min(1 << 16, max(16, S * target_s / max(t, 1e-3))))
+        S_max = min(1 << 16, w["n_refs"])
+        S = int(min(S_max, max(16, S * target_s / max(t, 1e-3))))
         rows = np.sort(rng.choice(w["n_refs"], S, replace=False))
         t = oracle_sample_step(q, modes, seed, w["n_refs"], thr, rows, w["k"], w["threshold"])
-        if t >= 0.6 * target_s or S == 1 << 16:
+        if t >= 0.6 * target_s or S == S_max:
             break
     return {"value": q.shape[0] * S / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"all {q.shape[0]} queries x {S} sampled references (per-locus scores + top-{w['k']}), "
@@ -260,7 +261,7 @@ def run_reference(args, w):
     S = 16
     t = oracle_sample_step(q, modes, seed, w["n_refs"], thr, np.sort(rng.choice(w["n_refs"], S, replace=False)),
                            w["k"], w["threshold"])
-    S = int(min(1 << 16, max(16, S * step_s / max(t, 1e-3))))
+    S = int(min(1 << 16, w["n_refs"], max(16, S * step_s / max(t, 1e-3))))
     times = []
     for i in range(args.warmup + args.steps):
         rows = np.sort(rng.choice(w["n_refs"], S, replace=False))
@@ -408,10 +409,20 @@ def run_gpu(args, w):
     d_mod = torch.from_numpy(modes).to(dev)
     sc = torch.empty((n_q, k), dtype=torch.int32, device=dev)
     ix = torch.empty((n_q, k), dtype=torch.int64, device=dev)
+    full = args.config == "c1"  # the two full uint16 score matrices, one per mode
+    if full:
+        m_mis = torch.full((n_q,), gen.MODE_MISMATCH, dtype=torch.uint8, device=dev)
+        m_une = torch.full((n_q,), gen.MODE_UNEXPLAINED, dtype=torch.uint8, device=dev)
+        out_mis = torch.empty((n_q, n_refs), dtype=torch.int16, device=dev)
+        out_une = torch.empty((n_q, n_refs), dtype=torch.int16, device=dev)
 
     def step():
         q = s.build_queries(d_src, d_off, n_loci)
-        B.fastid_topk(s.ctx, db, q, d_mod, k, T, sc, ix)
+        if full:
+            B.fastid_scores(s.ctx, db, q, m_mis, out_mis)
+            B.fastid_scores(s.ctx, db, q, m_une, out_une)
+        else:
+            B.fastid_topk(s.ctx, db, q, d_mod, k, T, sc, ix)
 
     pairs_per_step = n_q * n_refs
     res = {f: time_form(args, s, db, f, step, pairs_per_step, n_loci, world, dev) for f in forms}
@@ -420,12 +431,28 @@ def run_gpu(args, w):
 
     # end to end through the host-buffer API, headline form
     B.fastid_set_form(s.ctx, B.FORM_PLAIN if head == "plain" else B.FORM_TENSOR)
+    if full:  # contributor alleles in, both score matrices out, through pinned buffers
+        h_src = torch.from_numpy(src).pin_memory()
+        h_mis = torch.empty((n_q, n_refs), dtype=torch.int16, pin_memory=True)
+        h_une = torch.empty((n_q, n_refs), dtype=torch.int16, pin_memory=True)
+
+        def e2e_step():
+            d_src.copy_(h_src, non_blocking=True)
+            step()
+            h_mis.copy_(out_mis, non_blocking=True)
+            h_une.copy_(out_une, non_blocking=True)
+            torch.cuda.synchronize()
+            return h_src.numel(), 4 * n_q * n_refs
+    else:
+        def e2e_step():
+            _, _, h2d_, d2h_ = s.search_host(db, src, off, modes, k, T)
+            return h2d_, d2h_
     for _ in range(max(1, args.warmup // 2)):
-        s.search_host(db, src, off, modes, k, T)
+        e2e_step()
     barrier(world, dev)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _, _, h2d, d2h = s.search_host(db, src, off, modes, k, T)
+        h2d, d2h = e2e_step()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_value = pairs_per_step * args.steps * world / e2e_s
 
@@ -435,6 +462,8 @@ def run_gpu(args, w):
             "data": "synthetic",
             "config": {"workload": w["workload"], "n_queries": n_q, "n_refs": n_refs, "n_loci": n_loci, "k": k,
                        "threshold": T, "form": head, "parallelism": f"replicas{world}",
+                       "output": "both full uint16 score matrices (both scores of every pair)" if full
+                       else "per-query top-k",
                        "l2": "inputs larger than L2 (packed database %.2f GB%s)" % (
                            n_refs * n_loci / 8 / 1e9,
                            ", e4m3 copy %.1f GB" % (n_refs * n_loci / 1e9) if flags else "")},
