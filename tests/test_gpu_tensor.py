@@ -136,3 +136,30 @@ def test_paired_launch_parity(ts, n_q, n_refs, k):
     torch.cuda.synchronize()
     assert B.fastid_sync_status(ts.ctx) == B.OK
     db.close()
+
+
+@pytest.mark.parametrize("n_q", [100, 256, 257, 600])
+def test_auto_form_both_operands(n_q):
+    """FASTID_FORM_AUTO reads the packed rows for calls of at most 256 queries
+    and the FP8 copy above: results equal the oracle on both sides of the
+    switch."""
+    import __graft_entry__
+    __graft_entry__.build()
+    s = Searcher(0, B.FORM_AUTO)
+    rng = np.random.default_rng(n_q)
+    R = (rng.random((3000, 700)) < 0.3).astype(np.uint8)
+    Q = (rng.random((n_q, 700)) < 0.3).astype(np.uint8)
+    modes = (rng.random(n_q) < 0.5).astype(np.uint8)
+    db = s.load_refs_alleles(torch.from_numpy(R).cuda(), 700)
+    assert db.info()["flags"] == B.REFS_TENSOR
+    q = torch.empty((n_q, words64(700)), dtype=torch.int64, device="cuda")
+    B.fastid_pack(s.ctx, torch.from_numpy(Q).cuda(), 700, q)
+    sc, ix = s.topk(db, q, torch.from_numpy(modes).cuda(), 12, 400)
+    torch.cuda.synchronize()
+    assert B.fastid_sync_status(s.ctx) == B.OK
+    mis, une = oracle.scores(R, Q)
+    es, ei = oracle.topk(oracle.select(mis, une, modes), 12, 400)
+    assert np.array_equal(sc.cpu().numpy().view(np.uint32), es)
+    assert np.array_equal(ix.cpu().numpy(), ei)
+    db.close()
+    s.ctx.close()
