@@ -285,6 +285,19 @@ fastid_status fastid_compare_streamed(fastid_ctx *ctx, const uint64_t *refs_host
                                       uint32_t *hit_score_dev, int64_t *hit_count_dev,
                                       fastid_stream stream);
 
+/* ------------------------------------------------------------- diagnostics */
+/*
+ * The library's bounded device wait, on a flag the caller owns: a one-thread
+ * kernel waits until *flag_dev (uint32, device memory) is nonzero, for at
+ * most wait_ms milliseconds (1 .. 10000).  If the limit runs out it records a
+ * timeout in the context's status word -- the next fastid_sync_status returns
+ * FASTID_ETIMEOUT -- exactly as the compare kernels do when one of their
+ * pipeline waits runs out, and the context stays usable.  For testing the
+ * failure path without faulting a GPU.  Errors: EINVAL, ECUDA.
+ */
+fastid_status fastid_wait_flag(fastid_ctx *ctx, const uint32_t *flag_dev, int32_t wait_ms,
+                               fastid_stream stream);
+
 /* ------------------------------------------------- batched persistent plans */
 /*
  * Many query batches of uneven size against several reference databases

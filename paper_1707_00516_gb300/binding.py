@@ -70,6 +70,7 @@ _PROTOS = {
                                     _P]),
     "fastid_compare_streamed": (_I32, [_P, _P, _I64, _I32, _I64, _U32, _I64, _P, _I64, _I64, _P, _U32, _I64, _P,
                                        _P, _P, _P, _P]),
+    "fastid_wait_flag": (_I32, [_P, _P, _I32, _P]),
     "fastid_plan_create": (_I32, [_P, _P, _I32, _P, _I32, _I32, _U32, _I32, ctypes.POINTER(_P)]),
     "fastid_plan_run": (_I32, [_P, _P]),
     "fastid_plan_capture": (_I32, [_P, _P]),
@@ -214,6 +215,12 @@ def fastid_profile_read(ctx: Context, reset: bool = True) -> dict:
     ctx.check(load_library().fastid_profile_read(ctx.handle, ctypes.byref(ms), ctypes.byref(ml),
                                                  ctypes.byref(al), 1 if reset else 0))
     return {"main_ms": ms.value, "main_launches": ml.value, "all_launches": al.value}
+
+
+def fastid_wait_flag(ctx: Context, flag: torch.Tensor, wait_ms: int, stream=None) -> None:
+    """Bounded device wait on flag (int32, one element, device) -- see fastid.h."""
+    f = _dev(flag, torch.int32, "flag", 1)
+    ctx.check(load_library().fastid_wait_flag(ctx.handle, f, wait_ms, _stream_ptr(stream)))
 
 
 def fastid_sync_status(ctx: Context, stream=None) -> int:

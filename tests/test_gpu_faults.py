@@ -1,0 +1,77 @@
+"""Failure paths on the GPU without faulting it: a bounded device wait that
+runs out (a flag nothing sets) is reported as FASTID_ETIMEOUT and leaves the
+context usable; an allocation the device cannot satisfy is FASTID_ENOMEM with
+nothing enqueued."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1707_00516_gb300 import binding as B  # noqa: E402
+from paper_1707_00516_gb300.search import Searcher, words64  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def s():
+    import __graft_entry__
+    __graft_entry__.build()
+    sr = Searcher(0, B.FORM_TENSOR)
+    yield sr
+    sr.ctx.close()
+
+
+def _small_topk(s):
+    rng = np.random.default_rng(5)
+    R = (rng.random((500, 300)) < 0.3).astype(np.uint8)
+    Q = (rng.random((20, 300)) < 0.3).astype(np.uint8)
+    modes = (rng.random(20) < 0.5).astype(np.uint8)
+    db = s.load_refs_alleles(torch.from_numpy(R).cuda(), 300)
+    q = torch.empty((20, words64(300)), dtype=torch.int64, device="cuda")
+    B.fastid_pack(s.ctx, torch.from_numpy(Q).cuda(), 300, q)
+    sc, ix = s.topk(db, q, torch.from_numpy(modes).cuda(), 8)
+    mis, une = oracle.scores(R, Q)
+    es, ei = oracle.topk(oracle.select(mis, une, modes), 8, B.NO_THRESHOLD)
+    ok = np.array_equal(sc.cpu().numpy().view(np.uint32), es) and np.array_equal(ix.cpu().numpy(), ei)
+    db.close()
+    return ok
+
+
+def test_bounded_wait_times_out_and_context_survives(s):
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.fastid_wait_flag(s.ctx, flag, 100)  # nothing sets the flag
+    assert B.fastid_sync_status(s.ctx) == B.ETIMEOUT
+    # the status word was read and cleared; the context still computes
+    assert _small_topk(s)
+    assert B.fastid_sync_status(s.ctx) == B.OK
+
+
+def test_bounded_wait_ends_when_flag_set(s):
+    flag = torch.ones(1, dtype=torch.int32, device="cuda")
+    B.fastid_wait_flag(s.ctx, flag, 5000)
+    assert B.fastid_sync_status(s.ctx) == B.OK
+
+
+def test_wait_flag_arguments(s):
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for ms in (0, 10001):
+        with pytest.raises(B.FastIDError) as e:
+            B.fastid_wait_flag(s.ctx, flag, ms)
+        assert e.value.status == B.EINVAL
+
+
+def test_allocation_failure_is_enomem(s):
+    """A database far larger than the device (2^31 - 1 references x 65536 loci,
+    ~17.6 TB packed): the allocation fails, the call returns FASTID_ENOMEM and
+    the caller's buffer is never read."""
+    small = torch.zeros((4, 1024), dtype=torch.int64, device="cuda")
+    lib = B.load_library()
+    import ctypes
+    out = ctypes.c_void_p()
+    st = lib.fastid_load_refs(s.ctx.handle, small.data_ptr(), (1 << 31) - 1, 65536, 1024, 0, ctypes.byref(out), None)
+    assert st == B.ENOMEM
+    assert not out.value
+    assert _small_topk(s)
+    assert B.fastid_sync_status(s.ctx) == B.OK
