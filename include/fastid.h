@@ -177,6 +177,19 @@ fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int6
                                int32_t n_loci, int64_t ld_words, uint32_t flags,
                                fastid_refdb **out, fastid_stream stream);
 
+/*
+ * Write a database's packed rows to a file (a 32-byte header -- magic
+ * "FASTIDDB", version, N, row count, words per row -- then the rows, locus l
+ * at bit l % 64 of word l / 64), after synchronising the device.  A database
+ * file is the restart point of a service: fastid_load_refs_file reads it back
+ * into a new database, with its FP8 copy if flags asks for one.
+ * Errors: EINVAL (I/O, or a file that is not a consistent database file),
+ * ENOMEM, ECUDA.
+ */
+fastid_status fastid_save_refs(fastid_ctx *ctx, const fastid_refdb *db, const char *path);
+fastid_status fastid_load_refs_file(fastid_ctx *ctx, const char *path, uint32_t flags,
+                                    fastid_refdb **out, fastid_stream stream);
+
 /* Synchronise the device and free a database.  NULL is accepted. */
 fastid_status fastid_free_refs(fastid_ctx *ctx, fastid_refdb *db);
 

@@ -71,6 +71,8 @@ _PROTOS = {
     "fastid_compare_streamed": (_I32, [_P, _P, _I64, _I32, _I64, _U32, _I64, _P, _I64, _I64, _P, _U32, _I64, _P,
                                        _P, _P, _P, _P]),
     "fastid_wait_flag": (_I32, [_P, _P, _I32, _P]),
+    "fastid_save_refs": (_I32, [_P, _P, ctypes.c_char_p]),
+    "fastid_load_refs_file": (_I32, [_P, ctypes.c_char_p, _U32, _P, _P]),
     "fastid_plan_create": (_I32, [_P, _P, _I32, _P, _I32, _I32, _U32, _I32, ctypes.POINTER(_P)]),
     "fastid_plan_run": (_I32, [_P, _P]),
     "fastid_plan_capture": (_I32, [_P, _P]),
@@ -215,6 +217,19 @@ def fastid_profile_read(ctx: Context, reset: bool = True) -> dict:
     ctx.check(load_library().fastid_profile_read(ctx.handle, ctypes.byref(ms), ctypes.byref(ml),
                                                  ctypes.byref(al), 1 if reset else 0))
     return {"main_ms": ms.value, "main_launches": ml.value, "all_launches": al.value}
+
+
+def fastid_save_refs(ctx: Context, db: RefDB, path: str) -> None:
+    ctx.check(load_library().fastid_save_refs(ctx.handle, db.handle, os.fsencode(path)))
+
+
+def fastid_load_refs_file(ctx: Context, path: str, flags: int = 0, stream=None) -> RefDB:
+    h = _P()
+    ctx.check(load_library().fastid_load_refs_file(ctx.handle, os.fsencode(path), flags, ctypes.byref(h),
+                                                   _stream_ptr(stream)))
+    n, l, f, b = _I64(), _I32(), _U32(), _I64()
+    ctx.check(load_library().fastid_refs_info(h, ctypes.byref(n), ctypes.byref(l), ctypes.byref(f), ctypes.byref(b)))
+    return RefDB(ctx, h, n.value, l.value, f.value)
 
 
 def fastid_wait_flag(ctx: Context, flag: torch.Tensor, wait_ms: int, stream=None) -> None:

@@ -75,3 +75,39 @@ def test_allocation_failure_is_enomem(s):
     assert not out.value
     assert _small_topk(s)
     assert B.fastid_sync_status(s.ctx) == B.OK
+
+
+def test_database_file_roundtrip(s, tmp_path):
+    """fastid_save_refs then fastid_load_refs_file: the reloaded database (with
+    and without its FP8 copy) gives the same top-k as the original; a damaged
+    or truncated file is FASTID_EINVAL."""
+    rng = np.random.default_rng(8)
+    n_loci = 777
+    R = (rng.random((2500, n_loci)) < 0.3).astype(np.uint8)
+    Q = (rng.random((40, n_loci)) < 0.3).astype(np.uint8)
+    modes = (rng.random(40) < 0.5).astype(np.uint8)
+    db = s.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci)
+    path = str(tmp_path / "refs.fastiddb")
+    B.fastid_save_refs(s.ctx, db, path)
+    q = torch.empty((40, words64(n_loci)), dtype=torch.int64, device="cuda")
+    B.fastid_pack(s.ctx, torch.from_numpy(Q).cuda(), n_loci, q)
+    m = torch.from_numpy(modes).cuda()
+    sc0, ix0 = s.topk(db, q, m, 9)
+    for flags in (B.REFS_TENSOR, 0):
+        db2 = B.fastid_load_refs_file(s.ctx, path, flags)
+        assert db2.n_refs == 2500 and db2.n_loci == n_loci and db2.info()["flags"] == flags
+        sc1, ix1 = s.topk(db2, q, m, 9)
+        assert torch.equal(sc0, sc1) and torch.equal(ix0, ix1)
+        db2.close()
+    db.close()
+    raw = open(path, "rb").read()
+    bad = tmp_path / "bad.fastiddb"
+    bad.write_bytes(b"NOTADB!!" + raw[8:])
+    with pytest.raises(B.FastIDError) as e:
+        B.fastid_load_refs_file(s.ctx, str(bad), 0)
+    assert e.value.status == B.EINVAL
+    bad.write_bytes(raw[: len(raw) // 2])
+    with pytest.raises(B.FastIDError) as e:
+        B.fastid_load_refs_file(s.ctx, str(bad), 0)
+    assert e.value.status == B.EINVAL
+    assert B.fastid_sync_status(s.ctx) == B.OK
