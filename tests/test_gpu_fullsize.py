@@ -10,7 +10,10 @@ The oracle cannot produce the whole score matrix here, so the checks are
   * no reference of a seeded random sample of 4096 beats a list's k-th entry
     (and every sampled reference that should be in a list is);
   * every planted contributor (score 0) is found;
-  * the plain and tensor forms return identical lists.
+  * the plain and tensor forms return identical lists;
+  * for 32 seeded queries of the 20M-reference workload (16 individuals, 16
+    mixtures) the oracle scans every reference, and its top-k lists equal the
+    returned ones exactly.
 """
 import numpy as np
 import pytest
@@ -23,6 +26,10 @@ pytestmark = pytest.mark.gpu
 
 from paper_1707_00516_gb300 import binding as B  # noqa: E402
 from paper_1707_00516_gb300.search import Searcher  # noqa: E402
+
+UINT32_MAX = 0xFFFFFFFF
+FULL_SCAN_PER_MODE = 16
+SCAN_CHUNK = 1 << 18
 
 CASES = {
     "c3": dict(n_refs=20_000_000, n_loci=2048, k=32, T=512, forms=("tensor", "plain")),
@@ -117,3 +124,49 @@ def test_fullsize_sampled_parity(name):
                 assert (j, r) in hit_set, (j, r)
         zq, zr = np.nonzero(ss == 0)
         assert set(zip(zq.tolist(), sample[zr].tolist())) <= hit_set
+    # 6. the full scan, on the largest workload
+    if name == "c3":
+        _full_scan(seed, thr, Q, recipe.modes, n_refs, k, T, sc, ix)
+
+
+def _full_scan(seed, thr, Q, modes, n_refs, k, T, sc, ix):
+    """The oracle's exact top-k over every reference for a seeded query subset.
+
+    The references are regenerated chunk by chunk by the seeded generator's
+    device form (the same counter-based draws as gen.allele_rows; three rows of
+    every chunk are checked against the host form), copied to the host and
+    scored there by oracle.scores / oracle.select / oracle.topk.  A chunk's
+    lists merge into the running ones by (score, reference).  Each query's
+    running k-th score bounds the next chunk's candidates: an entry above it
+    cannot enter the list, and ties at it are kept, so the result is the same.
+    """
+    rng = np.random.default_rng(seed + 7)
+    sel = np.concatenate([rng.choice(np.nonzero(modes == m)[0], FULL_SCAN_PER_MODE, replace=False)
+                          for m in (gen.MODE_MISMATCH, gen.MODE_UNEXPLAINED)])
+    Qs, ms = Q[sel], modes[sel]
+    best_s = np.full((sel.size, k), UINT32_MAX, np.uint32)
+    best_i = np.full((sel.size, k), -1, np.int64)
+    thr_dev = torch.from_numpy(thr.view(np.int32)).cuda()
+    alle = torch.empty((SCAN_CHUNK, Q.shape[1]), dtype=torch.uint8, device="cuda")
+    for r0 in range(0, n_refs, SCAN_CHUNK):
+        n = min(SCAN_CHUNK, n_refs - r0)
+        gen.allele_rows_device(seed, gen.STREAM_DB, thr_dev, alle[:n], row0=r0)
+        R = alle[:n].cpu().numpy()
+        probe = np.array([0, n // 2, n - 1])
+        assert np.array_equal(R[probe], gen.allele_rows(seed, gen.STREAM_DB, r0 + probe, thr)), r0
+        mis, une = oracle.scores(R, Qs)
+        ss = oracle.select(mis, une, ms)
+        ids = np.arange(r0, r0 + n, dtype=np.int64)
+        for j in range(sel.size):
+            cs, ci = oracle.topk(ss[j:j + 1], k, min(T, int(best_s[j, -1])), ref_ids=ids)
+            s_all = np.concatenate([best_s[j], cs[0]])
+            i_all = np.concatenate([best_i[j], ci[0]])
+            ok = i_all >= 0
+            order = np.lexsort((i_all[ok], s_all[ok]))[:k]
+            best_s[j], best_i[j] = UINT32_MAX, -1
+            best_s[j, :order.size] = s_all[ok][order]
+            best_i[j, :order.size] = i_all[ok][order]
+    del alle
+    torch.cuda.empty_cache()
+    assert np.array_equal(sc[sel], best_s)
+    assert np.array_equal(ix[sel], best_i)
