@@ -725,7 +725,7 @@ def run_c5(args, w):
     hm = m.cpu().numpy()
     offs = np.concatenate([[0], np.cumsum(sizes)])
     srv = Server(s.ctx, db, k, w["threshold"], hbm_budget_bytes=args.hbm_budget, max_wave=args.max_wave,
-                 max_slots=3)
+                 max_slots=args.slots)
     futs, t_sub = [], []
     launches0 = None
     B.fastid_profile_read(s.ctx, reset=True)
@@ -783,8 +783,12 @@ def main(argv=None):
                     help="override the number of references (smaller captures for profiling)")
     ap.add_argument("--seconds", type=float, default=30.0, help="c5: measured serving time")
     ap.add_argument("--warmup-seconds", type=float, default=3.0, help="c5: warm-up serving time")
-    ap.add_argument("--max-wave", type=int, default=4096, help="c5: queries per wave")
+    ap.add_argument("--max-wave", type=int, default=256,
+                    help="c5: queries per wave at most (256: one 2-CTA pair of query tiles, <= 6.7 ms)")
     ap.add_argument("--hbm-budget", type=int, default=4 << 30, help="c5: bytes of HBM for in-flight waves")
+    ap.add_argument("--slots", type=int, default=1,
+                    help="c5: waves in flight at most (one coalesces the most: a wave of up to 128 "
+                         "queries costs about the same as a wave of one)")
     ap.add_argument("--streamed", type=int, default=0, metavar="BLOCK",
                     help="c1-c3: keep the references in pinned host memory and stream them in blocks of BLOCK "
                          "references (fastid_topk_streamed)")

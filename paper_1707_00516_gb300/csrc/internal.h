@@ -45,8 +45,11 @@ struct fastid_refdb {
 namespace fastid {
 // Operand of a comparison call: 0 plain form, 1 tensor form over the FP8 copy,
 // 2 tensor form over the packed rows (expanded on chip).  AUTO takes the FP8
-// copy, when there is one, above AUTO_PACKED_MAX_Q queries.
-constexpr int64_t AUTO_PACKED_MAX_Q = 256;
+// copy, when there is one, above AUTO_PACKED_MAX_Q queries: one query tile
+// streams the packed rows faster (20M references at N = 2048: 4.0 ms against
+// 5.7 ms), two tiles already run faster as a pair over the FP8 copy (6.7 ms
+// against 7.9 ms at k = 16 and 11.2 ms at k = 32).
+constexpr int64_t AUTO_PACKED_MAX_Q = 128;
 int pick_operand(int form, bool has_fp8, int64_t n_q);
 
 // The hit-list half of fastid_compare: every (q, r) with score <= threshold of

@@ -138,11 +138,11 @@ def test_paired_launch_parity(ts, n_q, n_refs, k):
     db.close()
 
 
-@pytest.mark.parametrize("n_q", [100, 256, 257, 600])
+@pytest.mark.parametrize("n_q", [100, 128, 129, 300, 600])
 def test_auto_form_both_operands(n_q):
-    """FASTID_FORM_AUTO reads the packed rows for calls of at most 256 queries
-    and the FP8 copy above: results equal the oracle on both sides of the
-    switch."""
+    """FASTID_FORM_AUTO reads the packed rows for calls of at most 128 queries
+    and the FP8 copy above (paired from two query tiles on; 300 queries pad to
+    four tiles): results equal the oracle on both sides of the switch."""
     import __graft_entry__
     __graft_entry__.build()
     s = Searcher(0, B.FORM_AUTO)
