@@ -251,7 +251,7 @@ def run_reference(args, w):
     import oracle
     oracle.build()
     seed = gen.config_seed(w["cfg"])
-    recipe = recipe_for(args.config, n_refs=w["n_refs"])
+    recipe = recipe_for(args.config, n_refs=w["n_refs"], n_q=w.get("n_q"))
     thr = gen.maf_thresholds(seed, w["n_loci"])
     src, off, modes = query_inputs(recipe, thr)
     q = oracle.mix(src, off)
@@ -319,12 +319,21 @@ def load_peaks():
             "fallback"
 
 
+def form_code(args, form_name):
+    """FASTID_FORM_* of a bench form: plain, or the tensor form over the FP8
+    copy (default) or over the packed rows (--operand packed)."""
+    from paper_1707_00516_gb300 import binding as B
+    if form_name == "plain":
+        return B.FORM_PLAIN
+    return B.FORM_TENSOR_PACKED if args.operand == "packed" else B.FORM_TENSOR
+
+
 def time_form(args, s, db, form_name, step_fn, pairs_per_step, n_loci, world, dev):
     """Warm up and time `args.steps` steps of one compute form; returns the
     device-timed result and the roofline of its main compare kernel."""
     import torch
     from paper_1707_00516_gb300 import binding as B
-    B.fastid_set_form(s.ctx, B.FORM_PLAIN if form_name == "plain" else B.FORM_TENSOR)
+    B.fastid_set_form(s.ctx, form_code(args, form_name))
     for _ in range(args.warmup):
         step_fn()
     torch.cuda.synchronize()
@@ -371,13 +380,15 @@ def time_form(args, s, db, form_name, step_fn, pairs_per_step, n_loci, world, de
         peak = bf16 * FP8_OVER_BF16
         achieved = 2.0 * pairs_per_step * n_loci / (main_s * main_per_step) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "kernel": "tensor_kernel (tcgen05 kind::f8f6f4, EPI_TOPK)",
+                "kernel": "tensor_kernel (tcgen05 kind::f8f6f4, EPI_TOPK" +
+                          (", packed rows expanded on chip)" if args.operand == "packed" else ")"),
                 "peak_source": f"bf16 dense burst {bf16:.1f} TFLOP/s ({peak_src}) x {FP8_OVER_BF16:g} "
                                f"(nominal e4m3/bf16 dense ratio, 4.5/2.25 PFLOP/s)"}
     roof["frac"] = achieved / peak
     roof["kernel_ms"] = main_s * 1e3
     key = f"{form_name}/{args.config}"
-    tr = NCU_TRAFFIC.get(key)
+    # the captured counters hold for the unmodified workload only
+    tr = None if (args.refs or args.queries or args.operand != "fp8") else NCU_TRAFFIC.get(key)
     roof["traffic"] = tr[0] if tr and tr[1] == kernel_source_hash(form_name) else None
     return {"value": value, "ms_per_step": ms_max / args.steps, "roofline": roof, "clocks": clocks,
             "gpu_launches": int(prof["all_launches"])}
@@ -399,9 +410,9 @@ def run_gpu(args, w):
     s = Searcher(local, B.FORM_AUTO)
     seed = gen.config_seed(w["cfg"])
     n_refs, n_loci, k, T = w["n_refs"], w["n_loci"], w["k"], w["threshold"]
-    flags = B.REFS_TENSOR if "tensor" in forms else 0
+    flags = B.REFS_TENSOR if "tensor" in forms and args.operand == "fp8" else 0
     db, thr = build_db(s, seed, n_refs, n_loci, flags)
-    recipe = recipe_for(args.config, n_refs=n_refs)
+    recipe = recipe_for(args.config, n_refs=n_refs, n_q=w.get("n_q"))
     src, off, modes = query_inputs(recipe, thr)
     n_q = recipe.n_queries
     d_src = torch.from_numpy(src).to(dev)
@@ -430,7 +441,7 @@ def run_gpu(args, w):
     hr = res[head]
 
     # end to end through the host-buffer API, headline form
-    B.fastid_set_form(s.ctx, B.FORM_PLAIN if head == "plain" else B.FORM_TENSOR)
+    B.fastid_set_form(s.ctx, form_code(args, head))
     if full:  # contributor alleles in, both score matrices out, through pinned buffers
         h_src = torch.from_numpy(src).pin_memory()
         h_mis = torch.empty((n_q, n_refs), dtype=torch.int16, pin_memory=True)
@@ -461,7 +472,8 @@ def run_gpu(args, w):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32" if head == "plain" else "e4m3xe4m3->f32",
             "data": "synthetic",
             "config": {"workload": w["workload"], "n_queries": n_q, "n_refs": n_refs, "n_loci": n_loci, "k": k,
-                       "threshold": T, "form": head, "parallelism": f"replicas{world}",
+                       "threshold": T, "form": head, "operand": args.operand if head == "tensor" else None,
+                       "parallelism": f"replicas{world}",
                        "output": "both full uint16 score matrices (both scores of every pair)" if full
                        else "per-query top-k",
                        "l2": "inputs larger than L2 (packed database %.2f GB%s)" % (
@@ -513,7 +525,7 @@ def run_streamed(args, w):
     del alle, packed
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    recipe = recipe_for(args.config, n_refs=n_refs)
+    recipe = recipe_for(args.config, n_refs=n_refs, n_q=w.get("n_q"))
     q, modes = device_queries(s, seed, recipe, thr_dev, n_loci)
     n_q = q.size(0)
     sc = torch.empty((n_q, k), dtype=torch.int32, device=dev)
@@ -781,6 +793,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--refs", type=int, default=None,
                     help="override the number of references (smaller captures for profiling)")
+    ap.add_argument("--queries", type=int, default=None,
+                    help="c1-c3: override the number of queries (the recipe's first N)")
+    ap.add_argument("--operand", choices=["fp8", "packed"], default="fp8",
+                    help="c1-c3, tensor form: reference operand read from the FP8 copy or from the packed rows "
+                         "(expanded on chip)")
     ap.add_argument("--seconds", type=float, default=30.0, help="c5: measured serving time")
     ap.add_argument("--warmup-seconds", type=float, default=3.0, help="c5: warm-up serving time")
     ap.add_argument("--max-wave", type=int, default=256,
@@ -798,6 +815,15 @@ def main(argv=None):
     if args.refs:
         w["n_refs"] = args.refs
         w["workload"] = w["workload"].replace("20M", f"{args.refs}").replace("1M", f"{args.refs}")
+    if args.queries:
+        if "n_q" not in w:
+            ap.error("--queries applies to c1, c2 and c3")
+        old = w["n_q"]
+        w["n_q"] = args.queries
+        w["workload"] = w["workload"].replace(f"{old}q_", f"{args.queries}q_").replace(f"{old}mix_",
+                                                                                       f"{args.queries}mix_")
+    if args.operand == "packed":
+        w["workload"] += "_packed_operand"
     if args.impl == "reference":
         run_reference(args, w)
     elif args.config == "c4":
