@@ -705,6 +705,28 @@ def run_c4(args, w):
     s.ctx.close()
 
 
+# Serving defaults: one wave in flight (a wave of up to 128 queries costs about
+# the same as a wave of one, so arrivals are best coalesced into the next wave)
+# of at most 256 queries (one 2-CTA pair of query tiles), in a 4 GB budget.
+C5_DEFAULTS = dict(slots=1, max_wave=256, hbm_budget=4 << 30)
+
+
+def c5_requests(w, seed: int, horizon: float):
+    """Serving requests over `horizon` seconds: Poisson arrival times (mean
+    w["rate"] per second), request sizes log-uniform on 1-256, and one recipe
+    of mixtures of 1-5 contributors over all requests' queries in order (a
+    single contributor is an individual query, mismatch mode)."""
+    rng = np.random.default_rng([seed, 0xC5])
+    n_req = int(w["rate"] * horizon * 1.2) + 16
+    arrivals = np.cumsum(rng.exponential(1.0 / w["rate"], n_req))
+    n_req = int(np.searchsorted(arrivals, horizon))
+    arrivals = arrivals[:n_req]
+    sizes = gen.log_uniform_sizes(n_req, 1, 256, seed, salt=0xC55)
+    rec = gen.recipe_mixtures(int(sizes.sum()), w["n_refs"], w["n_loci"], seed, 1, 5, salt=0xC555)
+    rec.modes = np.where(np.diff(rec.offsets) == 1, gen.MODE_MISMATCH, gen.MODE_UNEXPLAINED).astype(np.uint8)
+    return arrivals, sizes, rec
+
+
 def run_c5(args, w):
     """Serving: Poisson arrivals of query batches against a resident 20M
     database, continuous batching, p50/p99 request latency."""
@@ -721,17 +743,10 @@ def run_c5(args, w):
     n_refs, n_loci, k = w["n_refs"], w["n_loci"], w["k"]
     db, thr = build_db(s, seed, n_refs, n_loci, B.REFS_TENSOR)
     thr_dev = torch.from_numpy(thr.view(np.int32)).to(dev)
-    rng = np.random.default_rng([seed, 0xC5])
     horizon = args.warmup_seconds + args.seconds
-    n_req = int(w["rate"] * horizon * 1.2) + 16
-    gaps = rng.exponential(1.0 / w["rate"], n_req)
-    arrivals = np.cumsum(gaps)
-    n_req = int(np.searchsorted(arrivals, horizon))
-    arrivals = arrivals[:n_req]
-    sizes = gen.log_uniform_sizes(n_req, 1, 256, seed, salt=0xC55)
+    arrivals, sizes, rec = c5_requests(w, seed, horizon)
+    n_req = arrivals.size
     total = int(sizes.sum())
-    rec = gen.recipe_mixtures(total, n_refs, n_loci, seed, 1, 5, salt=0xC555)
-    rec.modes = np.where(np.diff(rec.offsets) == 1, gen.MODE_MISMATCH, gen.MODE_UNEXPLAINED).astype(np.uint8)
     q, m = device_queries(s, seed, rec, thr_dev, n_loci)
     hq = q.cpu().numpy().view(np.uint64)
     hm = m.cpu().numpy()
@@ -800,12 +815,10 @@ def main(argv=None):
                          "(expanded on chip)")
     ap.add_argument("--seconds", type=float, default=30.0, help="c5: measured serving time")
     ap.add_argument("--warmup-seconds", type=float, default=3.0, help="c5: warm-up serving time")
-    ap.add_argument("--max-wave", type=int, default=256,
-                    help="c5: queries per wave at most (256: one 2-CTA pair of query tiles, <= 6.7 ms)")
-    ap.add_argument("--hbm-budget", type=int, default=4 << 30, help="c5: bytes of HBM for in-flight waves")
-    ap.add_argument("--slots", type=int, default=1,
-                    help="c5: waves in flight at most (one coalesces the most: a wave of up to 128 "
-                         "queries costs about the same as a wave of one)")
+    ap.add_argument("--max-wave", type=int, default=C5_DEFAULTS["max_wave"], help="c5: queries per wave at most")
+    ap.add_argument("--hbm-budget", type=int, default=C5_DEFAULTS["hbm_budget"],
+                    help="c5: bytes of HBM for in-flight waves")
+    ap.add_argument("--slots", type=int, default=C5_DEFAULTS["slots"], help="c5: waves in flight at most")
     ap.add_argument("--streamed", type=int, default=0, metavar="BLOCK",
                     help="c1-c3: keep the references in pinned host memory and stream them in blocks of BLOCK "
                          "references (fastid_topk_streamed)")
