@@ -109,6 +109,12 @@ struct TcSched {
     int32_t tpx;    // query tiles (pairs) per tile group
     int32_t chunk;  // reference tiles per chunk
     int32_t pf;     // 1: prefetch the next reference tile into L2 (tpx == 1 only)
+    // Tail: groups a*b .. a*b + t_groups - 1 (otherwise idle) take reference
+    // tiles [r_main, n_rt) for t_tpx query tiles (pairs) each, in chunks of
+    // t_chunk; the a x b grid covers [0, r_main).  t_groups == 0: no tail,
+    // r_main == n_rt.
+    int32_t r_main;
+    int32_t t_groups, t_tpx, t_chunk;
 };
 
 // Host-side description of one tensor-form launch over up to TC_MAXP panels.

@@ -105,6 +105,13 @@ __global__ void topk_merge_sched_kernel(const uint64_t *__restrict__ partial, co
         uint64_t v = lane < k ? partial[(slot * k + lane) * TC_TILE_Q + ql] : KEY_EMPTY;
         acc = warp_merge32(acc, v, lane);
     }
+    if (sc.t_groups > 0) {  // the tail group holding this query tile (see TcSched)
+        const int64_t cpg = M.pair ? 2 : 1;
+        const int64_t t = qq / sc.t_tpx, lt = qq - t * sc.t_tpx;
+        const int64_t slot = (int64_t)sc.slot0 + (int64_t)sc.a * sc.b * cpg * sc.tpx + (t * cpg + rank) * sc.t_tpx + lt;
+        uint64_t v = lane < k ? partial[(slot * k + lane) * TC_TILE_Q + ql] : KEY_EMPTY;
+        acc = warp_merge32(acc, v, lane);
+    }
     if (lane < k) {
         jb.out_s[lane] = acc == KEY_EMPTY ? 0xFFFFFFFFu : (uint32_t)(acc >> 32);
         jb.out_i[lane] = acc == KEY_EMPTY ? -1ll : (int64_t)(uint32_t)acc;

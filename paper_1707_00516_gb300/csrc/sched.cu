@@ -30,6 +30,18 @@ constexpr int64_t PREFETCH_BUDGET = 32ll << 20;
 constexpr double TPX_PENALTY = 0.08;
 constexpr double SLICE_PENALTY = 0.005;
 
+// A tail (see TcSched) is added where it shortens the busiest group by at
+// least this fraction.
+constexpr double TAIL_MIN_GAIN = 0.02;
+
+// Relative cost of a reference tile in a tail group (several query tiles over
+// chunks re-read from L2, lists saved and resumed) against one in the grid
+// (one query tile, prefetched stream).  Measured on 2048 queries x 20M
+// references at N = 2048 (a tail of 4 groups x 2 tile pairs): 1.2, 1.3 and 1.4
+// all gave 40.7 ms against 41.8 ms without a tail, while the grid model's own
+// penalty (1.1) left the tail finishing last (43.3 ms).
+constexpr double TAIL_COST = 1.3;
+
 }  // namespace
 
 int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, const int64_t *tile_bytes,
@@ -45,6 +57,10 @@ int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, co
         sc.tpx = 1;
         sc.chunk = 1;
         sc.pf = 0;
+        sc.r_main = (int32_t)std::max<int64_t>(n_rt[p], 0);
+        sc.t_groups = 0;
+        sc.t_tpx = 1;
+        sc.t_chunk = 1;
         if (n_qq[p] <= 0 || n_rt[p] <= 0) continue;
         // a x b grid minimising the busiest group's cost: its reference
         // tiles, weighted as above when it holds several query tiles.
@@ -75,8 +91,30 @@ int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, co
             const int64_t c = L2_CHUNK_BUDGET / std::max<int64_t>(1, best_b * tile_bytes[p]);
             sc.chunk = (int32_t)std::min<int64_t>(std::max<int64_t>(2, c), std::max<int64_t>(1, slice));
         }
-        groups = std::max<int32_t>(groups, sc.a * sc.b);
-        slots += (int64_t)sc.a * sc.b * ctas_per_group * sc.tpx;
+        // Tail: groups the a x b grid leaves idle take the last reference
+        // tiles for several query tiles each, and the grid's slices shrink so
+        // that both finish together: r_main / b = t_tpx * (n_rt - r_main) * cost,
+        // with the several-query-tile cost of the model above.
+        const int64_t spare = (int64_t)G - best_a * best_b;
+        if (best_t == 1 && best_a >= 2 && spare >= 1) {
+            const int64_t tg = std::min<int64_t>(spare, best_a);
+            const int64_t tt = (best_a + tg - 1) / tg;
+            const int64_t tg_eff = (best_a + tt - 1) / tt;
+            const double f = (double)tt * TAIL_COST;
+            const int64_t r_main = (int64_t)((double)n_rt[p] * f / (1.0 / (double)best_b + f));
+            const double old_busy = (double)((n_rt[p] + best_b - 1) / best_b);
+            const double new_busy = (double)((r_main + best_b - 1) / best_b);
+            if (r_main >= best_b && r_main < n_rt[p] && new_busy <= old_busy * (1.0 - TAIL_MIN_GAIN)) {
+                sc.r_main = (int32_t)r_main;
+                sc.t_groups = (int32_t)tg_eff;
+                sc.t_tpx = (int32_t)tt;
+                const int64_t c = L2_CHUNK_BUDGET / std::max<int64_t>(1, tg_eff * tile_bytes[p]);
+                sc.t_chunk = (int32_t)std::min<int64_t>(std::max<int64_t>(2, c), n_rt[p] - r_main);
+                if (best_t == 1) sc.chunk = (int32_t)std::max<int64_t>(1, (r_main + best_b - 1) / best_b);
+            }
+        }
+        groups = std::max<int32_t>(groups, sc.a * sc.b + sc.t_groups);
+        slots += (int64_t)sc.a * sc.b * ctas_per_group * sc.tpx + (int64_t)sc.t_groups * ctas_per_group * sc.t_tpx;
         if (slots > INT32_MAX) return -1;
     }
     // Largest panel first: every group enters it together, so the groups of

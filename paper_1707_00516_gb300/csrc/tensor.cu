@@ -330,27 +330,41 @@ __device__ __forceinline__ void panel_rendezvous(unsigned int *ctr, bool wait) {
 }
 
 // The work of one group (see TcSched) in panel p: reference tiles
-// [r_lo, r_hi) walked in chunks, query tiles (pairs) [q_lo, q_hi).  Empty
-// (q_lo == q_hi) when the panel's grid has no group wg.
+// [r_lo, r_hi) walked in chunks, query tiles (pairs) [q_lo, q_hi), top-k
+// slots from slot (this CTA's first; one per query tile).  Empty
+// (q_lo == q_hi) when the panel's grid and tail have no group wg.
 struct GroupWork {
     int64_t r_lo, r_hi;
     int32_t q_lo, q_hi, chunk;
+    int64_t slot;
 };
 
-__device__ __forceinline__ GroupWork group_work(const TensorArgs &a, int64_t wg, int p) {
+// cpg: CTAs per group (2 when paired), rank: this CTA's rank in its group.
+__device__ __forceinline__ GroupWork group_work(const TensorArgs &a, int64_t wg, int p, int cpg, int rank) {
     GroupWork w;
     w.r_lo = w.r_hi = 0;
     w.q_lo = w.q_hi = 0;
     w.chunk = 1;
+    w.slot = 0;
     const TcSched &sc = a.panel[p].sc;
-    if (sc.n_qq > 0 && wg < (int64_t)sc.a * sc.b) {
+    const int64_t grid = (int64_t)sc.a * sc.b;
+    if (sc.n_qq <= 0) return w;
+    if (wg < grid) {
         const int64_t x = wg / sc.b, y = wg - x * sc.b;
-        const int64_t n_rt = a.panel[p].n_rt;
-        w.r_lo = y * n_rt / sc.b;
-        w.r_hi = (y + 1) * n_rt / sc.b;
+        w.r_lo = y * (int64_t)sc.r_main / sc.b;
+        w.r_hi = (y + 1) * (int64_t)sc.r_main / sc.b;
         w.q_lo = (int32_t)(x * sc.tpx);
         w.q_hi = (int32_t)min((int64_t)sc.n_qq, (x + 1) * sc.tpx);
         w.chunk = sc.chunk;
+        w.slot = (int64_t)sc.slot0 + (wg * cpg + rank) * sc.tpx;
+    } else if (wg < grid + sc.t_groups) {
+        const int64_t t = wg - grid;
+        w.r_lo = sc.r_main;
+        w.r_hi = a.panel[p].n_rt;
+        w.q_lo = (int32_t)min((int64_t)sc.n_qq, t * sc.t_tpx);
+        w.q_hi = (int32_t)min((int64_t)sc.n_qq, (t + 1) * sc.t_tpx);
+        w.chunk = sc.t_chunk;
+        w.slot = (int64_t)sc.slot0 + grid * cpg * sc.tpx + (t * cpg + rank) * sc.t_tpx;
     }
     return w;
 }
@@ -480,7 +494,7 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
             bool ok = true;
             for (int pi = 0; pi < args.n_panels && ok; ++pi) {
                 const int p = args.order[pi];
-                const GroupWork W = group_work(args, wg, p);
+                const GroupWork W = group_work(args, wg, p, PAIR ? 2 : 1, rank);
                 if (pi > 0 && args.arrive) panel_rendezvous(args.arrive + pi, W.q_lo < W.q_hi);
                 if (W.q_lo >= W.q_hi) continue;
                 asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[p])) : "memory");
@@ -547,7 +561,7 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
             bool ok = true;
             for (int pi = 0; pi < args.n_panels && ok; ++pi) {
                 const int p = args.order[pi];
-                const GroupWork W = group_work(args, wg, p);
+                const GroupWork W = group_work(args, wg, p, PAIR ? 2 : 1, rank);
                 if (W.q_lo >= W.q_hi) continue;
                 const int n_kb = args.panel[p].n_kb;
                 for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
@@ -600,7 +614,7 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
         bool ok = true;
         for (int pi = 0; pi < args.n_panels && ok; ++pi) {
             const int p = args.order[pi];
-            const GroupWork W = group_work(args, wg, p);
+            const GroupWork W = group_work(args, wg, p, PAIR ? 2 : 1, rank);
             if (W.q_lo >= W.q_hi) continue;
             const int n_kb = args.panel[p].n_kb;
             for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
@@ -638,7 +652,7 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
         bool ok = true;
         for (int pi = 0; pi < args.n_panels && ok; ++pi) {
             const int p = args.order[pi];
-            const GroupWork W = group_work(args, wg, p);
+            const GroupWork W = group_work(args, wg, p, PAIR ? 2 : 1, rank);
             if (W.q_lo >= W.q_hi) continue;
             const PanelDesc &P = args.panel[p];
             const int64_t n_refs = P.n_refs;
@@ -650,8 +664,7 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                     const bool qvalid = q < P.n_q;
                     const float cq = P.qconst[q];
                     const float cut0 = qvalid ? tplus1 - cq : -__int_as_float(0x7f800000);
-                    uint64_t *slot = args.partial +
-                                     ((int64_t)P.sc.slot0 + c * P.sc.tpx + (qq - W.q_lo)) * (int64_t)k * TC_BM + row;
+                    uint64_t *slot = args.partial + (W.slot + (qq - W.q_lo)) * (int64_t)k * TC_BM + row;
                     if (topk && rc > W.r_lo) {
                         list_load(slot, ls, lr, k);
                     } else {
