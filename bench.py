@@ -454,9 +454,13 @@ def run_gpu(args, w):
             h_une.copy_(out_une, non_blocking=True)
             torch.cuda.synchronize()
             return h_src.numel(), 4 * n_q * n_refs
-    else:
+    else:  # the inputs wait in pinned host memory, as an application's would
+        h_src = torch.from_numpy(src).pin_memory()
+        h_off = torch.from_numpy(off).pin_memory()
+        h_mod = torch.from_numpy(modes).pin_memory()
+
         def e2e_step():
-            _, _, h2d_, d2h_ = s.search_host(db, src, off, modes, k, T)
+            _, _, h2d_, d2h_ = s.search_host(db, h_src, h_off, h_mod, k, T)
             return h2d_, d2h_
     for _ in range(max(1, args.warmup // 2)):
         e2e_step()

@@ -2,9 +2,9 @@
 queries given as contributor allele rows, on the device or on the host.
 
 The host path (`Searcher.search_host`) is what an application calls with
-numpy arrays: it copies the inputs to the device through pinned staging
-buffers, runs pack -> mix -> top-k (or hits) in the library's kernels and
-copies the result back.
+host inputs (numpy arrays, staged through pinned buffers, or pinned CPU
+tensors, copied directly): it copies them to the device, runs pack -> mix ->
+top-k in the library's kernels and copies the result back.
 """
 from __future__ import annotations
 
@@ -119,18 +119,29 @@ class Searcher:
         v.numpy()[...] = arr
         return v
 
-    def search_host(self, db: B.RefDB, src_alleles: np.ndarray, offsets: np.ndarray, modes: np.ndarray,
-                    k: int, threshold: int = B.NO_THRESHOLD):
+    def _host_input(self, name, x, dtype: np.dtype) -> torch.Tensor:
+        """A pinned host tensor holding x: x itself when it already is a
+        contiguous pinned CPU tensor of that dtype, else a staged copy."""
+        if isinstance(x, torch.Tensor):
+            if x.device.type != "cpu" or x.dtype != _TORCH[np.dtype(dtype)]:
+                raise ValueError(f"{name}: expected a CPU tensor of {np.dtype(dtype)}")
+            if x.is_pinned() and x.is_contiguous():
+                return x
+            x = x.numpy()
+        return self._pin(name, np.ascontiguousarray(x, dtype))
+
+    def search_host(self, db: B.RefDB, src_alleles, offsets, modes, k: int, threshold: int = B.NO_THRESHOLD):
         """Top-k for queries given on the host as contributor rows.
 
-        src_alleles uint8 [n_src, N]; offsets int32 [n_q + 1]; modes uint8 [n_q].
-        Returns numpy (scores uint32 [n_q, k], idx int64 [n_q, k]) and the
-        bytes copied each way.
+        src_alleles uint8 [n_src, N]; offsets int32 [n_q + 1]; modes uint8 [n_q]:
+        numpy arrays (staged through pinned buffers) or pinned CPU tensors
+        (copied to the device directly).  Returns numpy (scores uint32
+        [n_q, k], idx int64 [n_q, k]) and the bytes copied each way.
         """
         n_loci = src_alleles.shape[1]
-        h_src = self._pin("src", np.ascontiguousarray(src_alleles, np.uint8))
-        h_off = self._pin("off", np.ascontiguousarray(offsets, np.int32))
-        h_mod = self._pin("mod", np.ascontiguousarray(modes, np.uint8))
+        h_src = self._host_input("src", src_alleles, np.uint8)
+        h_off = self._host_input("off", offsets, np.int32)
+        h_mod = self._host_input("mod", modes, np.uint8)
         d_src = self._buf("d_src", h_src.shape, torch.uint8)
         d_off = self._buf("d_off", h_off.shape, torch.int32)
         d_mod = self._buf("d_mod", h_mod.shape, torch.uint8)
