@@ -276,3 +276,30 @@ def test_invalid_arguments(searcher):
         B.fastid_load_refs(searcher.ctx, q, 0)
     assert e.value.status == B.EINVAL
     db.close()
+
+
+# ---- host in, host out -----------------------------------------------------------
+
+def test_search_host_inputs(searcher):
+    """Searcher.search_host from numpy arrays (staged), from pinned CPU tensors
+    (copied directly) and from unpinned CPU tensors: the same lists, equal to
+    the oracle's; a tensor of the wrong dtype is refused."""
+    n_refs, n_loci, k, T = 2500, 555, 10, 300
+    R, Q, modes, src, rec = make_case(n_refs, n_loci, 40, 60, seed=77)
+    db = load(searcher, R, n_loci)
+    off = rec.offsets.astype(np.int32)
+    mis, une = oracle.scores(R, Q)
+    es, ei = oracle.topk(oracle.select(mis, une, modes), k, T)
+    inputs = {
+        "numpy": (src, off, modes),
+        "pinned": tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (src, off, modes)),
+        "unpinned": tuple(torch.from_numpy(np.ascontiguousarray(a)) for a in (src, off, modes)),
+    }
+    for name, (a, o, m) in inputs.items():
+        sc, ix, h2d, d2h = searcher.search_host(db, a, o, m, k, T)
+        assert np.array_equal(sc, es) and np.array_equal(ix, ei), name
+        assert h2d == src.nbytes + off.nbytes + modes.nbytes and d2h == 12 * k * Q.shape[0], name
+    with pytest.raises(ValueError):
+        searcher.search_host(db, torch.from_numpy(src.astype(np.int32)), off, modes, k, T)
+    assert B.fastid_sync_status(searcher.ctx) == B.OK
+    db.close()
