@@ -400,11 +400,19 @@ __device__ __forceinline__ void list_load(const uint64_t *slot_row, int32_t (&ls
 // PK launches: the reference operand arrives packed (TC_P_BYTES per stage,
 // row r at r * 16 bytes: loci 0-63 then 64-127 of the stage) and warps 6.. (pk_threads)
 // expand it into the FP8 stage the MMA reads.  A reference "1" is e4m3 2.0
-// (byte 0x40: one bit per byte, so four loci take one multiply and one mask)
-// and the query operand is encoded at half scale (+-0.5), so D is unchanged.
+// (byte 0x40) and the query operand is encoded at half scale (+-0.5), so D is
+// unchanged.
+//
+// Locus order.  D sums over loci, so both operands may list the loci of a
+// 32-locus group in any common order.  PK uses the order that makes expansion
+// cheapest: byte 4j + k of the group holds locus 8k + j (j = 0..7, k = 0..3).
+// Then the four bytes 4j .. 4j+3 are bit j of each byte of the group's packed
+// word w, moved to bit 6 by one shift and kept by one mask:
+// (w << (6 - j)) & 0x40404040 (no other bit reaches a bit 6).  The query
+// operand of PK launches is written in the same order (encode_query_row).
 // The stage layout is the TMA's 128-byte swizzle: 16-byte chunk c of row r
 // sits at r * 128 + ((c ^ (r & 7)) << 4) from a 1024-byte aligned base.
-__device__ __forceinline__ uint32_t bits4_to_two(uint32_t x) { return ((x & 0xFu) * 0x08102040u) & 0x40404040u; }
+constexpr uint32_t PK_BIT6 = 0x40404040u;
 
 template <int NT>
 __device__ __forceinline__ void expand_stage(const uint8_t *sp, uint8_t *sb, int t) {
@@ -415,14 +423,13 @@ __device__ __forceinline__ void expand_stage(const uint8_t *sp, uint8_t *sb, int
         const uint2 hi = *reinterpret_cast<const uint2 *>(sp + r * 16 + 8);
         const uint32_t w[4] = {lo.x, lo.y, hi.x, hi.y};  // 32 loci each
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const uint32_t bits = w[c >> 1] >> (16 * (c & 1));  // loci 16c .. 16c+15
-            uint4 o;
-            o.x = bits4_to_two(bits);
-            o.y = bits4_to_two(bits >> 4);
-            o.z = bits4_to_two(bits >> 8);
-            o.w = bits4_to_two(bits >> 12);
-            *reinterpret_cast<uint4 *>(sb + r * 128 + ((c ^ (r & 7)) << 4)) = o;
+        for (int m = 0; m < 4; ++m) {  // chunks 2m (j = 0..3) and 2m + 1 (j = 4..7) of group m
+            const uint32_t x = w[m];
+            const uint4 o0 = make_uint4((x << 6) & PK_BIT6, (x << 5) & PK_BIT6, (x << 4) & PK_BIT6,
+                                        (x << 3) & PK_BIT6);
+            const uint4 o1 = make_uint4((x << 2) & PK_BIT6, (x << 1) & PK_BIT6, x & PK_BIT6, (x >> 1) & PK_BIT6);
+            *reinterpret_cast<uint4 *>(sb + r * 128 + (((2 * m) ^ (r & 7)) << 4)) = o0;
+            *reinterpret_cast<uint4 *>(sb + r * 128 + (((2 * m + 1) ^ (r & 7)) << 4)) = o1;
         }
     }
 }
@@ -812,11 +819,39 @@ __global__ void refs_e4m3_kernel(const uint64_t *__restrict__ packed, int64_t ld
 // warp.  src == nullptr (a padding row) writes zeros.
 // `one` is the e4m3 byte of +1 on this operand's scale: 0x38 (1.0) against the
 // FP8 reference operand, 0x30 (0.5) against PK's expanded references (2.0).
+// pk: PK's locus order (see expand_stage), else loci in order.
 __device__ __forceinline__ void encode_query_row(const uint64_t *__restrict__ src, bool mis, int32_t n_words,
                                                  int32_t n_loci, int32_t kpad, uint8_t *__restrict__ dst,
-                                                 float *__restrict__ qc, int lane, uint32_t one = 0x38u) {
+                                                 float *__restrict__ qc, int lane, uint32_t one = 0x38u,
+                                                 bool pk = false) {
     const bool valid = src != nullptr;
     uint32_t pc = 0;
+    if (pk) {
+        // chunk c: words i = 0..3 hold j = 4 (c & 1) + i; byte k of word i is
+        // locus 32 (c >> 1) + 8k + j
+        for (int32_t c = lane; c < kpad / 16; c += 32) {
+            const int32_t l0 = (c >> 1) * 32;
+            uint32_t bits = 0;
+            if (valid && (l0 >> 6) < n_words) bits = (uint32_t)(src[l0 >> 6] >> (l0 & 63));
+            const int32_t live = n_loci - l0;
+            const uint32_t in_n = !valid ? 0u : live >= 32 ? 0xFFFFFFFFu : live <= 0 ? 0u : ((1u << live) - 1u);
+            bits &= in_n;
+            const int32_t j0 = 4 * (c & 1);
+            pc += __popc(bits & (0x0F0F0F0Fu << j0));
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t qb = (bits >> (j0 + i)) & 0x01010101u;  // Q_l, one per byte
+                const uint32_t nb = (in_n >> (j0 + i)) & 0x01010101u;  // l < N
+                w[i] = (nb & ~qb) * one | (mis ? qb * (one | 0x80u) : 0u);
+            }
+            reinterpret_cast<uint4 *>(dst)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, off);
+        if (lane == 0) *qc = mis ? (float)pc : 0.f;
+        return;
+    }
     for (int32_t c = lane; c < kpad / 16; c += 32) {
         const int32_t l0 = c * 16;
         uint32_t bits = 0;
@@ -847,13 +882,13 @@ __device__ __forceinline__ void encode_query_row(const uint64_t *__restrict__ sr
 __global__ void queries_e4m3_kernel(const uint64_t *__restrict__ q, int64_t ld_q, int64_t n_q, int32_t n_words,
                                     int32_t n_loci, const uint8_t *__restrict__ modes, int64_t n_q_pad,
                                     int32_t kpad, uint8_t *__restrict__ out, float *__restrict__ qconst,
-                                    uint32_t one) {
+                                    uint32_t one, bool pk) {
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n_q_pad; r += warps_total) {
         const bool valid = r < n_q;
         encode_query_row(valid ? q + r * ld_q : nullptr, valid && modes[r] == FASTID_MODE_MISMATCH, n_words, n_loci,
-                         kpad, out + r * (int64_t)kpad, qconst + r, lane, one);
+                         kpad, out + r * (int64_t)kpad, qconst + r, lane, one, pk);
     }
 }
 
@@ -930,7 +965,7 @@ cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, in
     int64_t blocks = (n_q_pad + 7) / 8;
     if (blocks > 65535) blocks = 65535;
     queries_e4m3_kernel<<<(unsigned)blocks, 256, 0, s>>>(q, ld_q, n_q, n_words, n_loci, modes, n_q_pad, kpad, out,
-                                                         qconst, half ? 0x30u : 0x38u);
+                                                         qconst, half ? 0x30u : 0x38u, half);
     return cudaGetLastError();
 }
 
