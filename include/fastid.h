@@ -79,8 +79,8 @@ enum {
                                       bytes; no FP8 copy needed)                          */
 };
 /* FASTID_FORM_AUTO: the tensor form; its reference operand is the FP8 copy when
- * the database has one and the call has more than 128 queries (one query tile),
- * else the packed rows. */
+ * the database has one and the call has more than 256 queries (two query
+ * tiles), or more than 128 for fastid_topk with k > 16; else the packed rows. */
 
 /* fastid_load_refs flags */
 enum {

@@ -401,8 +401,9 @@ fastid_status prepare(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q
 }
 
 // 0 plain, 1 tensor form over the FP8 copy, 2 tensor form over the packed rows.
-fastid_status pick_form(fastid_ctx *ctx, const fastid_refdb *db, int64_t n_q, int *tensor) {
-    *tensor = fastid::pick_operand(ctx->form, db->fp8 != nullptr, n_q);
+// slots16: the launch keeps 16-slot lists (k <= 16, or no top-k).
+fastid_status pick_form(fastid_ctx *ctx, const fastid_refdb *db, int64_t n_q, int *tensor, bool slots16 = true) {
+    *tensor = fastid::pick_operand(ctx->form, db->fp8 != nullptr, n_q, slots16);
     return FASTID_OK;
 }
 
@@ -531,7 +532,7 @@ fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_
     if (k < 1 || k > FASTID_MAX_K) return fail(ctx, FASTID_EINVAL, "k out of range: %d", k);
     if (n_q > 0 && (!out_scores_dev || !out_idx_dev)) return fail(ctx, FASTID_EINVAL, "output is NULL");
     int tensor;
-    if ((st = pick_form(ctx, db, n_q, &tensor))) return st;
+    if ((st = pick_form(ctx, db, n_q, &tensor, k <= 16))) return st;
     if (n_q == 0) return FASTID_OK;
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -606,7 +607,7 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
 
 namespace fastid {
 
-int pick_operand(int form, bool has_fp8, int64_t n_q) {
+int pick_operand(int form, bool has_fp8, int64_t n_q, bool slots16) {
     switch (form) {
         case FASTID_FORM_PLAIN:
             return 0;
@@ -615,7 +616,7 @@ int pick_operand(int form, bool has_fp8, int64_t n_q) {
         case FASTID_FORM_TENSOR:
             return has_fp8 ? 1 : 2;
         default:  // AUTO: a few queries read the operand about once; packed rows are 1/8 of the bytes
-            return has_fp8 && n_q > AUTO_PACKED_MAX_Q ? 1 : 2;
+            return has_fp8 && n_q > (slots16 ? AUTO_PACKED_MAX_Q16 : AUTO_PACKED_MAX_Q) ? 1 : 2;
     }
 }
 

@@ -45,12 +45,15 @@ struct fastid_refdb {
 namespace fastid {
 // Operand of a comparison call: 0 plain form, 1 tensor form over the FP8 copy,
 // 2 tensor form over the packed rows (expanded on chip).  AUTO takes the FP8
-// copy, when there is one, above AUTO_PACKED_MAX_Q queries: one query tile
-// streams the packed rows faster (20M references at N = 2048: 4.0 ms against
-// 5.7 ms), two tiles already run faster as a pair over the FP8 copy (6.7 ms
-// against 7.9 ms at k = 16 and 11.2 ms at k = 32).
+// copy, when there is one, above AUTO_PACKED_MAX_Q queries, or above
+// AUTO_PACKED_MAX_Q16 for launches with 16-slot lists (k <= 16, hits, score
+// matrices), whose packed kernel has twice the expanding warps.  Measured on
+// 20M references at N = 2048: one query tile, packed rows 3.35 ms (k = 16) /
+// 4.15 ms (k = 32) against 5.8 ms over the FP8 copy; two tiles, packed rows
+// 6.4 ms (k = 16) / 8.4 ms (k = 32) against 6.7 ms as a pair over the FP8 copy.
 constexpr int64_t AUTO_PACKED_MAX_Q = 128;
-int pick_operand(int form, bool has_fp8, int64_t n_q);
+constexpr int64_t AUTO_PACKED_MAX_Q16 = 256;
+int pick_operand(int form, bool has_fp8, int64_t n_q, bool slots16 = true);
 
 // The hit-list half of fastid_compare: every (q, r) with score <= threshold of
 // this call is appended at atomicAdd(count) (stored while < capacity),

@@ -128,8 +128,8 @@ fastid_status check_refs(fastid_ctx *ctx, const StreamRefs &r) {
 // caller's stream; `compare(b, db, r0)` enqueues block b's comparison of
 // db (references r0 .. r0 + db.n_refs - 1) there.
 template <class Setup, class Compare>
-fastid_status stream_blocks(fastid_ctx *ctx, const StreamRefs &R, int64_t n_q, cudaStream_t s, Setup setup,
-                            Compare compare) {
+fastid_status stream_blocks(fastid_ctx *ctx, const StreamRefs &R, int64_t n_q, bool slots16, cudaStream_t s,
+                            Setup setup, Compare compare) {
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return scuda(ctx, e, "cudaSetDevice");
     const int32_t n_words = (R.n_loci + 63) / 64;
@@ -139,7 +139,7 @@ fastid_status stream_blocks(fastid_ctx *ctx, const StreamRefs &R, int64_t n_q, c
     // calls pick it): the FP8 operand is built per block only for the tensor
     // form over the FP8 copy; the plain form and the tensor form over packed
     // rows read the padded rows.
-    const int op = pick_operand(ctx->form, (R.flags & FASTID_REFS_TENSOR) != 0, n_q);
+    const int op = pick_operand(ctx->form, (R.flags & FASTID_REFS_TENSOR) != 0, n_q, slots16);
     const bool tensor = op == 1;
     const bool rows = !tensor;
 
@@ -256,7 +256,7 @@ fastid_status fastid_topk_streamed(fastid_ctx *ctx, const uint64_t *refs_host, i
         ctx->launches += 1;
         return FASTID_OK;
     };
-    return stream_blocks(ctx, R, n_q, s, setup, compare);
+    return stream_blocks(ctx, R, n_q, k <= 16, s, setup, compare);
 }
 
 fastid_status fastid_compare_streamed(fastid_ctx *ctx, const uint64_t *refs_host, int64_t n_refs, int32_t n_loci,
@@ -314,7 +314,7 @@ fastid_status fastid_compare_streamed(fastid_ctx *ctx, const uint64_t *refs_host
         ctx->launches += r0 != 0 && capacity > 0 ? 2 : 1;
         return FASTID_OK;
     };
-    if ((rs = stream_blocks(ctx, R, n_q, s, setup, compare)) != FASTID_OK) return rs;
+    if ((rs = stream_blocks(ctx, R, n_q, true, s, setup, compare)) != FASTID_OK) return rs;
     cudaError_t e = launch_hits_finish(count, capacity, hit_q_dev, hit_r_dev, hit_score_dev, hit_count_dev, sort_tmp,
                                        ctx->dev_status, s);
     if (e != cudaSuccess) return scuda(ctx, e, "hit list finish");

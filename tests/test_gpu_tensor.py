@@ -138,11 +138,13 @@ def test_paired_launch_parity(ts, n_q, n_refs, k):
     db.close()
 
 
-@pytest.mark.parametrize("n_q", [100, 128, 129, 300, 600])
-def test_auto_form_both_operands(n_q):
-    """FASTID_FORM_AUTO reads the packed rows for calls of at most 128 queries
-    and the FP8 copy above (paired from two query tiles on; 300 queries pad to
-    four tiles): results equal the oracle on both sides of the switch."""
+@pytest.mark.parametrize("n_q,k", [(100, 12), (128, 12), (129, 12), (256, 12), (257, 12), (300, 12), (600, 12),
+                                   (128, 32), (129, 32)])
+def test_auto_form_both_operands(n_q, k):
+    """FASTID_FORM_AUTO reads the packed rows up to 256 queries at k <= 16 and
+    up to 128 at k > 16, and the FP8 copy above (paired from two query tiles
+    on; 300 queries pad to four tiles): results equal the oracle on both sides
+    of each switch."""
     import __graft_entry__
     __graft_entry__.build()
     s = Searcher(0, B.FORM_AUTO)
@@ -154,11 +156,11 @@ def test_auto_form_both_operands(n_q):
     assert db.info()["flags"] == B.REFS_TENSOR
     q = torch.empty((n_q, words64(700)), dtype=torch.int64, device="cuda")
     B.fastid_pack(s.ctx, torch.from_numpy(Q).cuda(), 700, q)
-    sc, ix = s.topk(db, q, torch.from_numpy(modes).cuda(), 12, 400)
+    sc, ix = s.topk(db, q, torch.from_numpy(modes).cuda(), k, 400)
     torch.cuda.synchronize()
     assert B.fastid_sync_status(s.ctx) == B.OK
     mis, une = oracle.scores(R, Q)
-    es, ei = oracle.topk(oracle.select(mis, une, modes), 12, 400)
+    es, ei = oracle.topk(oracle.select(mis, une, modes), k, 400)
     assert np.array_equal(sc.cpu().numpy().view(np.uint32), es)
     assert np.array_equal(ix.cpu().numpy(), ei)
     db.close()
