@@ -25,3 +25,24 @@ def test_recorded_traffic_matches_current_sources():
         form, config = key.split("/")
         assert form in ("tensor", "plain") and config in bench.WORKLOADS
         assert bytes_ > 0 and len(h) == 16
+
+
+def test_reference_arm_json_line(capsys):
+    """`bench.py --impl reference` prints one JSON line with the contract's keys:
+    the oracle timed on the host, its cpu_baseline and an e2e block with no
+    host-device bytes (run on the small 64 x 10k workload)."""
+    import json
+
+    import bench
+    bench.main(["--impl", "reference", "--config", "c1", "--steps", "1", "--warmup", "0"])
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == bench.WORKLOADS["c1"]["workload"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
