@@ -5,6 +5,7 @@ integers; the test is equality with the oracle."""
 import numpy as np
 import pytest
 
+import gen
 import oracle
 
 torch = pytest.importorskip("torch")
@@ -165,3 +166,35 @@ def test_auto_form_both_operands(n_q, k):
     assert np.array_equal(ix.cpu().numpy(), ei)
     db.close()
     s.ctx.close()
+
+
+def test_schedule_tail_exact():
+    """2048 queries x 100,000 references at N = 96 (words ragged), top-16. The
+    schedule is 8 tile pairs on 76 clusters: an 8 x 9 grid over the first 374
+    reference tiles plus a tail of 4 clusters x 2 pairs over the last 17. The
+    unpaired packed form gets a 16 x 9 grid plus 8 x 2. Both forms' lists equal
+    the oracle's element by element, so every tail slot is written and merged."""
+    import __graft_entry__
+    __graft_entry__.build()
+    n_refs, n_loci, n_q, k = 100_000, 96, 2048, 16
+    rng = np.random.default_rng(2024)
+    thr = gen.maf_thresholds(31, n_loci)
+    R = gen.allele_rows(31, gen.STREAM_DB, np.arange(n_refs), thr)
+    Q = (rng.random((n_q, n_loci)) < 0.35).astype(np.uint8)
+    Q[:64] = R[rng.integers(0, n_refs, 64)]
+    modes = (rng.random(n_q) < 0.5).astype(np.uint8)
+    mis, une = oracle.scores(R, Q)
+    es, ei = oracle.topk(oracle.select(mis, une, modes), k)
+    for form in (B.FORM_TENSOR, B.FORM_TENSOR_PACKED):
+        s = Searcher(0, form)
+        db = s.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci,
+                                 flags=B.REFS_TENSOR if form == B.FORM_TENSOR else 0)
+        q = torch.empty((n_q, words64(n_loci)), dtype=torch.int64, device="cuda")
+        B.fastid_pack(s.ctx, torch.from_numpy(Q).cuda(), n_loci, q)
+        sc, ix = s.topk(db, q, torch.from_numpy(modes).cuda(), k)
+        torch.cuda.synchronize()
+        assert B.fastid_sync_status(s.ctx) == B.OK
+        assert np.array_equal(sc.cpu().numpy().view(np.uint32), es), form
+        assert np.array_equal(ix.cpu().numpy(), ei), form
+        db.close()
+        s.ctx.close()
