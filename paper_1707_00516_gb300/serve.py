@@ -80,6 +80,9 @@ class Server:
             self._free.put(s)
         self._pending: collections.deque = collections.deque()
         self._cv = threading.Condition()
+        # a context is used by one host thread at a time: the dispatcher's
+        # launches and the completion thread's status reads take turns
+        self._lib = threading.Lock()
         self._inflight: queue.Queue = queue.Queue()
         self._stop = False
         self.latencies: list[float] = []
@@ -160,8 +163,9 @@ class Server:
         with torch.cuda.stream(slot.stream):
             slot.d_q[:n].copy_(slot.h_q[:n], non_blocking=True)
             slot.d_m[:n].copy_(slot.h_m[:n], non_blocking=True)
-            B.fastid_topk(self.ctx, self.db, slot.d_q[:n], slot.d_m[:n], self.k, self.threshold, slot.d_sc[:n],
-                          slot.d_ix[:n], stream=slot.stream)
+            with self._lib:
+                B.fastid_topk(self.ctx, self.db, slot.d_q[:n], slot.d_m[:n], self.k, self.threshold,
+                              slot.d_sc[:n], slot.d_ix[:n], stream=slot.stream)
             slot.h_sc[:n].copy_(slot.d_sc[:n], non_blocking=True)
             slot.h_ix[:n].copy_(slot.d_ix[:n], non_blocking=True)
             slot.done.record(slot.stream)
@@ -172,17 +176,28 @@ class Server:
             if item is None:
                 return
             slot, wave, n = item
-            slot.done.synchronize()
-            sc = slot.h_sc[:n].numpy().view(np.uint32)
-            ix = slot.h_ix[:n].numpy()
-            now = time.perf_counter()
-            o = 0
-            for r in wave:
-                r.future.set_result((sc[o:o + r.n].copy(), ix[o:o + r.n].copy()))
-                self.latencies.append(now - r.t_submit)
-                self.records.append((r.t_submit, now - r.t_submit))
-                o += r.n
-            self.waves += 1
-            self.queries += n
-            self.wave_sizes.append(n)
+            try:
+                slot.done.synchronize()
+                # conditions the device recorded (a bounded wait that ran out):
+                # the wave's results are not delivered.  The status word is the
+                # context's, so with several waves in flight a condition fails
+                # the wave whose completion reads it first.
+                with self._lib:
+                    self.ctx.check(B.fastid_sync_status(self.ctx, slot.stream))
+                sc = slot.h_sc[:n].numpy().view(np.uint32)
+                ix = slot.h_ix[:n].numpy()
+                now = time.perf_counter()
+                o = 0
+                for r in wave:
+                    r.future.set_result((sc[o:o + r.n].copy(), ix[o:o + r.n].copy()))
+                    self.latencies.append(now - r.t_submit)
+                    self.records.append((r.t_submit, now - r.t_submit))
+                    o += r.n
+                self.waves += 1
+                self.queries += n
+                self.wave_sizes.append(n)
+            except Exception as e:  # report to every request of the wave
+                for r in wave:
+                    if not r.future.done():
+                        r.future.set_exception(e)
             self._free.put(slot)

@@ -93,3 +93,29 @@ def test_budget_limits_slots(env):
     srv.close()
     with pytest.raises(RuntimeError):
         srv.submit(reqs[0][0], reqs[0][1])
+
+
+def test_device_condition_fails_its_wave(env):
+    """A condition the device records (here a bounded wait that ran out,
+    planted through fastid_wait_flag on the server's context while it is
+    idle) fails the requests of the wave that reads it with FASTID_ETIMEOUT;
+    the status word is cleared, and the next wave's results are delivered and
+    equal the oracle's.  No GPU fault or hang is involved."""
+    s, db, R, thr, seed = env
+    reqs = _requests(R, thr, seed, 2, np.random.default_rng(11))
+    srv = Server(s.ctx, db, 8, B.NO_THRESHOLD, hbm_budget_bytes=1 << 30, max_wave=512, max_slots=1)
+    try:
+        flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+        B.fastid_wait_flag(s.ctx, flag, 50)  # nothing sets the flag: the wait runs out
+        torch.cuda.synchronize()
+        f = srv.submit(reqs[0][0], reqs[0][1])
+        with pytest.raises(B.FastIDError) as e:
+            f.result(timeout=120)
+        assert e.value.status == B.ETIMEOUT
+        sc, ix = srv.submit(reqs[1][0], reqs[1][1]).result(timeout=120)
+        mis, une = oracle.scores(R, reqs[1][2])
+        es, ei = oracle.topk(oracle.select(mis, une, reqs[1][1]), 8)
+        assert np.array_equal(sc, es) and np.array_equal(ix, ei)
+    finally:
+        srv.close()
+    assert B.fastid_sync_status(s.ctx) == B.OK
