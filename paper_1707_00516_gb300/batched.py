@@ -85,7 +85,9 @@ class BatchedSearch:
             self._h_ix[oi:oi + n * k].copy_(ix.view(-1), non_blocking=True)
             os_ += n * k
             oi += n * k
-        torch.cuda.current_stream().synchronize()
+        # synchronises the stream; raises if the device recorded a condition
+        # (a bounded wait that ran out): results are then not returned
+        self.ctx.check(B.fastid_sync_status(self.ctx, torch.cuda.current_stream()))
         scores, idx = [], []
         off = 0
         for (_, q, _, _, _) in self.batches:

@@ -157,7 +157,9 @@ class Searcher:
         o_ix = self._pin_out("o_ix", (n_q, k), torch.int64)
         o_sc.copy_(sc, non_blocking=True)
         o_ix.copy_(ix, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        # synchronises the stream; raises if the device recorded a condition
+        # (a bounded wait that ran out): results are then not returned
+        self.ctx.check(B.fastid_sync_status(self.ctx, torch.cuda.current_stream()))
         h2d = h_src.numel() + 4 * h_off.numel() + h_mod.numel()
         d2h = 4 * o_sc.numel() + 8 * o_ix.numel()
         return o_sc.numpy().view(np.uint32).copy(), o_ix.numpy().copy(), h2d, d2h

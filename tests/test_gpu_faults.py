@@ -111,3 +111,26 @@ def test_database_file_roundtrip(s, tmp_path):
         B.fastid_load_refs_file(s.ctx, str(bad), 0)
     assert e.value.status == B.EINVAL
     assert B.fastid_sync_status(s.ctx) == B.OK
+
+
+def test_search_host_raises_on_device_condition(s):
+    """The host-buffer path reads the status word before returning: with a
+    planted timeout (a bounded wait on a flag nothing sets) search_host raises
+    FASTID_ETIMEOUT instead of returning results; the next call returns the
+    oracle's lists."""
+    rng = np.random.default_rng(9)
+    R = (rng.random((700, 200)) < 0.3).astype(np.uint8)
+    src = (rng.random((30, 200)) < 0.3).astype(np.uint8)
+    off = np.arange(31, dtype=np.int32)  # one contributor per query
+    modes = (rng.random(30) < 0.5).astype(np.uint8)
+    db = s.load_refs_alleles(torch.from_numpy(R).cuda(), 200)
+    B.fastid_wait_flag(s.ctx, torch.zeros(1, dtype=torch.int32, device="cuda"), 50)
+    with pytest.raises(B.FastIDError) as e:
+        s.search_host(db, src, off, modes, 6)
+    assert e.value.status == B.ETIMEOUT
+    sc, ix, _, _ = s.search_host(db, src, off, modes, 6)
+    mis, une = oracle.scores(R, src)
+    es, ei = oracle.topk(oracle.select(mis, une, modes), 6)
+    assert np.array_equal(sc, es) and np.array_equal(ix, ei)
+    db.close()
+    assert B.fastid_sync_status(s.ctx) == B.OK
