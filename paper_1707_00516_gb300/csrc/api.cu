@@ -235,6 +235,7 @@ fastid_status fastid_set_form(fastid_ctx *ctx, int32_t form) {
 }
 
 fastid_status fastid_sync_status(fastid_ctx *ctx, fastid_stream stream) {
+    FASTID_RANGE();
     if (!ctx) return FASTID_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -251,6 +252,7 @@ fastid_status fastid_sync_status(fastid_ctx *ctx, fastid_stream stream) {
 fastid_status fastid_pack(fastid_ctx *ctx, const uint8_t *alleles_dev, int64_t n, int32_t n_loci,
                           int64_t ld_alleles, uint64_t *packed_dev, int64_t ld_words, uint32_t *norms_dev,
                           fastid_stream stream) {
+    FASTID_RANGE();
     if (!ctx) return FASTID_EINVAL;
     if (n < 0) return fail(ctx, FASTID_EINVAL, "n < 0");
     if (n_loci < 1 || n_loci > FASTID_MAX_LOCI) return fail(ctx, FASTID_EINVAL, "n_loci out of range: %d", n_loci);
@@ -267,6 +269,7 @@ fastid_status fastid_pack(fastid_ctx *ctx, const uint8_t *alleles_dev, int64_t n
 fastid_status fastid_mix(fastid_ctx *ctx, const uint64_t *src_dev, int64_t ld_src, int32_t n_words,
                          const int32_t *offsets_dev, int64_t n_mix, uint64_t *out_dev, int64_t ld_out,
                          uint32_t *norms_dev, fastid_stream stream) {
+    FASTID_RANGE();
     if (!ctx) return FASTID_EINVAL;
     if (n_mix < 0) return fail(ctx, FASTID_EINVAL, "n_mix < 0");
     if (n_words < 1 || ld_src < n_words || ld_out < n_words)
@@ -282,6 +285,7 @@ fastid_status fastid_mix(fastid_ctx *ctx, const uint64_t *src_dev, int64_t ld_sr
 
 fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int64_t n_refs, int32_t n_loci,
                                int64_t ld_words, uint32_t flags, fastid_refdb **out, fastid_stream stream) {
+    FASTID_RANGE();
     if (!ctx) return FASTID_EINVAL;
     if (!out) return fail(ctx, FASTID_EINVAL, "out is NULL");
     *out = nullptr;
@@ -443,6 +447,7 @@ fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint
     const int64_t tile_bytes = (int64_t)tensor_tile_r() * (pk ? db->ld64 * 8 : db->kpad);
     L.n_groups = make_tensor_schedule(1, &n_qq, &n_rt, &tile_bytes, L.pair ? ctx->pair_clusters : ctx->grid_tensor,
                                       L.pair ? 2 : 1, L.sched, L.order, &L.n_slots);
+    if (L.n_groups == -2) return fail(ctx, FASTID_EDEVICE, "schedule self-check failed (debug build)");
     if (L.n_groups < 0) return fail(ctx, FASTID_EINVAL, "too many query tiles (top-k slots)");
     tp->n_ctas = (int64_t)L.n_groups * (L.pair ? 2 : 1);
     size_t extra = 0;
@@ -482,6 +487,7 @@ extern "C" {
 fastid_status fastid_scores(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev, int64_t ld_q,
                             int64_t n_q, const uint8_t *modes_dev, void *out_dev, int32_t out_bytes,
                             int64_t ld_out, fastid_stream stream) {
+    FASTID_RANGE();
     fastid_status st = check_query_args(ctx, db, queries_dev, ld_q, n_q, modes_dev);
     if (st) return st;
     if (out_bytes != 2 && out_bytes != 4) return fail(ctx, FASTID_EINVAL, "out_bytes must be 2 or 4");
@@ -527,6 +533,7 @@ fastid_status fastid_scores(fastid_ctx *ctx, const fastid_refdb *db, const uint6
 fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev, int64_t ld_q,
                           int64_t n_q, const uint8_t *modes_dev, int32_t k, uint32_t threshold,
                           uint32_t *out_scores_dev, int64_t *out_idx_dev, fastid_stream stream) {
+    FASTID_RANGE();
     fastid_status st = check_query_args(ctx, db, queries_dev, ld_q, n_q, modes_dev);
     if (st) return st;
     if (k < 1 || k > FASTID_MAX_K) return fail(ctx, FASTID_EINVAL, "k out of range: %d", k);
@@ -576,6 +583,7 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
                              int64_t n_q, const uint8_t *modes_dev, uint32_t threshold, int64_t capacity,
                              int64_t *hit_q_dev, int64_t *hit_r_dev, uint32_t *hit_score_dev,
                              int64_t *hit_count_dev, fastid_stream stream) {
+    FASTID_RANGE();
     fastid_status st = check_query_args(ctx, db, queries_dev, ld_q, n_q, modes_dev);
     if (st) return st;
     if (capacity < 0) return fail(ctx, FASTID_EINVAL, "capacity < 0");

@@ -152,8 +152,9 @@ struct TcLaunch {
 
 // Fills sched[] and order[] for n panels, each over (up to) G work groups of
 // `ctas_per_group` CTAs; returns the number of groups the launch needs (max
-// of a * b; -1: too many top-k slots) and sets *n_slots.  tile_bytes: bytes
-// of one reference tile of the operand.
+// of a * b + t_groups; -1: too many top-k slots; -2, debug builds only: the
+// schedule's self-check failed) and sets *n_slots.  tile_bytes: bytes of one
+// reference tile of the operand.
 int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, const int64_t *tile_bytes,
                              int32_t G, int32_t ctas_per_group, TcSched *sched, int32_t *order,
                              int32_t *n_slots);

@@ -61,6 +61,7 @@ struct HostBuf {
 extern "C" {
 
 fastid_status fastid_save_refs(fastid_ctx *ctx, const fastid_refdb *db, const char *path) {
+    FASTID_RANGE();
     if (!ctx) return FASTID_EINVAL;
     if (!db || !path) return ffail(ctx, FASTID_EINVAL, "database or path is NULL");
     cudaError_t e = cudaSetDevice(db->device);
@@ -96,6 +97,7 @@ fastid_status fastid_save_refs(fastid_ctx *ctx, const fastid_refdb *db, const ch
 
 fastid_status fastid_load_refs_file(fastid_ctx *ctx, const char *path, uint32_t flags, fastid_refdb **out,
                                     fastid_stream stream) {
+    FASTID_RANGE();
     if (!ctx) return FASTID_EINVAL;
     if (!path || !out) return ffail(ctx, FASTID_EINVAL, "path or out is NULL");
     *out = nullptr;

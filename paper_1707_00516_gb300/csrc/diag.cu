@@ -39,6 +39,7 @@ using namespace fastid;
 
 extern "C" fastid_status fastid_wait_flag(fastid_ctx *ctx, const uint32_t *flag_dev, int32_t wait_ms,
                                           fastid_stream stream) {
+    FASTID_RANGE();
     if (!ctx) return FASTID_EINVAL;
     if (!flag_dev) {
         ctx->last_error = "flag is NULL";

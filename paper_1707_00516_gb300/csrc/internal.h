@@ -2,11 +2,27 @@
 // translation units that implement entry points.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 #include <utility>
 #include <vector>
 
 #include "common.cuh"
+
+namespace fastid {
+// One NVTX range per C-ABI call, named after the entry point, so that a
+// profiler or tracer attributes every kernel to the call that launched it
+// (e.g. ncu --nvtx --nvtx-include "fastid_topk/").  Without a tool attached
+// the push and pop return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace fastid
+#define FASTID_RANGE() ::fastid::NvtxRange fastid_nvtx_range_(__func__)
 
 struct fastid_ctx {
     int device = 0;

@@ -68,6 +68,7 @@ extern "C" fastid_status fastid_topk_noalloc(fastid_ctx *ctx, const fastid_refdb
                                              int64_t ld_q, int64_t n_q, const uint8_t *modes_dev, int32_t k,
                                              uint32_t threshold, uint32_t *out_scores_dev, int64_t *out_idx_dev,
                                              fastid_stream stream) {
+    FASTID_RANGE();
     using namespace fastid;
     if (!ctx) return FASTID_EINVAL;
     if (!db) return set_error(ctx, FASTID_EINVAL, "database is NULL");

@@ -75,6 +75,7 @@ extern "C" {
 fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs, int32_t n_panels,
                                  const fastid_batch *batches, int32_t n_batches, int32_t k, uint32_t threshold,
                                  int32_t variant, fastid_plan **out) {
+    FASTID_RANGE();
     if (!ctx) return FASTID_EINVAL;
     if (!out) return perr(ctx, FASTID_EINVAL, "out is NULL");
     *out = nullptr;
@@ -135,6 +136,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
                                       L.order, &L.n_slots);
     if (L.n_groups < 0) {
         free_plan(P);
+        if (L.n_groups == -2) return perr(ctx, FASTID_EDEVICE, "schedule self-check failed (debug build)");
         return perr(ctx, FASTID_EINVAL, "plan too large (top-k slots)");
     }
     P->n_ctas = (int64_t)L.n_groups * (pair ? 2 : 1);
@@ -252,6 +254,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
 }
 
 fastid_status fastid_plan_run(fastid_plan *plan, fastid_stream stream) {
+    FASTID_RANGE();
     if (!plan) return FASTID_EINVAL;
     fastid_ctx *ctx = plan->ctx;
     cudaStream_t s = (cudaStream_t)stream;
@@ -273,6 +276,7 @@ fastid_status fastid_plan_run(fastid_plan *plan, fastid_stream stream) {
 }
 
 fastid_status fastid_plan_capture(fastid_plan *plan, fastid_stream stream) {
+    FASTID_RANGE();
     if (!plan) return FASTID_EINVAL;
     fastid_ctx *ctx = plan->ctx;
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -312,6 +316,7 @@ fastid_status fastid_plan_capture(fastid_plan *plan, fastid_stream stream) {
 }
 
 fastid_status fastid_plan_replay(fastid_plan *plan, fastid_stream stream) {
+    FASTID_RANGE();
     if (!plan) return FASTID_EINVAL;
     fastid_ctx *ctx = plan->ctx;
     if (!plan->graph_exec) return perr(ctx, FASTID_EINVAL, "plan has no captured graph: call fastid_plan_capture");

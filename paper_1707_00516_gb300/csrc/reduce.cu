@@ -74,7 +74,28 @@ struct MergeSched {
     int32_t pair;
     int32_t k;
     TcSched sc[TC_MAXP];
+    int64_t n_slots;   // slots in partial (checked by debug builds)
+    uint32_t *status;  // the context's status word
 };
+
+// Debug builds (FASTID_DEBUG) check every slot a merge reads against the
+// slot count; a slot out of range records ST_DEVICE with detail code 1 and is
+// read as empty.  Release builds take the schedule's word for it.
+__device__ __forceinline__ bool merge_slot_ok(const MergeSched &M, int64_t slot) {
+#ifdef FASTID_DEBUG
+    if (slot < 0 || slot >= M.n_slots) {
+        if ((threadIdx.x & 31) == 0) {
+            atomicOr(M.status, ST_DEVICE);
+            atomicExch(M.status + 1, 1u);
+        }
+        return false;
+    }
+#else
+    (void)M;
+    (void)slot;
+#endif
+    return true;
+}
 
 __global__ void topk_merge_sched_kernel(const uint64_t *__restrict__ partial, const MergeSched M,
                                         const MergeJob *__restrict__ jobs, int64_t n_jobs,
@@ -102,14 +123,14 @@ __global__ void topk_merge_sched_kernel(const uint64_t *__restrict__ partial, co
         const int64_t wg = x * sc.b + y;
         const int64_t cta = M.pair ? 2 * wg + rank : wg;
         const int64_t slot = (int64_t)sc.slot0 + cta * sc.tpx + li;
-        uint64_t v = lane < k ? partial[(slot * k + lane) * TC_TILE_Q + ql] : KEY_EMPTY;
+        uint64_t v = lane < k && merge_slot_ok(M, slot) ? partial[(slot * k + lane) * TC_TILE_Q + ql] : KEY_EMPTY;
         acc = warp_merge32(acc, v, lane);
     }
     if (sc.t_groups > 0) {  // the tail group holding this query tile (see TcSched)
         const int64_t cpg = M.pair ? 2 : 1;
         const int64_t t = qq / sc.t_tpx, lt = qq - t * sc.t_tpx;
         const int64_t slot = (int64_t)sc.slot0 + (int64_t)sc.a * sc.b * cpg * sc.tpx + (t * cpg + rank) * sc.t_tpx + lt;
-        uint64_t v = lane < k ? partial[(slot * k + lane) * TC_TILE_Q + ql] : KEY_EMPTY;
+        uint64_t v = lane < k && merge_slot_ok(M, slot) ? partial[(slot * k + lane) * TC_TILE_Q + ql] : KEY_EMPTY;
         acc = warp_merge32(acc, v, lane);
     }
     if (lane < k) {
@@ -318,6 +339,8 @@ cudaError_t launch_merge_sched(const uint64_t *partial, const TcLaunch &L, const
     M.pair = L.pair;
     M.k = L.k;
     for (int p = 0; p < TC_MAXP; ++p) M.sc[p] = L.sched[p];
+    M.n_slots = L.n_slots;
+    M.status = L.status;
     const int wpb = 8;
     int64_t blocks = (n_jobs + wpb - 1) / wpb;
     topk_merge_sched_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, M, jobs, n_jobs, out_scores, out_idx);

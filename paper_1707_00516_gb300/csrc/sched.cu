@@ -42,6 +42,50 @@ constexpr double TAIL_MIN_GAIN = 0.02;
 // penalty (1.1) left the tail finishing last (43.3 ms).
 constexpr double TAIL_COST = 1.3;
 
+#ifdef FASTID_DEBUG
+// Debug builds: every (query tile, reference tile) unit of the panel is
+// covered exactly once by the grid and the tail, and every CTA's top-k slots
+// are distinct and inside [slot0, slot_end).  The unit and slot mapping
+// restates the kernel's group_work (csrc/tensor.cu).
+bool schedule_consistent(const TcSched &sc, int64_t n_qq, int64_t n_rt, int cpg, int64_t slot_end) {
+    if (n_qq <= 0 || n_rt <= 0) return true;
+    std::vector<uint8_t> cov((size_t)(n_qq * n_rt), 0);
+    std::vector<uint8_t> used((size_t)std::max<int64_t>(slot_end - sc.slot0, 0), 0);
+    const int64_t grid = (int64_t)sc.a * sc.b;
+    for (int64_t wg = 0; wg < grid + sc.t_groups; ++wg) {
+        int64_t r_lo, r_hi, q_lo, q_hi, base, tpx;
+        if (wg < grid) {
+            const int64_t x = wg / sc.b, y = wg - x * sc.b;
+            r_lo = y * (int64_t)sc.r_main / sc.b;
+            r_hi = (y + 1) * (int64_t)sc.r_main / sc.b;
+            tpx = sc.tpx;
+            q_lo = x * tpx;
+            q_hi = std::min<int64_t>(n_qq, (x + 1) * tpx);
+            base = sc.slot0 + wg * cpg * tpx;
+        } else {
+            const int64_t t = wg - grid;
+            r_lo = sc.r_main;
+            r_hi = n_rt;
+            tpx = sc.t_tpx;
+            q_lo = std::min<int64_t>(n_qq, t * tpx);
+            q_hi = std::min<int64_t>(n_qq, (t + 1) * tpx);
+            base = sc.slot0 + grid * cpg * sc.tpx + t * cpg * tpx;
+        }
+        for (int64_t qq = q_lo; qq < q_hi; ++qq) {
+            for (int rank = 0; rank < cpg; ++rank) {
+                const int64_t s = base + rank * tpx + (qq - q_lo) - sc.slot0;
+                if (s < 0 || s >= (int64_t)used.size() || used[(size_t)s]++) return false;
+            }
+            for (int64_t rt = r_lo; rt < r_hi; ++rt)
+                if (++cov[(size_t)(qq * n_rt + rt)] != 1) return false;
+        }
+    }
+    for (uint8_t c : cov)
+        if (c != 1) return false;
+    return true;
+}
+#endif
+
 }  // namespace
 
 int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, const int64_t *tile_bytes,
@@ -116,6 +160,9 @@ int32_t make_tensor_schedule(int n, const int64_t *n_qq, const int64_t *n_rt, co
         groups = std::max<int32_t>(groups, sc.a * sc.b + sc.t_groups);
         slots += (int64_t)sc.a * sc.b * ctas_per_group * sc.tpx + (int64_t)sc.t_groups * ctas_per_group * sc.t_tpx;
         if (slots > INT32_MAX) return -1;
+#ifdef FASTID_DEBUG
+        if (!schedule_consistent(sc, n_qq[p], n_rt[p], ctas_per_group, slots)) return -2;
+#endif
     }
     // Largest panel first: every group enters it together, so the groups of
     // a slice stay in step and share its tiles through L2; the small panels

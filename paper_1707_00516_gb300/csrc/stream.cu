@@ -226,6 +226,7 @@ fastid_status fastid_topk_streamed(fastid_ctx *ctx, const uint64_t *refs_host, i
                                    const uint64_t *queries_dev, int64_t ld_q, int64_t n_q, const uint8_t *modes_dev,
                                    int32_t k, uint32_t threshold, uint32_t *out_scores_dev, int64_t *out_idx_dev,
                                    fastid_stream stream) {
+    FASTID_RANGE();
     if (!ctx) return FASTID_EINVAL;
     const StreamRefs R{refs_host, n_refs, n_loci, ld_words, flags, block_refs};
     fastid_status rs = check_refs(ctx, R);
@@ -265,6 +266,7 @@ fastid_status fastid_compare_streamed(fastid_ctx *ctx, const uint64_t *refs_host
                                       const uint8_t *modes_dev, uint32_t threshold, int64_t capacity,
                                       int64_t *hit_q_dev, int64_t *hit_r_dev, uint32_t *hit_score_dev,
                                       int64_t *hit_count_dev, fastid_stream stream) {
+    FASTID_RANGE();
     if (!ctx) return FASTID_EINVAL;
     const StreamRefs R{refs_host, n_refs, n_loci, ld_words, flags, block_refs};
     fastid_status rs = check_refs(ctx, R);

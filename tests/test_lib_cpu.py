@@ -25,8 +25,8 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(fastid_\w+)\s*\(", src)))
 
 
-def exported_functions():
-    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True, check=True).stdout
+def exported_functions(path=LIB):
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
     return sorted({ln.split()[-1] for ln in out.splitlines() if " T fastid_" in ln})
 
 
@@ -76,3 +76,11 @@ def test_library_missing_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(B, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         B.load_library(str(tmp_path / "nope.so"))
+
+
+def test_debug_build_exports_match():
+    """The FASTID_DEBUG build (device-side consistency checks, schedule
+    self-check) compiles and exports the same entry points."""
+    path = build(debug=True)
+    assert os.path.basename(path) == "libfastid_debug.so"
+    assert exported_functions(path) == declared_functions()
