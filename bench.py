@@ -119,8 +119,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 200):
         self.gpu = gpu_index
+        self.interval_ms = int(interval_ms)
         self.proc = None
         self.lines: list[str] = []
 
@@ -128,7 +129,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
         except (OSError, FileNotFoundError):
@@ -711,8 +712,11 @@ def run_c4(args, w):
 
 # Serving defaults: one wave in flight (a wave of up to 128 queries costs about
 # the same as a wave of one, so arrivals are best coalesced into the next wave)
-# of at most 256 queries (two query tiles), in a 4 GB budget.
-C5_DEFAULTS = dict(slots=1, max_wave=256, hbm_budget=4 << 30)
+# of at most 256 queries (two query tiles), in a 4 GB budget.  Clocks are
+# sampled once a second: the serving window is latency-measured, and with the
+# 200 ms sampling of the device-timed configs some runs showed a 94-124 ms
+# stall (p99 23-25 ms) that runs sampled once a second did not (p99 15.7 ms).
+C5_DEFAULTS = dict(slots=1, max_wave=256, hbm_budget=4 << 30, clock_ms=1000)
 
 
 def c5_requests(w, seed: int, horizon: float):
@@ -761,7 +765,7 @@ def run_c5(args, w):
     launches0 = None
     B.fastid_profile_read(s.ctx, reset=True)
     t_start = time.perf_counter()
-    clk = ClockSampler(0)
+    clk = ClockSampler(0, args.clock_ms)
     clk.start()
     for i in range(n_req):
         delay = t_start + arrivals[i] - time.perf_counter()
@@ -823,6 +827,8 @@ def main(argv=None):
     ap.add_argument("--hbm-budget", type=int, default=C5_DEFAULTS["hbm_budget"],
                     help="c5: bytes of HBM for in-flight waves")
     ap.add_argument("--slots", type=int, default=C5_DEFAULTS["slots"], help="c5: waves in flight at most")
+    ap.add_argument("--clock-ms", type=int, default=C5_DEFAULTS["clock_ms"],
+                    help="c5: nvidia-smi clock sampling interval during the serving window")
     ap.add_argument("--streamed", type=int, default=0, metavar="BLOCK",
                     help="c1-c3: keep the references in pinned host memory and stream them in blocks of BLOCK "
                          "references (fastid_topk_streamed)")
