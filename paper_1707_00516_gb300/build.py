@@ -90,4 +90,5 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    # python -m paper_1707_00516_gb300.build [--force] [-v] [--debug]
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))
