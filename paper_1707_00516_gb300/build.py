@@ -4,6 +4,9 @@ Each ``csrc/*.cu`` compiles to an object under ``_build/`` in parallel; the
 objects link into ``libfastid.so`` next to this file.  The public header is
 ``include/fastid.h`` at the repository root.
 
+``build_peaks()`` compiles the roofline microbenchmarks (``probe/peaks.cu``)
+into ``libfastid_peaks.so``; the comparison library does not link them.
+
 ``build(debug=True)`` makes ``libfastid_debug.so`` (objects under
 ``_build_debug/``) with FASTID_DEBUG defined: device-side consistency checks
 that record ST_DEVICE in the context's status word instead of trusting the
@@ -26,6 +29,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfastid.so")
 BUILD_DEBUG = os.path.join(PKG, "_build_debug")
 LIB_DEBUG = os.path.join(PKG, "libfastid_debug.so")
+PEAKS_SRC = os.path.join(PKG, "probe", "peaks.cu")
+LIB_PEAKS = os.path.join(PKG, "libfastid_peaks.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -87,6 +92,19 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, lib_path)
     return lib_path
+
+
+def build_peaks(force: bool = False) -> str:
+    """Compile (if stale) and return the path of libfastid_peaks.so."""
+    if not force and not _stale(LIB_PEAKS, [PEAKS_SRC, __file__]):
+        return LIB_PEAKS
+    tmp = LIB_PEAKS + f".tmp{os.getpid()}"
+    cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PEAKS_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB_PEAKS)
+    return LIB_PEAKS
 
 
 if __name__ == "__main__":

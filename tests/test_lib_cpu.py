@@ -84,3 +84,23 @@ def test_debug_build_exports_match():
     path = build(debug=True)
     assert os.path.basename(path) == "libfastid_debug.so"
     assert exported_functions(path) == declared_functions()
+
+
+def test_peaks_library_builds_and_exports():
+    """The roofline microbenchmarks compile for sm_103a and export their
+    three entry points."""
+    from paper_1707_00516_gb300.build import build_peaks
+    path = build_peaks()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    names = sorted({ln.split()[-1] for ln in out.splitlines() if " T fastid_peaks_" in ln})
+    assert names == ["fastid_peaks_alu", "fastid_peaks_b1", "fastid_peaks_mma"]
+
+
+def test_peaks_operand_encoding():
+    """e4m3: +1 = 0x38 (exponent 7 = bias), -1 = 0xB8; e2m1: +1 = 0x2
+    (exponent 1 = bias), -1 = 0xA; element 2i in the low nibble of byte i."""
+    import numpy as np
+    from paper_1707_00516_gb300.peaks import encode
+    v = np.array([[1, -1, 0, 1]])
+    assert encode(v, False).tolist() == [[0x38, 0xB8, 0x00, 0x38]]
+    assert encode(v, True).tolist() == [[0xA2, 0x20]]
