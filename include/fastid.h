@@ -74,9 +74,16 @@ enum {
     FASTID_FORM_TENSOR = 2,        /* 0/1 and +-1 operands in FP8 e4m3 on tcgen05, FP32 accum,
                                       the reference operand read from the database's FP8 copy
                                       (FASTID_REFS_TENSOR), else from its packed rows      */
-    FASTID_FORM_TENSOR_PACKED = 3  /* the tensor form with the reference operand always read
+    FASTID_FORM_TENSOR_PACKED = 3, /* the tensor form with the reference operand always read
                                       as packed bits and expanded to FP8 on chip (1/8 of the
                                       bytes; no FP8 copy needed)                          */
+    FASTID_FORM_TENSOR_FP4 = 4,    /* 0/1 and +-1 operands as block-scaled FP4 (e2m1 with unit
+                                      scale factors, tcgen05 kind::mxf4), FP32 accum: twice
+                                      the FP8 rate per clock; the reference operand read from
+                                      the database's FP4 copy (FASTID_REFS_FP4), else from its
+                                      packed rows expanded to FP4 on chip                 */
+    FASTID_FORM_TENSOR_FP4_PACKED = 5 /* the FP4 tensor form with the reference operand always
+                                      read as packed bits and expanded on chip            */
 };
 /* FASTID_FORM_AUTO: the tensor form; its reference operand is the FP8 copy when
  * the database has one and the call has more than 256 queries (two query
@@ -84,7 +91,8 @@ enum {
 
 /* fastid_load_refs flags */
 enum {
-    FASTID_REFS_TENSOR = 1u /* also build the FP8 operand copy used by the tensor form */
+    FASTID_REFS_TENSOR = 1u, /* also build the FP8 operand copy used by the tensor form  */
+    FASTID_REFS_FP4 = 2u     /* also build the FP4 operand copy (half a byte per locus)  */
 };
 
 #define FASTID_MAX_K 32          /* largest k accepted by fastid_topk          */
@@ -166,8 +174,10 @@ fastid_status fastid_mix(fastid_ctx *ctx, const uint64_t *src_dev, int64_t ld_sr
 /*
  * Copy n_refs packed reference profiles into a device-resident database
  * owned by the library (the known profiles of Sec. II-B, matrix A), compute
- * their popcounts, and with FASTID_REFS_TENSOR also build the FP8 operand copy
- * (1 byte per locus) used by the tensor form.  The caller's buffer may be
+ * their popcounts, with FASTID_REFS_TENSOR also build the FP8 operand copy
+ * (1 byte per locus) used by the tensor form, and with FASTID_REFS_FP4 the FP4
+ * operand copy (loci padded to 256, half a byte each) used by
+ * FASTID_FORM_TENSOR_FP4.  The caller's buffer may be
  * freed once the stream has passed this call.
  *  packed_dev  uint64 [n_refs][ld_words], bits at loci >= n_loci zero.
  *  n_refs      1 .. 2^31 - 1;  n_loci 1 .. FASTID_MAX_LOCI.

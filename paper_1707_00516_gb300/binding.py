@@ -21,8 +21,8 @@ LIB_PATH = os.path.join(_PKG, "libfastid.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EUNSUPPORTED, EDEVICE = range(8)
 MODE_MISMATCH, MODE_UNEXPLAINED = 0, 1
-FORM_AUTO, FORM_PLAIN, FORM_TENSOR, FORM_TENSOR_PACKED = 0, 1, 2, 3
-REFS_TENSOR = 1
+FORM_AUTO, FORM_PLAIN, FORM_TENSOR, FORM_TENSOR_PACKED, FORM_TENSOR_FP4, FORM_TENSOR_FP4_PACKED = range(6)
+REFS_TENSOR, REFS_FP4 = 1, 2
 MAX_K = 32
 MAX_LOCI = 65536
 NO_THRESHOLD = 0xFFFFFFFF

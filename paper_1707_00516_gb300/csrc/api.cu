@@ -228,7 +228,7 @@ const char *fastid_last_error(const fastid_ctx *ctx) { return ctx ? ctx->last_er
 fastid_status fastid_set_form(fastid_ctx *ctx, int32_t form) {
     if (!ctx) return FASTID_EINVAL;
     if (form != FASTID_FORM_AUTO && form != FASTID_FORM_PLAIN && form != FASTID_FORM_TENSOR &&
-        form != FASTID_FORM_TENSOR_PACKED)
+        form != FASTID_FORM_TENSOR_PACKED && form != FASTID_FORM_TENSOR_FP4 && form != FASTID_FORM_TENSOR_FP4_PACKED)
         return fail(ctx, FASTID_EINVAL, "unknown form %d", form);
     ctx->form = form;
     return FASTID_OK;
@@ -293,7 +293,7 @@ fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int6
     if (n_loci < 1 || n_loci > FASTID_MAX_LOCI) return fail(ctx, FASTID_EINVAL, "n_loci out of range");
     if (ld_words < (n_loci + 63) / 64) return fail(ctx, FASTID_EINVAL, "ld_words too small");
     if (!packed_dev) return fail(ctx, FASTID_EINVAL, "packed is NULL");
-    if (flags & ~(uint32_t)FASTID_REFS_TENSOR) return fail(ctx, FASTID_EINVAL, "unknown flags");
+    if (flags & ~(uint32_t)(FASTID_REFS_TENSOR | FASTID_REFS_FP4)) return fail(ctx, FASTID_EINVAL, "unknown flags");
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     fastid_refdb *db = new (std::nothrow) fastid_refdb();
     if (!db) return fail(ctx, FASTID_ENOMEM, "host allocation");
@@ -325,7 +325,9 @@ fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int6
     }
     count_launches(ctx, 1);
     db->kpad = tensor_kpad(n_loci);
+    db->kbytes4 = tensor_kbytes4(n_loci);
     e = make_packed_map(&db->map_p, db->packed, db->n_pad, db->ld64);
+    if (e == cudaSuccess) e = make_packed_map(&db->map_p4, db->packed, db->n_pad, db->ld64, 4, tensor_tile_r4());
     if (e != cudaSuccess) {
         cudaStreamSynchronize((cudaStream_t)stream);
         cudaFree(db->packed);
@@ -355,6 +357,29 @@ fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int6
         db->bytes += (int64_t)fbytes;
         count_launches(ctx, 1);
     }
+    if (flags & FASTID_REFS_FP4) {
+        const size_t fbytes = (size_t)db->n_pad * db->kbytes4;
+        e = cudaMalloc(&db->fp4, fbytes);
+        if (e == cudaSuccess)
+            e = launch_refs_e2m1(db->packed, db->ld64, db->n_pad, (int32_t)db->ld64, db->n_pad, db->kbytes4, db->fp4,
+                                 ctx->grid_tensor * 32, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = make_operand_map(&db->map_b4, db->fp4, db->n_pad, db->kbytes4, tensor_tile_r4());
+        if (e == cudaSuccess)
+            e = make_operand_map(&db->map_b4_half, db->fp4, db->n_pad, db->kbytes4, tensor_tile_r4() / 2);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamSynchronize((cudaStream_t)stream);
+            if (db->fp4) cudaFree(db->fp4);
+            if (db->fp8) cudaFree(db->fp8);
+            cudaFree(db->packed);
+            cudaFree(db->norms);
+            delete db;
+            return fail(ctx, e == cudaErrorMemoryAllocation ? FASTID_ENOMEM : FASTID_ECUDA,
+                        "FP4 operand copy (%zu bytes): %s", fbytes, cudaGetErrorString(e));
+        }
+        db->bytes += (int64_t)fbytes;
+        count_launches(ctx, 1);
+    }
     *out = db;
     return FASTID_OK;
 }
@@ -366,6 +391,7 @@ fastid_status fastid_free_refs(fastid_ctx *ctx, fastid_refdb *db) {
     cudaFree(db->packed);
     cudaFree(db->norms);
     if (db->fp8) cudaFree(db->fp8);
+    if (db->fp4) cudaFree(db->fp4);
     delete db;
     (void)ctx;
     return FASTID_OK;
@@ -404,10 +430,10 @@ fastid_status prepare(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q
     return FASTID_OK;
 }
 
-// 0 plain, 1 tensor form over the FP8 copy, 2 tensor form over the packed rows.
-// slots16: the launch keeps 16-slot lists (k <= 16, or no top-k).
-fastid_status pick_form(fastid_ctx *ctx, const fastid_refdb *db, int64_t n_q, int *tensor, bool slots16 = true) {
-    *tensor = fastid::pick_operand(ctx->form, db->fp8 != nullptr, n_q, slots16);
+// The call's operand (fastid::Operand).  slots16: the launch keeps 16-slot
+// lists (k <= 16, or no top-k).
+fastid_status pick_form(fastid_ctx *ctx, const fastid_refdb *db, int64_t n_q, int *op, bool slots16 = true) {
+    *op = fastid::pick_operand(ctx->form, db->fp8 != nullptr, db->fp4 != nullptr, n_q, slots16);
     return FASTID_OK;
 }
 
@@ -431,20 +457,25 @@ struct TensorPrep {
 
 enum ExtraKind { EXTRA_NONE, EXTRA_TOPK, EXTRA_HITS };
 
-// pk: reference operand read as packed rows and expanded on chip (unpaired;
-// queries encoded at half scale to match the expanded 2.0).
+// op (an operand other than OP_PLAIN): FP8 or FP4 operands; packed rows
+// expanded on chip are unpaired, and their FP8 queries are encoded at half
+// scale to match the expanded 2.0.
 fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q, int64_t ld_q, int64_t n_q,
                              const uint8_t *modes, cudaStream_t s, Scratch &scr, ExtraKind ek, int64_t karg,
-                             size_t *extra_off, TensorPrep *tp, bool pk) {
+                             size_t *extra_off, TensorPrep *tp, int op) {
     TcLaunch &L = tp->L;
     memset(&L, 0, sizeof L);
+    const bool pk = op_packed(op), f4 = op_f4(op);
     const int64_t n_qt = round_up(n_q, tensor_tile_q()) / tensor_tile_q();
     L.pk = pk ? 1 : 0;
+    L.f4 = f4 ? 1 : 0;
     L.pair = (!pk && ctx->pair_clusters > 0 && n_qt >= PAIR_MIN_TILES) ? 1 : 0;
     const int64_t n_q_pad = round_up(n_q, (int64_t)tensor_tile_q() * (L.pair ? 2 : 1));
     const int64_t n_qq = n_q_pad / tensor_tile_q() / (L.pair ? 2 : 1);
-    const int64_t n_rt = db->n_pad / tensor_tile_r();
-    const int64_t tile_bytes = (int64_t)tensor_tile_r() * (pk ? db->ld64 * 8 : db->kpad);
+    const int64_t tile_r = f4 ? tensor_tile_r4() : tensor_tile_r();
+    const int64_t n_rt = (db->n_pad + tile_r - 1) / tile_r;
+    const int32_t kbytes = f4 ? db->kbytes4 : db->kpad;  // operand row bytes
+    const int64_t tile_bytes = tile_r * (pk ? db->ld64 * 8 : kbytes);
     L.n_groups = make_tensor_schedule(1, &n_qq, &n_rt, &tile_bytes, L.pair ? ctx->pair_clusters : ctx->grid_tensor,
                                       L.pair ? 2 : 1, L.sched, L.order, &L.n_slots);
     if (L.n_groups == -2) return fail(ctx, FASTID_EDEVICE, "schedule self-check failed (debug build)");
@@ -454,22 +485,29 @@ fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint
     if (ek == EXTRA_TOPK) extra = (size_t)L.n_slots * tensor_tile_q() * (size_t)karg * 8;
     if (ek == EXTRA_HITS) extra = 256 + (size_t)(2 + hits_sort_elems(karg) * 3 / 2 + 1) * 8;
     Carver cv;
-    size_t o_a = cv.take<uint8_t>((size_t)n_q_pad * db->kpad);
+    size_t o_a = cv.take<uint8_t>((size_t)n_q_pad * kbytes);
     size_t o_c = cv.take<float>((size_t)n_q_pad);
     *extra_off = cv.take<uint8_t>(extra);
     FASTID_CUDA(ctx, scr.alloc(cv.off));
     uint8_t *a = at<uint8_t>(scr.p, o_a);
     float *qconst = at<float>(scr.p, o_c);
-    FASTID_CUDA(ctx, launch_queries_e4m3(q, ld_q, n_q, db->n_words64, db->n_loci, modes, n_q_pad, db->kpad, a,
-                                         qconst, pk, s));
+    if (f4)
+        FASTID_CUDA(ctx, launch_queries_e2m1(q, ld_q, n_q, db->n_words64, db->n_loci, modes, n_q_pad, kbytes, a,
+                                             qconst, s));
+    else
+        FASTID_CUDA(ctx, launch_queries_e4m3(q, ld_q, n_q, db->n_words64, db->n_loci, modes, n_q_pad, kbytes, a,
+                                             qconst, pk, s));
     count_launches(ctx, 1);
-    FASTID_CUDA(ctx, make_operand_map(&L.map_a[0], a, n_q_pad, db->kpad, tensor_tile_q()));
+    FASTID_CUDA(ctx, make_operand_map(&L.map_a[0], a, n_q_pad, kbytes, tensor_tile_q()));
     L.n_panels = 1;
-    L.map_b[0] = pk ? db->map_p : L.pair ? db->map_b_half : db->map_b;
+    if (f4)
+        L.map_b[0] = pk ? db->map_p4 : L.pair ? db->map_b4_half : db->map_b4;
+    else
+        L.map_b[0] = pk ? db->map_p : L.pair ? db->map_b_half : db->map_b;
     L.n_refs[0] = db->n_refs;
     L.n_q[0] = n_q;
     L.n_rt[0] = n_rt;
-    L.kpad[0] = db->kpad;
+    L.kpad[0] = kbytes;
     L.qconst[0] = qconst;
     L.status = ctx->dev_status;
     return FASTID_OK;
@@ -504,7 +542,7 @@ fastid_status fastid_scores(fastid_ctx *ctx, const fastid_refdb *db, const uint6
     if (tensor) {
         TensorPrep tp;
         if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_NONE, 0, &xo, &tp,
-                                 tensor == 2)))
+                                 tensor)))
             return st;
         tp.L.epi = out_bytes == 2 ? EPI_SCORES16 : EPI_SCORES32;
         tp.L.threshold = 0xFFFFFFFFu;
@@ -548,7 +586,7 @@ fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_
         TensorPrep tp;
         size_t xo;
         if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_TOPK, k, &xo, &tp,
-                                 tensor == 2)))
+                                 tensor)))
             return st;
         uint64_t *partial = at<uint64_t>(scr.p, xo);
         tp.L.epi = EPI_TOPK;
@@ -615,16 +653,21 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
 
 namespace fastid {
 
-int pick_operand(int form, bool has_fp8, int64_t n_q, bool slots16) {
+int pick_operand(int form, bool has_fp8, bool has_fp4, int64_t n_q, bool slots16) {
+    (void)has_fp4;
     switch (form) {
         case FASTID_FORM_PLAIN:
-            return 0;
+            return OP_PLAIN;
         case FASTID_FORM_TENSOR_PACKED:
-            return 2;
+            return OP_FP8_PACKED;
         case FASTID_FORM_TENSOR:
-            return has_fp8 ? 1 : 2;
+            return has_fp8 ? OP_FP8 : OP_FP8_PACKED;
+        case FASTID_FORM_TENSOR_FP4:
+            return has_fp4 ? OP_FP4 : OP_FP4_PACKED;
+        case FASTID_FORM_TENSOR_FP4_PACKED:
+            return OP_FP4_PACKED;
         default:  // AUTO: a few queries read the operand about once; packed rows are 1/8 of the bytes
-            return has_fp8 && n_q > (slots16 ? AUTO_PACKED_MAX_Q16 : AUTO_PACKED_MAX_Q) ? 1 : 2;
+            return has_fp8 && n_q > (slots16 ? AUTO_PACKED_MAX_Q16 : AUTO_PACKED_MAX_Q) ? OP_FP8 : OP_FP8_PACKED;
     }
 }
 
@@ -644,7 +687,7 @@ fastid_status compare_append(fastid_ctx *ctx, const fastid_refdb *db, const uint
         TensorPrep tp;
         size_t xo;
         if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_NONE, 0, &xo, &tp,
-                                 tensor == 2)))
+                                 tensor)))
             return st;
         tp.L.epi = EPI_HITS;
         tp.L.threshold = clamp_threshold(threshold, db->n_loci);

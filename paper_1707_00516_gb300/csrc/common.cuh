@@ -121,13 +121,14 @@ struct TcSched {
 struct TcLaunch {
     int32_t n_panels;
     int32_t pair;  // 2-CTA clusters sharing reference stages (groups are clusters, tiles are pairs)
-    int32_t pk;    // packed references expanded on chip (map_b over the packed rows; queries at half scale)
+    int32_t pk;    // packed references expanded on chip (map_b over the packed rows; FP8 queries at half scale)
+    int32_t f4;    // block-scaled FP4 operands (224-reference tiles); else FP8
     CUtensorMap map_a[TC_MAXP];
     CUtensorMap map_b[TC_MAXP];
     int64_t n_refs[TC_MAXP];
     int64_t n_q[TC_MAXP];
     int64_t n_rt[TC_MAXP];
-    int32_t kpad[TC_MAXP];
+    int32_t kpad[TC_MAXP];  // operand row bytes (a multiple of 128)
     const float *qconst[TC_MAXP];
     TcSched sched[TC_MAXP];
     int32_t order[TC_MAXP];  // panel order of every group's walk
@@ -214,8 +215,19 @@ cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_src
 cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
                                 const uint8_t *modes, int64_t n_q_pad, int32_t kpad, uint8_t *out, float *qconst,
                                 bool half, cudaStream_t s);
-// TMA map over packed rows for packed-reference (PK) launches.
-cudaError_t make_packed_map(CUtensorMap *map, const uint64_t *packed, int64_t rows, int64_t ld64);
+// TMA map over packed rows for packed-reference (PK) launches: boxes of 2
+// words x 256 rows (FP8 stages) or 4 words x 224 rows (FP4 stages).
+cudaError_t make_packed_map(CUtensorMap *map, const uint64_t *packed, int64_t rows, int64_t ld64, int box_words = 2,
+                            int box_rows = 256);
+// FP4 form: reference tile (224), operand row bytes of n_loci (loci padded to
+// 256, two per byte), the database's FP4 copy and the query operand.
+int tensor_tile_r4();
+int tensor_kbytes4(int32_t n_loci);
+cudaError_t launch_refs_e2m1(const uint64_t *packed, int64_t ld64, int64_t n_src, int32_t n_words, int64_t n_rows,
+                             int32_t kbytes, uint8_t *out, int max_blocks, cudaStream_t s);
+cudaError_t launch_queries_e2m1(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
+                                const uint8_t *modes, int64_t n_q_pad, int32_t kbytes, uint8_t *out, float *qconst,
+                                cudaStream_t s);
 
 cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s);
 cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s);

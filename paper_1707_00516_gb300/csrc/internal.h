@@ -51,25 +51,40 @@ struct fastid_refdb {
     uint32_t *norms = nullptr;   // [n_pad]
     uint8_t *fp8 = nullptr;      // [n_pad][kpad] e4m3 0/1 operand (FASTID_REFS_TENSOR)
     int32_t kpad = 0;            // loci padded to the tensor form's K stage
+    uint8_t *fp4 = nullptr;      // [n_pad][kbytes4] e2m1 0/1 operand (FASTID_REFS_FP4)
+    int32_t kbytes4 = 0;         // its row bytes: loci padded to 256, two per byte
     CUtensorMap map_b;           // TMA map over fp8 (boxes of K-stage x reference tile)
     CUtensorMap map_b_half;      // same, boxes of half a reference tile (paired launches)
     CUtensorMap map_p;           // TMA map over packed (boxes of 2 words x 256 refs, packed-operand launches)
+    CUtensorMap map_b4;          // TMA map over fp4 (boxes of 128 bytes x 224 refs)
+    CUtensorMap map_b4_half;     // same, boxes of 112 refs (paired FP4 launches)
+    CUtensorMap map_p4;          // TMA map over packed (boxes of 4 words x 224 refs, packed FP4 launches)
     int64_t bytes = 0;
     int device = 0;
 };
 
 namespace fastid {
-// Operand of a comparison call: 0 plain form, 1 tensor form over the FP8 copy,
-// 2 tensor form over the packed rows (expanded on chip).  AUTO takes the FP8
-// copy, when there is one, above AUTO_PACKED_MAX_Q queries, or above
-// AUTO_PACKED_MAX_Q16 for launches with 16-slot lists (k <= 16, hits, score
-// matrices), whose packed kernel has twice the expanding warps.  Measured on
-// 20M references at N = 2048: one query tile, packed rows 3.35 ms (k = 16) /
-// 4.15 ms (k = 32) against 5.8 ms over the FP8 copy; two tiles, packed rows
-// 6.4 ms (k = 16) / 8.4 ms (k = 32) against 6.7 ms as a pair over the FP8 copy.
+// Operand of a comparison call.
+enum Operand : int {
+    OP_PLAIN = 0,       // plain form (packed words, AND + POPC)
+    OP_FP8 = 1,         // tensor form over the database's FP8 copy
+    OP_FP8_PACKED = 2,  // tensor form over the packed rows, expanded to FP8 on chip
+    OP_FP4 = 3,         // tensor form over the database's FP4 copy
+    OP_FP4_PACKED = 4,  // tensor form over the packed rows, expanded to FP4 on chip
+};
+__host__ __device__ inline bool op_tensor(int op) { return op != OP_PLAIN; }
+__host__ __device__ inline bool op_packed(int op) { return op == OP_FP8_PACKED || op == OP_FP4_PACKED; }
+__host__ __device__ inline bool op_f4(int op) { return op == OP_FP4 || op == OP_FP4_PACKED; }
+// FP8 operands under AUTO: the FP8 copy, when there is one, above
+// AUTO_PACKED_MAX_Q queries, or above AUTO_PACKED_MAX_Q16 for launches with
+// 16-slot lists (k <= 16, hits, score matrices), whose packed kernel has twice
+// the expanding warps.  Measured on 20M references at N = 2048: one query
+// tile, packed rows 3.35 ms (k = 16) / 4.15 ms (k = 32) against 5.8 ms over
+// the FP8 copy; two tiles, packed rows 6.4 ms (k = 16) / 8.4 ms (k = 32)
+// against 6.7 ms as a pair over the FP8 copy.
 constexpr int64_t AUTO_PACKED_MAX_Q = 128;
 constexpr int64_t AUTO_PACKED_MAX_Q16 = 256;
-int pick_operand(int form, bool has_fp8, int64_t n_q, bool slots16 = true);
+int pick_operand(int form, bool has_fp8, bool has_fp4, int64_t n_q, bool slots16 = true);
 
 // The hit-list half of fastid_compare: every (q, r) with score <= threshold of
 // this call is appended at atomicAdd(count) (stored while < capacity),

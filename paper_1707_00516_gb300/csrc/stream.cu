@@ -139,8 +139,9 @@ fastid_status stream_blocks(fastid_ctx *ctx, const StreamRefs &R, int64_t n_q, b
     // calls pick it): the FP8 operand is built per block only for the tensor
     // form over the FP8 copy; the plain form and the tensor form over packed
     // rows read the padded rows.
-    const int op = pick_operand(ctx->form, (R.flags & FASTID_REFS_TENSOR) != 0, n_q, slots16);
-    const bool tensor = op == 1;
+    // An FP4 form takes the packed rows of each block, expanded on chip.
+    const int op = pick_operand(ctx->form, (R.flags & FASTID_REFS_TENSOR) != 0, false, n_q, slots16);
+    const bool tensor = op == OP_FP8;
     const bool rows = !tensor;
 
     StreamState st(ctx, s);
@@ -156,11 +157,13 @@ fastid_status stream_blocks(fastid_ctx *ctx, const StreamRefs &R, int64_t n_q, b
         db.ld64 = ld64;
         db.flags = R.flags;
         db.kpad = kpad;
+        db.kbytes4 = tensor_kbytes4(R.n_loci);
         sl.staging = static_cast<uint64_t *>(st.take((size_t)block * n_words * 8, e));
         if (rows) {
             db.packed = static_cast<uint64_t *>(st.take((size_t)cap * ld64 * 8, e));
             db.norms = static_cast<uint32_t *>(st.take((size_t)cap * 4, e));
             if (e == cudaSuccess) e = make_packed_map(&db.map_p, db.packed, cap, ld64);
+            if (e == cudaSuccess) e = make_packed_map(&db.map_p4, db.packed, cap, ld64, 4, tensor_tile_r4());
         }
         if (tensor) {
             db.fp8 = static_cast<uint8_t *>(st.take((size_t)cap * kpad, e));

@@ -1,5 +1,10 @@
 // Tensor-core form of the overloaded matrix multiply on 5th-generation
-// tensor cores (tcgen05), FP8 e4m3 operands, FP32 accumulation in TMEM.
+// tensor cores (tcgen05), FP32 accumulation in TMEM, with the 0/+-1 operands
+// in one of two encodings:
+//   FP8   kind::f8f6f4, e4m3 bytes (0x00, 0x38 = +1, 0xB8 = -1), K = 32 a MMA
+//   FP4   kind::mxf4 block-scaled, e2m1 nibbles (0x0, 0x2 = +1, 0xA = -1)
+//         with every ue8m0 scale factor 2^0, K = 64 a MMA: twice the FP8
+//         rate per SM clock on GB300, and a quarter of the FP8 copy's bytes.
 //
 // The paper computes POPC(AND(XOR(R, Q), R)) word by word (Eq. 1,
 // Algorithm 3).  On 0/1 vectors the same counts are ordinary dot products,
@@ -12,8 +17,10 @@
 // magnitude <= N <= 65536 < 2^24, exact in FP32 whatever the order of the
 // additions; 0, +1 and -1 are exact in e4m3 (0x00, 0x38, 0xB8).
 //
-// Tile: M = 128 queries (TMEM lanes) x N = 256 references (TMEM columns),
-// K staged 128 loci (one 128-byte swizzle atom) per pipeline stage by TMA.
+// Tile: M = 128 queries (TMEM lanes) x N = 256 references (TMEM columns;
+// 224 for FP4, whose two accumulators then leave TMEM columns 448-511 for the
+// scale factors), K staged one 128-byte swizzle atom per pipeline stage by
+// TMA (128 loci in FP8, 256 in FP4).
 // Warp roles in a 192-thread CTA, one CTA per SM (persistent):
 //   warp 0       TMA producer (one lane)
 //   warp 1       TMEM allocation + MMA issue (one lane)
@@ -42,19 +49,28 @@ constexpr int TC_THREADS = 192;     // producer, MMA issuer, 4 epilogue warps
 // 384 threads get at most 168 registers a thread, which the 16-slot top-k
 // fits (4 expanding warps) and the 32-slot one does not (2).
 __host__ __device__ constexpr int pk_threads(int km) { return km == 16 ? 128 : 64; }
-constexpr uint32_t TC_P_BYTES = 256 * 16;  // packed reference stage: 256 rows x 128 bits
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK;  // 16 KB
+// Packed reference stage of PK launches: BN rows of the stage's loci (128
+// bits for FP8, 256 for FP4).
+__host__ __device__ constexpr uint32_t pk_stage_bytes(int bn, bool f4) { return (uint32_t)bn * (f4 ? 32u : 16u); }
+// FP4 launches: reference tiles of 224, unit scale factors in TMEM columns
+// TC_SF_COL.. (A's from TC_SF_COL, B's from TC_SF_COL + 16), all lanes.
+constexpr int TC_BN4 = 224;
+constexpr uint32_t TC_SF_COL = 448;
+constexpr uint32_t TC_SF_UNIT = 0x7F7F7F7Fu;  // four ue8m0 bytes of 2^0
 constexpr uint64_t WAIT_NS = 2000000000ull;     // 2 s per wait
 constexpr uint64_t RENDEZVOUS_NS = 50000000ull;  // 50 ms per panel entry, then go on alone
 
 // Kernel variants: references per tile (the MMA's N) and pipeline depth.
 //   BN = 256: 32 KB reference stage, 4 stages, 2 x 256 TMEM columns
+//   BN = 224: 28 KB reference stage, 4 stages, 2 x 224 TMEM columns + scale
+//             factors (FP4)
 //   BN = 128: 16 KB reference stage, 6 stages, 2 x 128 TMEM columns
 template <int BN>
 struct TcShape {
-    static constexpr int STAGES = BN == 256 ? 4 : 6;
+    static constexpr int STAGES = BN == 128 ? 6 : 4;
     static constexpr uint32_t B_BYTES = (uint32_t)BN * TC_BK;
-    static constexpr uint32_t TMEM_COLS = BN == 256 ? 512 : 256;
+    static constexpr uint32_t TMEM_COLS = BN == 128 ? 256 : 512;
 };
 
 // One database ("panel") of a launch, with its schedule (TcSched).
@@ -62,15 +78,16 @@ struct PanelDesc {
     int64_t n_refs;
     int64_t n_q;          // real query rows (the operand is padded to whole tiles)
     int64_t n_rt;         // reference tiles
-    int32_t n_kb;         // K stages of 128 loci
+    int32_t n_kb;         // K stages of 128 operand bytes
     TcSched sc;
     const float *qconst;  // c_q per padded query row
 };
 
 struct TcMaps {
     CUtensorMap a[TC_MAXP];  // query operand of each panel (boxes 128 loci x 128 queries)
-    // reference operand of each panel: FP8 boxes of 128 loci x BN refs (BN/2 when
-    // paired), or, for PK launches, packed boxes of 2 words x 256 refs
+    // reference operand of each panel: boxes of 128 bytes x BN refs (BN/2 when
+    // paired), or, for PK launches, packed boxes of 2 (FP8) or 4 (FP4) words
+    // x BN refs
     CUtensorMap b[TC_MAXP];
 };
 
@@ -211,6 +228,26 @@ __device__ __forceinline__ void tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint6
         : "memory");
 }
 
+// Block-scaled FP4: scale factors of A and B read from TMEM at sfa / sfb.
+__device__ __forceinline__ void tc_mma_f4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+        : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns, every column the value v.
+__device__ __forceinline__ void tmem_fill16(uint32_t taddr, uint32_t v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+        "r"(v)
+        : "memory");
+}
+
 // 32 lanes x 32 consecutive 32-bit columns.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
@@ -245,6 +282,14 @@ __host__ __device__ constexpr uint32_t idesc_f8(int m, int n) {
            | (0u << 7) | (0u << 10)       // A, B format: E4M3
            | ((uint32_t)(n >> 3) << 17)   // N >> 3
            | ((uint32_t)(m >> 4) << 24);  // M >> 4
+}
+
+// Instruction descriptor, kind::mxf4 (block-scaled): B scale-factor id 0
+// (bits 4-5), A = B = E2M1 (1 at bits 7 and 10), both K-major, N >> 3 at bit
+// 17, scale type UE8M0 (bit 23), M >> 4 at bit 24 (for M = 128 the same bit
+// as M >> 7 at bit 27), A scale-factor id 0 (bits 29-30), K = 64 (bit 31 = 0).
+__host__ __device__ constexpr uint32_t idesc_mxf4(int m, int n) {
+    return (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | (1u << 23) | ((uint32_t)(m >> 4) << 24);
 }
 
 // Per-thread top-k list held in registers, ascending by score; entries of
@@ -434,16 +479,45 @@ __device__ __forceinline__ void expand_stage(const uint8_t *sp, uint8_t *sb, int
     }
 }
 
+// FP4 (PK launches): the stage holds 256 loci of each reference row (4
+// packed words, row r at r * 32 bytes) and each 32-locus word becomes one
+// 16-byte chunk of e2m1 nibbles, in the same 128-byte swizzle.  Locus order
+// inside a chunk: nibble n of its 32-bit word j holds locus 4n + j, so word j
+// is bit j of every nibble of the packed word w moved to bit 1 (e2m1 +1.0 =
+// 0x2) by one shift and kept by one mask.  The query operand of every FP4
+// launch is written in the same order (encode_query_row_f4), and so is the
+// database's FP4 copy (refs_e2m1_kernel).
+constexpr uint32_t PK4_BIT1 = 0x22222222u;
+
+template <int NT, int BN>
+__device__ __forceinline__ void expand_stage_f4(const uint8_t *sp, uint8_t *sb, int t) {
+#pragma unroll 1
+    for (int r = t; r < BN; r += NT) {
+        const uint4 lo = *reinterpret_cast<const uint4 *>(sp + r * 32);
+        const uint4 hi = *reinterpret_cast<const uint4 *>(sp + r * 32 + 16);
+        const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t x = w[c];
+            const uint4 o = make_uint4((x << 1) & PK4_BIT1, x & PK4_BIT1, (x >> 1) & PK4_BIT1, (x >> 2) & PK4_BIT1);
+            *reinterpret_cast<uint4 *>(sb + r * 128 + ((c ^ (r & 7)) << 4)) = o;
+        }
+    }
+}
+
 // PAIR: 2-CTA clusters; both CTAs walk the same reference tiles for the two
 // query tiles of a pair (rank r takes tile 2 qq + r), and each multicasts half
-// of every reference stage into both CTAs' shared memory (BN = 256 only).
+// of every reference stage into both CTAs' shared memory.
 // PK: packed reference operand expanded on chip (see expand_stage).
-template <int BN, bool PAIR, int KM, bool PK>
+// F4: block-scaled FP4 operands (kind::mxf4, BN = 224); else FP8 (BN = 256 or 128).
+template <int BN, bool PAIR, int KM, bool PK, bool F4>
 __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS, 1)
     tensor_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TensorArgs args) {
     using S = TcShape<BN>;
-    static_assert(!PAIR || BN == 256, "paired launches use 256-reference tiles");
-    static_assert(!PK || (BN == 256 && !PAIR), "packed-reference launches use unpaired 256-reference tiles");
+    static_assert(F4 ? BN == TC_BN4 : BN != TC_BN4, "FP4 launches use 224-reference tiles, FP8 ones 256 or 128");
+    static_assert(!PAIR || BN != 128, "paired launches use 256- or 224-reference tiles");
+    static_assert(!PK || (BN != 128 && !PAIR), "packed-reference launches use unpaired 256- or 224-reference tiles");
+    constexpr uint32_t P_BYTES = pk_stage_bytes(BN, F4);
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned operand stages (queries, references, and for PK the
     // packed reference stages), then the control block, then staging.
@@ -453,7 +527,7 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
     uint8_t *sA = base;
     uint8_t *sB = base + S::STAGES * TC_A_BYTES;
     uint8_t *sP = base + S::STAGES * (TC_A_BYTES + S::B_BYTES);  // PK only
-    TcSmem *ctl = reinterpret_cast<TcSmem *>(sP + (PK ? S::STAGES * TC_P_BYTES : 0));
+    TcSmem *ctl = reinterpret_cast<TcSmem *>(sP + (PK ? S::STAGES * P_BYTES : 0));
     // per-thread staging of one 32-column chunk, [32][128] floats (rare path)
     float *stage_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(ctl) + 256);
 
@@ -491,6 +565,19 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
     if (PAIR) cluster_sync();  // the peer's barriers exist before any multicast targets them
     tc_fence_after();
     const uint32_t tmem_base = ctl->tmem_base;
+    if (F4) {
+        // unit scale factors: TMEM columns TC_SF_COL .. TC_SF_COL + 63 of every
+        // lane (each epilogue warp fills its lane quadrant) before any MMA
+        if (warp >= 2 && warp < 6) {
+            const uint32_t t = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + TC_SF_COL;
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) tmem_fill16(t + c, TC_SF_UNIT);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -517,11 +604,11 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                                 ok = mbar_wait(smem_u32(&ctl->empty[stage]), phase ^ 1u, abort_flag, args.status, 1);
                                 if (!ok) break;
                                 const uint32_t fb = smem_u32(&ctl->full[stage]);
-                                mbar_expect_tx(fb, TC_A_BYTES + (PK ? TC_P_BYTES : S::B_BYTES));
+                                mbar_expect_tx(fb, TC_A_BYTES + (PK ? P_BYTES : S::B_BYTES));
                                 tma_load_2d(smem_u32(sA + stage * TC_A_BYTES), &maps.a[p], fb, kb * TC_BK,
                                             (int32_t)(qt * TC_BM));
-                                if (PK)  // 2 words (128 loci) x 256 references
-                                    tma_load_2d(smem_u32(sP + stage * TC_P_BYTES), &maps.b[p], fb, kb * 2,
+                                if (PK)  // the stage's loci as packed words (2 FP8, 4 FP4) x BN references
+                                    tma_load_2d(smem_u32(sP + stage * P_BYTES), &maps.b[p], fb, kb * (F4 ? 4 : 2),
                                                 (int32_t)(rt * BN));
                                 else if (PAIR)
                                     tma_load_2d_mc(smem_u32(sB + stage * S::B_BYTES + rank * (S::B_BYTES / 2)),
@@ -560,7 +647,7 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_f8(TC_BM, BN);
+            constexpr uint32_t idesc = F4 ? idesc_mxf4(TC_BM, BN) : idesc_f8(TC_BM, BN);
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
@@ -588,8 +675,13 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                                 const uint64_t ad = sw128_desc(smem_u32(sA + stage * TC_A_BYTES));
                                 const uint64_t bd = sw128_desc(smem_u32(sB + stage * S::B_BYTES));
 #pragma unroll
-                                for (int kk = 0; kk < TC_BK / 32; ++kk)  // K = 32 FP8 per MMA: +32 bytes = +2 in the address field
-                                    tc_mma_f8(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
+                                for (int kk = 0; kk < TC_BK / 32; ++kk) {  // 32 bytes of K per MMA: +2 in the address field
+                                    if (F4)  // K = 64 e2m1
+                                        tc_mma_f4(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, tmem_base + TC_SF_COL,
+                                                  tmem_base + TC_SF_COL + 16, (kb | kk) != 0);
+                                    else  // K = 32 e4m3
+                                        tc_mma_f8(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
+                                }
                                 if (PAIR)
                                     tc_commit_mc(smem_u32(&ctl->empty[stage]), (uint16_t)0x3);
                                 else
@@ -631,7 +723,10 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                         for (int kb = 0; kb < n_kb; ++kb) {
                             ok = mbar_wait(smem_u32(&ctl->full[stage]), phase, abort_flag, args.status, 9);
                             if (!ok) break;
-                            expand_stage<pk_threads(KM)>(sP + stage * TC_P_BYTES, sB + stage * S::B_BYTES, t);
+                            if (F4)
+                                expand_stage_f4<pk_threads(KM), BN>(sP + stage * P_BYTES, sB + stage * S::B_BYTES, t);
+                            else
+                                expand_stage<pk_threads(KM)>(sP + stage * P_BYTES, sB + stage * S::B_BYTES, t);
                             // generic-proxy writes, read next by the tensor core (async proxy)
                             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                             mbar_arrive(smem_u32(&ctl->bfull[stage]));
@@ -879,6 +974,69 @@ __device__ __forceinline__ void encode_query_row(const uint64_t *__restrict__ sr
     if (lane == 0) *qc = mis ? (float)pc : 0.f;
 }
 
+// Reference operand, FP4: row r holds kbytes = (loci padded to 256) / 2
+// bytes; its 16-byte chunk c covers loci 32c .. 32c + 31, in the nibble order
+// of expand_stage_f4 (nibble n of 32-bit word j = locus 32c + 4n + j).  From
+// packed rows at stride ld64 of which the first n_src rows and n_words words
+// exist (zero elsewhere).  One thread per 16 output bytes, streaming loads and
+// stores as in refs_e4m3_kernel.
+__global__ void refs_e2m1_kernel(const uint64_t *__restrict__ packed, int64_t ld64, int64_t n_src, int32_t n_words,
+                                 int64_t n_rows, int32_t kbytes, uint8_t *__restrict__ out) {
+    const int64_t per_row = kbytes / 16;
+    const int64_t total = n_rows * per_row;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / per_row, c = t - r * per_row;
+        const int32_t wi = (int32_t)(c >> 1);
+        const uint64_t w = (r < n_src && wi < n_words) ? __ldcs(packed + r * ld64 + wi) : 0ull;
+        const uint32_t x = (uint32_t)(w >> (32 * (c & 1)));
+        const uint4 o = make_uint4((x << 1) & PK4_BIT1, x & PK4_BIT1, (x >> 1) & PK4_BIT1, (x >> 2) & PK4_BIT1);
+        __stcs(reinterpret_cast<uint4 *>(out + r * (int64_t)kbytes) + c, o);
+    }
+}
+
+// Query operand, FP4, per mode and c_q for one row, by one warp: e2m1 +1
+// (0x2) where l < N and Q_l = 0; in mode 0 also -1 (0xA) where Q_l = 1; 0
+// elsewhere.  Same nibble order as the reference operand.  src == nullptr (a
+// padding row) writes zeros.
+__device__ __forceinline__ void encode_query_row_f4(const uint64_t *__restrict__ src, bool mis, int32_t n_words,
+                                                    int32_t n_loci, int32_t kbytes, uint8_t *__restrict__ dst,
+                                                    float *__restrict__ qc, int lane) {
+    const bool valid = src != nullptr;
+    uint32_t pc = 0;
+    for (int32_t c = lane; c < kbytes / 16; c += 32) {
+        const int32_t l0 = c * 32;
+        uint32_t bits = 0;
+        if (valid && (l0 >> 6) < n_words) bits = (uint32_t)(src[l0 >> 6] >> (l0 & 63));
+        const int32_t live = n_loci - l0;
+        const uint32_t in_n = !valid ? 0u : live >= 32 ? 0xFFFFFFFFu : live <= 0 ? 0u : ((1u << live) - 1u);
+        bits &= in_n;
+        pc += __popc(bits);
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t qb = (bits >> j) & 0x11111111u;  // Q at nibble n = locus 4n + j
+            const uint32_t nb = (in_n >> j) & 0x11111111u;  // l < N
+            w[j] = ((nb & ~qb) << 1) | (mis ? qb * 0xAu : 0u);
+        }
+        reinterpret_cast<uint4 *>(dst)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, off);
+    if (lane == 0) *qc = mis ? (float)pc : 0.f;
+}
+
+__global__ void queries_e2m1_kernel(const uint64_t *__restrict__ q, int64_t ld_q, int64_t n_q, int32_t n_words,
+                                    int32_t n_loci, const uint8_t *__restrict__ modes, int64_t n_q_pad,
+                                    int32_t kbytes, uint8_t *__restrict__ out, float *__restrict__ qconst) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n_q_pad; r += warps_total) {
+        const bool valid = r < n_q;
+        encode_query_row_f4(valid ? q + r * ld_q : nullptr, valid && modes[r] == FASTID_MODE_MISMATCH, n_words,
+                            n_loci, kbytes, out + r * (int64_t)kbytes, qconst + r, lane);
+    }
+}
+
 __global__ void queries_e4m3_kernel(const uint64_t *__restrict__ q, int64_t ld_q, int64_t n_q, int32_t n_words,
                                     int32_t n_loci, const uint8_t *__restrict__ modes, int64_t n_q_pad,
                                     int32_t kpad, uint8_t *__restrict__ out, float *__restrict__ qconst,
@@ -904,9 +1062,9 @@ __global__ void prep_jobs_kernel(const PrepJob *__restrict__ jobs, int64_t n_job
 }
 
 template <int BN>
-size_t tensor_smem(int epi, bool pk = false) {
+size_t tensor_smem(int epi, bool pk = false, bool f4 = false) {
     using S = TcShape<BN>;
-    size_t s = 1024 + S::STAGES * (size_t)(TC_A_BYTES + S::B_BYTES + (pk ? TC_P_BYTES : 0)) + 256;
+    size_t s = 1024 + S::STAGES * (size_t)(TC_A_BYTES + S::B_BYTES + (pk ? pk_stage_bytes(BN, f4) : 0)) + 256;
     if (epi == EPI_TOPK) s += (size_t)32 * TC_BM * sizeof(float);
     return s;
 }
@@ -947,7 +1105,29 @@ cudaError_t make_operand_map(CUtensorMap *map, const uint8_t *base, int64_t rows
 
 int tensor_tile_q() { return TC_BM; }
 int tensor_tile_r() { return 256; }
+int tensor_tile_r4() { return TC_BN4; }
 int tensor_kpad(int32_t n_loci) { return (n_loci + TC_BK - 1) / TC_BK * TC_BK; }
+int tensor_kbytes4(int32_t n_loci) { return (n_loci + 2 * TC_BK - 1) / (2 * TC_BK) * TC_BK; }
+
+cudaError_t launch_refs_e2m1(const uint64_t *packed, int64_t ld64, int64_t n_src, int32_t n_words, int64_t n_rows,
+                             int32_t kbytes, uint8_t *out, int max_blocks, cudaStream_t s) {
+    int64_t total = n_rows * (kbytes / 16);
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) return cudaSuccess;
+    refs_e2m1_kernel<<<(unsigned)blocks, 256, 0, s>>>(packed, ld64, n_src, n_words, n_rows, kbytes, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_queries_e2m1(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
+                                const uint8_t *modes, int64_t n_q_pad, int32_t kbytes, uint8_t *out, float *qconst,
+                                cudaStream_t s) {
+    int64_t blocks = (n_q_pad + 7) / 8;
+    if (blocks > 65535) blocks = 65535;
+    queries_e2m1_kernel<<<(unsigned)blocks, 256, 0, s>>>(q, ld_q, n_q, n_words, n_loci, modes, n_q_pad, kbytes, out,
+                                                         qconst);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_src, int32_t n_words, int64_t n_rows,
                              int32_t kpad, uint8_t *out, int max_blocks, cudaStream_t s) {
@@ -970,13 +1150,15 @@ cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, in
 }
 
 // PK reference operand: the packed rows [rows][ld64] uint64 themselves, in
-// boxes of 2 words (128 loci) x 256 references, unswizzled.
-cudaError_t make_packed_map(CUtensorMap *map, const uint64_t *packed, int64_t rows, int64_t ld64) {
+// boxes of box_words words (2 = 128 loci for FP8 stages, 4 = 256 for FP4) x
+// box_rows references, unswizzled.
+cudaError_t make_packed_map(CUtensorMap *map, const uint64_t *packed, int64_t rows, int64_t ld64, int box_words,
+                            int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     cuuint64_t dims[2] = {(cuuint64_t)ld64, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld64 * 8};
-    cuuint32_t box[2] = {2, 256};
+    cuuint32_t box[2] = {(cuuint32_t)box_words, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t *>(packed), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -996,7 +1178,7 @@ cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s
 // at once (0 if clusters are unavailable).
 int tensor_pair_clusters(int device) {
     size_t smem = tensor_smem<256>(EPI_TOPK);
-    if (cudaFuncSetAttribute(tensor_kernel<256, true, TC_KMAX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(tensor_kernel<256, true, TC_KMAX, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -1016,7 +1198,7 @@ int tensor_pair_clusters(int device) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tensor_kernel<256, true, TC_KMAX, false>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, tensor_kernel<256, true, TC_KMAX, false, false>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -1031,13 +1213,13 @@ int tensor_grid_target(int device) {
 
 namespace {
 
-// One launch of tensor_kernel<BN, PAIR, KM> over n_groups work groups (2-CTA
-// clusters when paired).
-template <int BN, bool PAIR, int KM, bool PK = false>
+// One launch of tensor_kernel<BN, PAIR, KM, PK, F4> over n_groups work groups
+// (2-CTA clusters when paired).
+template <int BN, bool PAIR, int KM, bool PK = false, bool F4 = false>
 cudaError_t launch_variant(const TcMaps &maps, const TensorArgs &a, int32_t n_groups, int epi, cudaStream_t s) {
-    const size_t smem = tensor_smem<BN>(epi, PK);
-    cudaError_t e =
-        cudaFuncSetAttribute(tensor_kernel<BN, PAIR, KM, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = tensor_smem<BN>(epi, PK, F4);
+    cudaError_t e = cudaFuncSetAttribute(tensor_kernel<BN, PAIR, KM, PK, F4>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof cfg);
@@ -1052,7 +1234,7 @@ cudaError_t launch_variant(const TcMaps &maps, const TensorArgs &a, int32_t n_gr
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = PAIR ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, tensor_kernel<BN, PAIR, KM, PK>, maps, a);
+    return cudaLaunchKernelEx(&cfg, tensor_kernel<BN, PAIR, KM, PK, F4>, maps, a);
 }
 
 }  // namespace
@@ -1089,9 +1271,20 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
     a.partial = L.partial;
     a.status = L.status;
     a.arrive = L.arrive;
-    if (L.pair && bn != 256) return cudaErrorInvalidValue;
     // 16-slot lists when k allows (half the insert network, 32 fewer registers)
     const bool k16 = L.epi != EPI_TOPK || L.k <= 16;
+    if (L.f4) {  // 224-reference tiles whatever bn says
+        if (L.pk) {
+            if (L.pair) return cudaErrorInvalidValue;
+            return k16 ? launch_variant<TC_BN4, false, 16, true, true>(maps, a, L.n_groups, L.epi, s)
+                       : launch_variant<TC_BN4, false, 32, true, true>(maps, a, L.n_groups, L.epi, s);
+        }
+        if (L.pair) return k16 ? launch_variant<TC_BN4, true, 16, false, true>(maps, a, L.n_groups, L.epi, s)
+                               : launch_variant<TC_BN4, true, 32, false, true>(maps, a, L.n_groups, L.epi, s);
+        return k16 ? launch_variant<TC_BN4, false, 16, false, true>(maps, a, L.n_groups, L.epi, s)
+                   : launch_variant<TC_BN4, false, 32, false, true>(maps, a, L.n_groups, L.epi, s);
+    }
+    if (L.pair && bn != 256) return cudaErrorInvalidValue;
     if (L.pk) {
         if (L.pair || bn != 256) return cudaErrorInvalidValue;
         return k16 ? launch_variant<256, false, 16, true>(maps, a, L.n_groups, L.epi, s)

@@ -39,9 +39,9 @@ Q[:32] = R[rng.integers(0, n_refs, 32)]
 modes = (rng.random(n_q) < 0.5).astype(np.uint8)
 mis, une = oracle.scores(R, Q)
 es, ei = oracle.topk(oracle.select(mis, une, modes), k)
-for form in (B.FORM_TENSOR, B.FORM_TENSOR_PACKED, B.FORM_PLAIN):
+for form in (B.FORM_TENSOR, B.FORM_TENSOR_PACKED, B.FORM_TENSOR_FP4, B.FORM_TENSOR_FP4_PACKED, B.FORM_PLAIN):
     s = Searcher(0, form)
-    db = s.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci, flags=B.REFS_TENSOR if form == B.FORM_TENSOR else 0)
+    db = s.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci)
     q = torch.empty((n_q, words64(n_loci)), dtype=torch.int64, device="cuda")
     B.fastid_pack(s.ctx, torch.from_numpy(Q).cuda(), n_loci, q)
     sc, ix = s.topk(db, q, torch.from_numpy(modes).cuda(), k)

@@ -13,14 +13,15 @@ from paper_1707_00516_gb300 import binding as B  # noqa: E402
 from paper_1707_00516_gb300.search import Searcher, words64  # noqa: E402
 
 
-FORMS = {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "packed": B.FORM_TENSOR_PACKED}
+FORMS = {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "packed": B.FORM_TENSOR_PACKED, "fp4": B.FORM_TENSOR_FP4,
+         "fp4packed": B.FORM_TENSOR_FP4_PACKED}
 
 
 @pytest.fixture(scope="module", params=sorted(FORMS))
 def searcher(request):
     """One searcher per compute form; databases are loaded with the flags
-    the form needs (the tensor form's e4m3 operand copy; none for the plain
-    form and for the tensor form over packed rows)."""
+    the form needs (the e4m3 or e2m1 operand copy of the tensor forms; none
+    for the plain form and for the tensor forms over packed rows)."""
     import __graft_entry__
     __graft_entry__.build()
     s = Searcher(0, FORMS[request.param])

@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 from paper_1707_00516_gb300 import binding as B  # noqa: E402
 from paper_1707_00516_gb300.search import Searcher, words64  # noqa: E402
 
-FORMS = {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "packed": B.FORM_TENSOR_PACKED}
+FORMS = {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "packed": B.FORM_TENSOR_PACKED, "fp4": B.FORM_TENSOR_FP4,
+         "fp4packed": B.FORM_TENSOR_FP4_PACKED}
 
 
 def _configs(n=48, seed=20251203):
@@ -61,7 +62,7 @@ def test_random_config(searchers, cfg):
     hit_T = T if T != B.NO_THRESHOLD else int(np.percentile(exp, 2))
     oq, orr, osc = oracle.hits(exp, hit_T)
     for name, s in searchers.items():
-        flags = B.REFS_TENSOR if name == "tensor" else 0
+        flags = {"tensor": B.REFS_TENSOR, "fp4": B.REFS_FP4}.get(name, 0)
         db = s.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci, flags=flags)
         q = torch.empty((n_q, words64(n_loci)), dtype=torch.int64, device="cuda")
         B.fastid_pack(s.ctx, torch.from_numpy(Q).cuda(), n_loci, q)

@@ -17,7 +17,8 @@ from paper_1707_00516_gb300 import binding as B  # noqa: E402
 from paper_1707_00516_gb300.search import Searcher, words64  # noqa: E402
 
 
-FORMS = {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "packed": B.FORM_TENSOR_PACKED}
+FORMS = {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "packed": B.FORM_TENSOR_PACKED,
+         "fp4packed": B.FORM_TENSOR_FP4}  # streamed FP4 blocks are expanded on chip
 
 
 @pytest.fixture(scope="module", params=sorted(FORMS))

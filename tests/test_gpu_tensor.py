@@ -15,11 +15,15 @@ from paper_1707_00516_gb300 import binding as B  # noqa: E402
 from paper_1707_00516_gb300.search import Searcher, words64  # noqa: E402
 
 
-@pytest.fixture(scope="module", params=["fp8", "packed"])
+TENSOR_FORMS = {"fp8": B.FORM_TENSOR, "packed": B.FORM_TENSOR_PACKED, "fp4": B.FORM_TENSOR_FP4,
+                "fp4packed": B.FORM_TENSOR_FP4_PACKED}
+
+
+@pytest.fixture(scope="module", params=list(TENSOR_FORMS))
 def ts(request):
     import __graft_entry__
     __graft_entry__.build()
-    s = Searcher(0, B.FORM_TENSOR if request.param == "fp8" else B.FORM_TENSOR_PACKED)
+    s = Searcher(0, TENSOR_FORMS[request.param])
     yield s
     s.ctx.close()
 
@@ -172,7 +176,8 @@ def test_schedule_tail_exact():
     """2048 queries x 100,000 references at N = 96 (words ragged), top-16. The
     schedule is 8 tile pairs on 76 clusters: an 8 x 9 grid over the first 374
     reference tiles plus a tail of 4 clusters x 2 pairs over the last 17. The
-    unpaired packed form gets a 16 x 9 grid plus 8 x 2. Both forms' lists equal
+    unpaired packed form gets a 16 x 9 grid plus 8 x 2; the FP4 forms (224
+    references a tile) get their own grids and tails. Every form's lists equal
     the oracle's element by element, so every tail slot is written and merged."""
     import __graft_entry__
     __graft_entry__.build()
@@ -185,10 +190,9 @@ def test_schedule_tail_exact():
     modes = (rng.random(n_q) < 0.5).astype(np.uint8)
     mis, une = oracle.scores(R, Q)
     es, ei = oracle.topk(oracle.select(mis, une, modes), k)
-    for form in (B.FORM_TENSOR, B.FORM_TENSOR_PACKED):
+    for form in (B.FORM_TENSOR, B.FORM_TENSOR_PACKED, B.FORM_TENSOR_FP4, B.FORM_TENSOR_FP4_PACKED):
         s = Searcher(0, form)
-        db = s.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci,
-                                 flags=B.REFS_TENSOR if form == B.FORM_TENSOR else 0)
+        db = s.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci)
         q = torch.empty((n_q, words64(n_loci)), dtype=torch.int64, device="cuda")
         B.fastid_pack(s.ctx, torch.from_numpy(Q).cuda(), n_loci, q)
         sc, ix = s.topk(db, q, torch.from_numpy(modes).cuda(), k)
