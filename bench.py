@@ -1,31 +1,35 @@
 #!/usr/bin/env python3
-"""FastID all-pairs comparison benchmark on GB300.
+"""FastID all-pairs comparison benchmark on one GB300.
 
 Metric: query x reference comparisons per second at N loci, bit-exact
-(results are checked against the CPU oracle on a sample by the tests and by
---check here).  One step = one pass of the whole path over one batch of
-queries: pack the queries' contributor alleles, build the mixtures (OR),
-compare every query with every resident reference and reduce to the
-per-query top-k under a threshold.  The reference database is resident in
-HBM (loaded once, outside the timed region).
+(results are checked against the CPU oracle by the tests), and for the
+serving and batched workloads the p50/p99 batch latency.  One step = one pass
+of the whole path over one batch of queries: pack the queries' contributor
+alleles, build the mixtures (OR), compare every query with every resident
+reference and reduce to the per-query top-k under a threshold.  The
+reference database is resident in HBM (loaded once, outside the timed region).
 
 Default workload: 2048 unknowns (1024 individuals, 1024 mixtures of 2-5
-people) x 20,000,000 references, N = 2048 loci, top-32, threshold 512.
+people) x 20,000,000 references, N = 2048 loci, top-32, threshold 512, timed
+in the plain, FP8 and FP4 forms (the fastest is the headline), followed by
+the serving workload (Poisson requests, p50/p99 latency) and the batched
+workload (256 uneven batches over 4 loci panels, one graph replay) as the
+line's `serving` and `batched` objects.
 
-    python bench.py [--steps K] [--warmup W] [--form plain|tensor|both]
-    python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
-    torchrun --nproc-per-node N bench.py --gpus N   (N independent replicas)
+    python bench.py [--steps K] [--warmup W] [--form all|plain|fp8|fp4|...]
+    python bench.py --config c4|c5        (batched / serving alone)
+    python bench.py --impl reference ...  (the CPU oracle on a bounded sample)
 
-Prints one JSON line (rank 0).
+The library compares on one device per call; bench.py runs on one GPU
+(--gpus 1) and refuses a multi-process launch.  Prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import re
-import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -46,11 +50,12 @@ import gen  # noqa: E402
 
 WORKLOADS = {
     "c3": dict(workload="2048q_x_20M_refs_N2048_top32_T512", n_q=2048, n_refs=20_000_000, n_loci=2048,
-               k=32, threshold=512, cfg=3),
+               k=32, threshold=512, cfg=3, output="per-query top-k"),
     "c2": dict(workload="2048mix_x_1M_refs_N4096_top16_T0", n_q=2048, n_refs=1_000_000, n_loci=4096,
-               k=16, threshold=0, cfg=2),
+               k=16, threshold=0, cfg=2, output="per-query top-k"),
     "c1": dict(workload="64q_x_10k_refs_N1024_full_uint16_matrices", n_q=64, n_refs=10_000, n_loci=1024,
-               k=32, threshold=0xFFFFFFFF, cfg=1),
+               k=32, threshold=0xFFFFFFFF, cfg=1,
+               output="both full uint16 score matrices (both scores of every pair)"),
     "c4": dict(workload="256_batches_1-512q_panels_N512-2048-8192-16384_x_4M_refs_top16", n_refs=4_000_000,
                panels=(512, 2048, 8192, 16384), n_batches=256, k=16, threshold=0xFFFFFFFF, cfg=4),
     "c5": dict(workload="serving_poisson200bps_1-256q_N2048_x_20M_refs_top16", n_refs=20_000_000, n_loci=2048,
@@ -60,12 +65,30 @@ WORKLOADS = {
 METRIC = "query x reference comparisons/s at N loci, bit-exact"
 UNIT = "comparisons/s"
 
-# Peak popcount rate of the plain form's bound: POPC issues 16 results per
-# clock per SM (integer-pipe throughput table for compute capability 10.x),
-# 152 SMs, at the maximum SM clock.
-POPC_PER_CLK_PER_SM = 16
-# Dense e4m3 tensor rate relative to bf16 (nominal 4.5 vs 2.25 PFLOP/s).
-FP8_OVER_BF16 = 2.0
+# Compute forms: FASTID_FORM_* name, the database copy it reads, the
+# arithmetic type of the line's dtype key.
+FORMS = {
+    "plain": ("FORM_PLAIN", 0, "u32"),
+    "fp8": ("FORM_TENSOR", "REFS_TENSOR", "e4m3xe4m3->f32"),
+    "fp8packed": ("FORM_TENSOR_PACKED", 0, "e4m3xe4m3->f32"),
+    "fp4": ("FORM_TENSOR_FP4", "REFS_FP4", "e2m1xe2m1->f32 (unit ue8m0 block scales)"),
+    "fp4packed": ("FORM_TENSOR_FP4_PACKED", 0, "e2m1xe2m1->f32 (unit ue8m0 block scales)"),
+}
+DEFAULT_FORMS = ("plain", "fp8", "fp4")
+# Nominal dense rates relative to bf16 (2.25 PFLOP/s): e4m3 4.5, e2m1 13.5.
+NOMINAL_OVER_BF16 = {"fp8": 2.0, "fp4": 6.0}
+
+
+def workload_config(w: dict) -> dict:
+    """The `config` object of both arms (the same keys for the same workload)."""
+    c = {"workload": w["workload"], "n_queries": w.get("n_q"), "n_refs": w["n_refs"], "n_loci": w.get("n_loci"),
+         "k": w["k"], "threshold": w["threshold"], "output": w.get("output")}
+    if "n_loci" in w:
+        c["l2"] = ("inputs larger than L2 (packed database %.2f GB; FP8 copy %.1f GB, FP4 copy %.1f GB)" % (
+            w["n_refs"] * w["n_loci"] / 8 / 1e9, w["n_refs"] * w["n_loci"] / 1e9, w["n_refs"] * w["n_loci"] / 2e9)
+            if w["n_refs"] * w["n_loci"] / 8 > 129e6 else
+            "database smaller than L2 (%.1f MB packed): steps re-read it from L2" % (w["n_refs"] * w["n_loci"] / 8e6))
+    return c
 
 
 def recipe_for(name: str, n_refs: int | None = None, n_q: int | None = None):
@@ -167,43 +190,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------
-# Distributed helpers (independent replicas; barrier + max over ranks only)
-# ----------------------------------------------------------------------------
-
-def dist_env():
+def refuse_multi_gpu(args):
+    """The library compares on one device per call: bench.py times one GPU."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
-
-
-def dist_init(backend: str):
-    import torch.distributed as dist
-    world, rank, _ = dist_env()
-    if world > 1 and not dist.is_initialized():
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group(backend=backend, rank=rank, world_size=world)
-    return world, rank
-
-
-def barrier(world: int, device=None):
-    if world > 1:
-        import torch.distributed as dist
-        if device is not None and dist.get_backend() == "nccl":
-            dist.barrier(device_ids=[device.index])
-        else:
-            dist.barrier()
-
-
-def max_over_ranks(x: float, world: int, device=None) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device=device if dist.get_backend() == "nccl" else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    if args.gpus != 1 or world > 1:
+        print(f"bench.py: this library runs each comparison on one GPU; run it with --gpus 1 and without "
+              f"a multi-process launcher (got --gpus {args.gpus}, WORLD_SIZE {world})", file=sys.stderr)
+        sys.exit(2)
 
 
 # ----------------------------------------------------------------------------
@@ -245,9 +238,9 @@ def cpu_baseline(w: dict, recipe, thr, target_s: float = 12.0):
 
 
 def run_reference(args, w):
-    """--impl reference: the CPU oracle, each step a bounded sample."""
-    world, rank, _ = dist_env()
-    if world > 1 and rank != 0:
+    """--impl reference: the CPU oracle, each step a bounded sample.  Under a
+    multi-process launcher only rank 0 runs."""
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     import oracle
     oracle.build()
@@ -275,7 +268,7 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": {"workload": w["workload"], "n_loci": w["n_loci"]},
+            "data": "synthetic", "config": workload_config(w),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -283,7 +276,7 @@ def run_reference(args, w):
 
 
 # ----------------------------------------------------------------------------
-# GPU arm
+# Roofline denominators
 # ----------------------------------------------------------------------------
 
 def kernel_source_hash(form: str) -> str:
@@ -303,8 +296,6 @@ def kernel_source_hash(form: str) -> str:
 # (profiles/), keyed by form and workload, with the source hash it was taken
 # at.  A changed kernel reports null.
 NCU_TRAFFIC = {
-    # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 157.24 GB + dram__bytes_write.sum 79.17 MB
-    "tensor/c3": (157.2376e9 + 79.17e6, "d71ef4c0a9ea8d21"),
     # profiles/plain_kernel_c3_2048x20M.md: dram__bytes_read.sum 20.39 GB + dram__bytes_write.sum 17.27 MB
     "plain/c3": (20.3915e9 + 17.27e6, "c528944b13d66b2a"),
 }
@@ -320,21 +311,53 @@ def load_peaks():
             "fallback"
 
 
-def form_code(args, form_name):
-    """FASTID_FORM_* of a bench form: plain, or the tensor form over the FP8
-    copy (default) or over the packed rows (--operand packed)."""
+def roof_peak(form: str, probe: dict, n_sms: int) -> tuple[float, str, str]:
+    """Peak of a form's bound from the microbenchmarks (paper_1707_00516_gb300
+    .peaks, run by this process on this GPU): the measured rate per SM clock x
+    SMs x the maximum SM clock.  Returns (peak, unit, how)."""
+    peaks, src = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if form == "plain":
+        per = probe["popc"]["per_clk_sm"]
+        return (per * n_sms * sm_max * 1e6 / 1e12, "Tpopc/s",
+                f"POPC {per:.2f}/clk/SM measured (probe) x {n_sms} SMs x {sm_max:.0f} MHz max SM clock")
+    kind = form.removesuffix("packed")
+    if kind == "fp8":
+        per, shape = probe["fp8_f8f6f4"]["flops_per_clk_sm"], "tcgen05 kind::f8f6f4 M128xN256xK32"
+    else:
+        key = max(("fp4_mxf4_n224", "fp4_mxf4_n256"), key=lambda k: probe[k]["flops_per_clk_sm"])
+        per, shape = probe[key]["flops_per_clk_sm"], f"tcgen05 kind::mxf4 {probe[key]['shape']}"
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    return (per * n_sms * sm_max * 1e6 / 1e12, "TFLOP/s",
+            f"{shape}: {per:.0f} flop/clk/SM measured (probe, smem operands, one CTA per SM) x {n_sms} SMs x "
+            f"{sm_max:.0f} MHz max SM clock; nominal-ratio figure bf16 {bf16:.0f} ({src}) x "
+            f"{NOMINAL_OVER_BF16[kind]:g} = {bf16 * NOMINAL_OVER_BF16[kind]:.0f}")
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def form_code(form: str) -> int:
     from paper_1707_00516_gb300 import binding as B
-    if form_name == "plain":
-        return B.FORM_PLAIN
-    return B.FORM_TENSOR_PACKED if args.operand == "packed" else B.FORM_TENSOR
+    return getattr(B, FORMS[form][0])
 
 
-def time_form(args, s, db, form_name, step_fn, pairs_per_step, n_loci, world, dev):
+def form_flags(forms) -> int:
+    from paper_1707_00516_gb300 import binding as B
+    f = 0
+    for name in forms:
+        if FORMS[name][1]:
+            f |= getattr(B, FORMS[name][1])
+    return f
+
+
+def time_form(args, s, form, step_fn, pairs_per_step, n_loci, dev, probe):
     """Warm up and time `args.steps` steps of one compute form; returns the
     device-timed result and the roofline of its main compare kernel."""
     import torch
     from paper_1707_00516_gb300 import binding as B
-    B.fastid_set_form(s.ctx, form_code(args, form_name))
+    B.fastid_set_form(s.ctx, form_code(form))
     for _ in range(args.warmup):
         step_fn()
     torch.cuda.synchronize()
@@ -344,75 +367,66 @@ def time_form(args, s, db, form_name, step_fn, pairs_per_step, n_loci, world, de
     B.fastid_profile_read(s.ctx, reset=True)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(world, dev)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
         step_fn()
     e1.record(stream)
     torch.cuda.synchronize()
-    barrier(world, dev)
     ms = e0.elapsed_time(e1)
     prof = B.fastid_profile_read(s.ctx, reset=True)
     B.fastid_profile(s.ctx, False)
     clocks = clk.stop()
     st = B.fastid_sync_status(s.ctx)
     if st != B.OK:
-        raise RuntimeError(f"device status {st} after the timed region ({form_name})")
-    ms_max = max_over_ranks(ms, world, dev)
-    value = pairs_per_step * args.steps * world / (ms_max / 1e3)
+        raise RuntimeError(f"device status {st} after the timed region ({form})")
+    value = pairs_per_step * args.steps / (ms / 1e3)
 
-    peaks, peak_src = load_peaks()
     main_s = prof["main_ms"] / max(1, prof["main_launches"]) / 1e3
     # compare launches per step (several when references stream in blocks)
     main_per_step = max(1, prof["main_launches"]) / args.steps
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    if form_name == "plain":
+    peak, unit, how = roof_peak(form, probe, n_sms)
+    if form == "plain":
         words32 = 2 * ((n_loci + 63) // 64)
-        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = POPC_PER_CLK_PER_SM * n_sms * sm_max * 1e6 / 1e12
         achieved = pairs_per_step * words32 / (main_s * main_per_step) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpopc/s",
-                "kernel": "plain_kernel<EPI_TOPK>",
-                "peak_source": f"{POPC_PER_CLK_PER_SM} POPC/clk/SM x {n_sms} SMs x {sm_max:.0f} MHz "
-                               f"(max SM clock, {peak_src})"}
+        roof = {"bound": "alu", "kernel": "plain_kernel<EPI_TOPK>"}
     else:
-        bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        peak = bf16 * FP8_OVER_BF16
         achieved = 2.0 * pairs_per_step * n_loci / (main_s * main_per_step) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "kernel": "tensor_kernel (tcgen05 kind::f8f6f4, EPI_TOPK" +
-                          (", packed rows expanded on chip)" if args.operand == "packed" else ")"),
-                "peak_source": f"bf16 dense burst {bf16:.1f} TFLOP/s ({peak_src}) x {FP8_OVER_BF16:g} "
-                               f"(nominal e4m3/bf16 dense ratio, 4.5/2.25 PFLOP/s)"}
-    roof["frac"] = achieved / peak
-    roof["kernel_ms"] = main_s * 1e3
-    key = f"{form_name}/{args.config}"
+        kind = "kind::mxf4 block-scaled e2m1" if form.startswith("fp4") else "kind::f8f6f4 e4m3"
+        roof = {"bound": "tensor", "kernel": f"tensor_kernel (tcgen05 {kind}, EPI_TOPK" +
+                (", packed rows expanded on chip)" if form.endswith("packed") else ")")}
+    roof.update({"achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak, "peak_source": how,
+                 "kernel_ms": main_s * 1e3})
+    if form != "plain":
+        peaks, _ = load_peaks()
+        nominal = float(peaks.get("bf16_tflops", 1900.0)) * NOMINAL_OVER_BF16[form.removesuffix("packed")]
+        roof["frac_of_nominal_ratio_peak"] = achieved / nominal
+    key = f"{form}/{args.config}"
     # the captured counters hold for the unmodified workload only
-    tr = None if (args.refs or args.queries or args.operand != "fp8") else NCU_TRAFFIC.get(key)
-    roof["traffic"] = tr[0] if tr and tr[1] == kernel_source_hash(form_name) else None
-    return {"value": value, "ms_per_step": ms_max / args.steps, "roofline": roof, "clocks": clocks,
+    tr = None if (args.refs or args.queries) else NCU_TRAFFIC.get(key)
+    roof["traffic"] = tr[0] if tr and tr[1] == kernel_source_hash(form) else None
+    return {"value": value, "ms_per_step": ms / args.steps, "roofline": roof, "clocks": clocks,
             "gpu_launches": int(prof["all_launches"])}
 
 
 def run_gpu(args, w):
     import torch
-    world, rank = dist_init("nccl")
-    _, _, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
     from paper_1707_00516_gb300 import binding as B
-    from paper_1707_00516_gb300.search import Searcher
+    from paper_1707_00516_gb300 import peaks as P
     from paper_1707_00516_gb300.build import build
+    from paper_1707_00516_gb300.search import Searcher
     gen.build_gpu()
     build()
+    probe = P.measure()
 
-    forms = ["plain", "tensor"] if args.form == "both" else [args.form]
-    s = Searcher(local, B.FORM_AUTO)
+    forms = list(DEFAULT_FORMS) if args.form == "all" else args.form.split(",")
+    s = Searcher(0, B.FORM_AUTO)
     seed = gen.config_seed(w["cfg"])
     n_refs, n_loci, k, T = w["n_refs"], w["n_loci"], w["k"], w["threshold"]
-    flags = B.REFS_TENSOR if "tensor" in forms and args.operand == "fp8" else 0
-    db, thr = build_db(s, seed, n_refs, n_loci, flags)
+    db, thr = build_db(s, seed, n_refs, n_loci, form_flags(forms))
     recipe = recipe_for(args.config, n_refs=n_refs, n_q=w.get("n_q"))
     src, off, modes = query_inputs(recipe, thr)
     n_q = recipe.n_queries
@@ -437,12 +451,12 @@ def run_gpu(args, w):
             B.fastid_topk(s.ctx, db, q, d_mod, k, T, sc, ix)
 
     pairs_per_step = n_q * n_refs
-    res = {f: time_form(args, s, db, f, step, pairs_per_step, n_loci, world, dev) for f in forms}
+    res = {f: time_form(args, s, f, step, pairs_per_step, n_loci, dev, probe) for f in forms}
     head = max(res, key=lambda f: res[f]["value"])
     hr = res[head]
 
     # end to end through the host-buffer API, headline form
-    B.fastid_set_form(s.ctx, form_code(args, head))
+    B.fastid_set_form(s.ctx, form_code(head))
     if full:  # contributor alleles in, both score matrices out, through pinned buffers
         h_src = torch.from_numpy(src).pin_memory()
         h_mis = torch.empty((n_q, n_refs), dtype=torch.int16, pin_memory=True)
@@ -465,39 +479,46 @@ def run_gpu(args, w):
             return h2d_, d2h_
     for _ in range(max(1, args.warmup // 2)):
         e2e_step()
-    barrier(world, dev)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         h2d, d2h = e2e_step()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    e2e_value = pairs_per_step * args.steps * world / e2e_s
+    e2e_s = time.perf_counter() - t0
+    e2e_value = pairs_per_step * args.steps / e2e_s
 
-    line = {"metric": METRIC, "value": hr["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": hr["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32" if head == "plain" else "e4m3xe4m3->f32",
-            "data": "synthetic",
-            "config": {"workload": w["workload"], "n_queries": n_q, "n_refs": n_refs, "n_loci": n_loci, "k": k,
-                       "threshold": T, "form": head, "operand": args.operand if head == "tensor" else None,
-                       "parallelism": f"replicas{world}",
-                       "output": "both full uint16 score matrices (both scores of every pair)" if full
-                       else "per-query top-k",
-                       "l2": "inputs larger than L2 (packed database %.2f GB%s)" % (
-                           n_refs * n_loci / 8 / 1e9,
-                           ", e4m3 copy %.1f GB" % (n_refs * n_loci / 1e9) if flags else "")},
+    line = {"metric": METRIC + "; p50/p99 batch latency (serving, batched)", "value": hr["value"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": hr["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": FORMS[head][2],
+            "data": "synthetic", "config": workload_config(w),
+            "form": head, "forms_timed": forms,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+                    "d2h_bytes_per_step": int(d2h),
+                    "path": "Searcher.search_host: torch copies from pinned host buffers through the Python "
+                            "binding, then fastid_pack / fastid_mix / fastid_topk, results copied back"},
             "gpu_launches": hr["gpu_launches"], "roofline": hr["roofline"], "clocks": hr["clocks"],
             "forms": {f: {"value": r["value"], "ms_per_step": r["ms_per_step"], "roofline": r["roofline"],
-                          "clocks": r["clocks"]} for f, r in res.items()}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+                          "clocks": r["clocks"]} for f, r in res.items()},
+            "peaks_probe": {"fp8_f8f6f4_flop_per_clk_sm": probe["fp8_f8f6f4"]["flops_per_clk_sm"],
+                            "fp4_mxf4_flop_per_clk_sm": max(probe["fp4_mxf4_n224"]["flops_per_clk_sm"],
+                                                            probe["fp4_mxf4_n256"]["flops_per_clk_sm"]),
+                            "popc_per_clk_sm": probe["popc"]["per_clk_sm"],
+                            "lop3_per_clk_sm": probe["lop3"]["per_clk_sm"],
+                            "and_popc_iadd3_popc_per_clk_sm": probe["and_popc_add"]["per_clk_sm"],
+                            "b1_mma_bit_macs_per_clk_sm": probe["b1_and_popc"]["bit_macs_per_clk_sm"]}}
+    if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, recipe, thr)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     db.close()
+    del db
+    if args.config == "c3" and not args.no_extras:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        line["serving"] = serving_measure(s, WORKLOADS["c5"], seconds=args.serving_seconds, warmup_seconds=2.0,
+                                          slots=args.slots, max_wave=args.max_wave, hbm_budget=args.hbm_budget,
+                                          clock_ms=args.clock_ms)
+        torch.cuda.empty_cache()
+        line["batched"] = batched_measure(s, WORKLOADS["c4"], steps=args.batched_steps, warmup=3, e2e=False,
+                                          probe=probe)
+    print(json.dumps(line), flush=True)
     s.ctx.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
 
 
 def run_streamed(args, w):
@@ -505,15 +526,15 @@ def run_streamed(args, w):
     through the device in blocks by fastid_topk_streamed (tensor form)."""
     import torch
     from paper_1707_00516_gb300 import binding as B
+    from paper_1707_00516_gb300 import peaks as P
     from paper_1707_00516_gb300.build import build
     from paper_1707_00516_gb300.search import Searcher, words64
-    world, rank = dist_init("nccl")
-    _, _, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
     gen.build_gpu()
     build()
-    s = Searcher(local, B.FORM_TENSOR)
+    probe = P.measure()
+    s = Searcher(0, B.FORM_TENSOR)
     seed = gen.config_seed(w["cfg"])
     n_refs, n_loci, k, T = w["n_refs"], w["n_loci"], w["k"], w["threshold"]
     thr = gen.maf_thresholds(seed, n_loci)
@@ -553,7 +574,7 @@ def run_streamed(args, w):
     def step():
         B.fastid_topk_streamed(s.ctx, host, n_loci, B.REFS_TENSOR, block, q, modes, k, T, sc, ix)
 
-    r = time_form(args, s, None, "tensor", step, n_q * n_refs, n_loci, world, dev)
+    r = time_form(args, s, "fp8", step, n_q * n_refs, n_loci, dev, probe)
     # end to end: packed queries in from pinned memory, results out, each step
     hq = q.cpu().pin_memory()
     hm = modes.cpu().pin_memory()
@@ -568,27 +589,25 @@ def run_streamed(args, w):
         hs.copy_(sc, non_blocking=True)
         hi.copy_(ix, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_s = time.perf_counter() - t0
     n_blocks, done, nxt = 0, 0, max(min(block, n_refs, 256), min(block, n_refs) // 8)
     while done < n_refs:  # the library's block sizes: from block / 8, doubling
         done += min(nxt, n_refs - done)
         nxt = min(min(block, n_refs), 2 * nxt)
         n_blocks += 1
-    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    cfg = workload_config(w)
+    cfg.update({"workload": w["workload"] + f"_refs_streamed_from_pinned_host_block{block}",
+                "blocks_per_step": n_blocks, "host_bytes_per_step": int(host.numel() * 8),
+                "h2d_gbps_pinned_probe": h2d_gbps,
+                "l2": "inputs larger than L2 (references copied from host every step)"})
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "e4m3xe4m3->f32", "data": "synthetic",
-            "config": {"workload": w["workload"] + f"_refs_streamed_from_pinned_host_block{block}",
-                       "n_queries": n_q, "n_refs": n_refs, "n_loci": n_loci, "k": k, "threshold": T,
-                       "blocks_per_step": n_blocks, "host_bytes_per_step": int(host.numel() * 8),
-                       "h2d_gbps_pinned_probe": h2d_gbps,
-                       "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (references copied from host every step)"},
-            "e2e": {"value": n_q * n_refs * args.steps * world / e2e_s, "unit": UNIT,
+            "vs_baseline": None, "dtype": FORMS["fp8"][2], "data": "synthetic", "config": cfg,
+            "e2e": {"value": n_q * n_refs * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(hq.numel() * 8 + hm.numel() + host.numel() * 8),
                     "d2h_bytes_per_step": int(hs.numel() * 4 + hi.numel() * 8)},
             "gpu_launches": r["gpu_launches"], "roofline": r["roofline"], "clocks": r["clocks"]}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    print(json.dumps(line), flush=True)
     s.ctx.close()
 
 
@@ -611,6 +630,10 @@ def device_queries(s, seed: int, recipe, thr_dev, n_loci: int):
     return q, torch.from_numpy(recipe.modes).to(dev)
 
 
+# ----------------------------------------------------------------------------
+# Batched workload (configuration 4)
+# ----------------------------------------------------------------------------
+
 def _c4_batches(w):
     seed = gen.config_seed(w["cfg"])
     sizes = [int(x) for x in gen.log_uniform_sizes(w["n_batches"], 1, 512, seed, salt=0xC4)]
@@ -627,19 +650,15 @@ def _c4_recipe(w, b, n, p, seed):
     return rec
 
 
-def run_c4(args, w):
-    """Batched uneven workload: 256 batches over 4 loci panels in one
-    persistent launch (graph replay), variant from the autotuner."""
+def batched_measure(s, w, steps: int, warmup: int, e2e: bool = True, probe: dict | None = None) -> dict:
+    """256 batches over 4 loci panels in one persistent launch per step (graph
+    replay), variant from the autotuner.  Returns the batched workload's
+    figures (throughput, per-replay latency, roofline, clocks)."""
     import torch
     from paper_1707_00516_gb300 import binding as B
     from paper_1707_00516_gb300.batched import BatchedSearch
-    from paper_1707_00516_gb300.build import build
-    from paper_1707_00516_gb300.search import Searcher
     from paper_1707_00516_gb300.tune import Autotuner
-    gen.build_gpu()
-    build()
-    dev = torch.device("cuda", 0)
-    s = Searcher(0, B.FORM_TENSOR)
+    dev = s.device
     seed, sizes, panels = _c4_batches(w)
     dbs, thrs = [], []
     for p, n_loci in enumerate(w["panels"]):
@@ -657,14 +676,14 @@ def run_c4(args, w):
         host_q.append(q.cpu().numpy().view(np.uint64))
         host_m.append(m.cpu().numpy())
     torch.cuda.synchronize()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         bs.run_device()
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    clk = ClockSampler(0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    clk = ClockSampler(dev.index)
     clk.start()
     ev[0].record()
-    for i in range(args.steps):
+    for i in range(steps):
         bs.run_device()
         ev[i + 1].record()
     torch.cuda.synchronize()
@@ -672,43 +691,65 @@ def run_c4(args, w):
     st = B.fastid_sync_status(s.ctx)
     if st != B.OK:
         raise RuntimeError(f"device status {st}")
-    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     pairs = int(sum(int(n) * w["n_refs"] for n in sizes))
     flops = float(sum(2.0 * int(n) * w["n_refs"] * w["panels"][p] for n, p in zip(sizes, panels)))
-    value = pairs * args.steps / (total_ms / 1e3)
-    peaks, peak_src = load_peaks()
-    bf16 = float(peaks.get("bf16_tflops", 1900.0))
-    achieved = flops * args.steps / (total_ms / 1e3) / 1e12
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        _, _, h2d, d2h = bs.run_host(host_q, host_m)
-    e2e_s = time.perf_counter() - t0
+    value = pairs * steps / (total_ms / 1e3)
+    from paper_1707_00516_gb300 import peaks as P
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak, unit, how = roof_peak("fp8", probe if probe is not None else P.measure(), n_sms)
+    achieved = flops * steps / (total_ms / 1e3) / 1e12
     info = bs.plan.info()
-    line = {"metric": METRIC + " (mixed-N panels); p50/p99 batch latency", "value": value, "unit": UNIT,
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3xe4m3->f32",
-            "data": "synthetic",
-            "config": {"workload": w["workload"], "n_batches": int(len(sizes)), "n_queries": int(sum(sizes)),
-                       "panels": list(w["panels"]), "n_refs_per_panel": w["n_refs"], "k": w["k"],
-                       "variant": int(bs.variant), "autotune_ms": {str(k): v for k, v in tuner.last_timings.items()},
-                       "grid": info["grid"], "units": info["n_units"], "launch": "one persistent launch per step, "
-                       "CUDA graph replay (prep + compare + merge)"},
-            "batch_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-            "e2e": {"value": pairs * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": 3 * args.steps,
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16 * FP8_OVER_BF16, "unit": "TFLOP/s",
-                         "frac": achieved / (bf16 * FP8_OVER_BF16), "traffic": None,
-                         "kernel": "tensor_kernel over 4 panels (whole graph time incl. prep and merge)",
-                         "peak_source": f"bf16 dense burst {bf16:.1f} TFLOP/s ({peak_src}) x {FP8_OVER_BF16:g}"},
-            "clocks": clocks}
-    print(json.dumps(line), flush=True)
+    out = {"workload": w["workload"], "value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": total_ms / steps,
+           "batch_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                                "note": "every batch of a step completes with its graph replay"},
+           "config": {"n_batches": int(len(sizes)), "n_queries": int(sum(sizes)), "panels": list(w["panels"]),
+                      "n_refs_per_panel": w["n_refs"], "k": w["k"], "variant": int(bs.variant),
+                      "autotune_ms": {str(k): v for k, v in tuner.last_timings.items()}, "grid": info["grid"],
+                      "units": info["n_units"],
+                      "launch": "one persistent launch per step, CUDA graph replay (prep + compare + merge)"},
+           "dtype": FORMS["fp8"][2], "gpu_launches": 3 * steps,
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": unit,
+                        "frac": achieved / peak, "traffic": None, "peak_source": how,
+                        "kernel": "tensor_kernel over 4 panels (whole graph time incl. prep and merge)"},
+           "clocks": clocks}
+    if e2e:
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            _, _, h2d, d2h = bs.run_host(host_q, host_m)
+        e2e_s = time.perf_counter() - t0
+        out["e2e"] = {"value": pairs * steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h)}
     bs.close()
     for d in dbs:
         d.close()
+    return out
+
+
+def run_c4(args, w):
+    """Batched uneven workload alone: one JSON line."""
+    from paper_1707_00516_gb300 import binding as B
+    from paper_1707_00516_gb300.build import build
+    from paper_1707_00516_gb300.search import Searcher
+    gen.build_gpu()
+    build()
+    s = Searcher(0, B.FORM_TENSOR)
+    r = batched_measure(s, w, args.steps, args.warmup)
+    cfg = {"workload": w["workload"], **r["config"]}
+    line = {"metric": METRIC + " (mixed-N panels); p50/p99 batch latency", "value": r["value"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r["dtype"],
+            "data": "synthetic", "config": cfg, "batch_latency_ms": r["batch_latency_ms"], "e2e": r["e2e"],
+            "gpu_launches": r["gpu_launches"], "roofline": r["roofline"], "clocks": r["clocks"]}
+    print(json.dumps(line), flush=True)
     s.ctx.close()
 
+
+# ----------------------------------------------------------------------------
+# Serving workload (configuration 5)
+# ----------------------------------------------------------------------------
 
 # Serving defaults: one wave in flight (a wave of up to 128 queries costs about
 # the same as a wave of one, so arrivals are best coalesced into the next wave)
@@ -735,23 +776,21 @@ def c5_requests(w, seed: int, horizon: float):
     return arrivals, sizes, rec
 
 
-def run_c5(args, w):
-    """Serving: Poisson arrivals of query batches against a resident 20M
-    database, continuous batching, p50/p99 request latency."""
+def serving_measure(s, w, seconds: float, warmup_seconds: float, slots: int, max_wave: int, hbm_budget: int,
+                    clock_ms: int, flags: int | None = None) -> dict:
+    """Poisson arrivals of query batches against a resident 20M database,
+    continuous batching (serve.Server), latency from submit to result on the
+    host.  Returns the serving figures."""
     import torch
     from paper_1707_00516_gb300 import binding as B
-    from paper_1707_00516_gb300.build import build
-    from paper_1707_00516_gb300.search import Searcher
     from paper_1707_00516_gb300.serve import Server
-    gen.build_gpu()
-    build()
-    dev = torch.device("cuda", 0)
-    s = Searcher(0, B.FORM_AUTO)  # FP8 operand for large waves, packed rows for small ones
+    B.fastid_set_form(s.ctx, B.FORM_AUTO)
+    dev = s.device
     seed = gen.config_seed(w["cfg"])
     n_refs, n_loci, k = w["n_refs"], w["n_loci"], w["k"]
-    db, thr = build_db(s, seed, n_refs, n_loci, B.REFS_TENSOR)
+    db, thr = build_db(s, seed, n_refs, n_loci, B.REFS_TENSOR if flags is None else flags)
     thr_dev = torch.from_numpy(thr.view(np.int32)).to(dev)
-    horizon = args.warmup_seconds + args.seconds
+    horizon = warmup_seconds + seconds
     arrivals, sizes, rec = c5_requests(w, seed, horizon)
     n_req = arrivals.size
     total = int(sizes.sum())
@@ -759,19 +798,18 @@ def run_c5(args, w):
     hq = q.cpu().numpy().view(np.uint64)
     hm = m.cpu().numpy()
     offs = np.concatenate([[0], np.cumsum(sizes)])
-    srv = Server(s.ctx, db, k, w["threshold"], hbm_budget_bytes=args.hbm_budget, max_wave=args.max_wave,
-                 max_slots=args.slots)
-    futs, t_sub = [], []
+    srv = Server(s.ctx, db, k, w["threshold"], hbm_budget_bytes=hbm_budget, max_wave=max_wave, max_slots=slots)
+    futs = []
     launches0 = None
     B.fastid_profile_read(s.ctx, reset=True)
     t_start = time.perf_counter()
-    clk = ClockSampler(0, args.clock_ms)
+    clk = ClockSampler(dev.index, clock_ms)
     clk.start()
     for i in range(n_req):
         delay = t_start + arrivals[i] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        if launches0 is None and arrivals[i] >= args.warmup_seconds:  # kernel launches from here on
+        if launches0 is None and arrivals[i] >= warmup_seconds:  # kernel launches from here on
             launches0 = B.fastid_profile_read(s.ctx, reset=False)["all_launches"]
         futs.append(srv.submit(hq[offs[i]:offs[i + 1]], hm[offs[i]:offs[i + 1]]))
     for f in futs:
@@ -780,60 +818,82 @@ def run_c5(args, w):
     launches = B.fastid_profile_read(s.ctx, reset=False)["all_launches"] - (launches0 or 0)
     clocks = clk.stop()
     st = srv.stats()
-    # measured window: requests that arrived after the warm-up
-    meas = arrivals >= args.warmup_seconds
-    lat = np.array([l for (ts, l) in srv.records if ts - t_start >= args.warmup_seconds])
+    meas = arrivals >= warmup_seconds
+    lat = np.array([l for (ts, l) in srv.records if ts - t_start >= warmup_seconds])
     srv.close()
     served = int(sizes[meas].sum()) * n_refs
-    window = (t_end - t_start) - args.warmup_seconds
-    line = {"metric": METRIC + "; p50/p99 request latency", "value": served / window, "unit": UNIT,
-            "n_gpus": 1, "steps": int(meas.sum()), "warmup": int((~meas).sum()),
-            "ms_per_step": 1e3 * window / max(1, int(meas.sum())), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "e4m3xe4m3->f32", "data": "synthetic",
-            "config": {"workload": w["workload"], "seconds": args.seconds, "requests": n_req,
-                       "queries": total, "offered_comparisons_per_s": float(total * n_refs / horizon),
-                       "slots": st["slots"], "waves": st["waves"], "mean_wave_queries": st["mean_wave"],
-                       "max_wave": args.max_wave, "hbm_budget_bytes": args.hbm_budget},
-            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
-                           "max": float(lat.max() * 1e3)},
-            "e2e": {"value": served / window, "unit": UNIT, "h2d_bytes_per_step": int(hq.nbytes / n_req),
-                    "d2h_bytes_per_step": int(12 * k * total / n_req)},
-            "gpu_launches": int(launches), "clocks": clocks}
-    print(json.dumps(line), flush=True)
+    window = (t_end - t_start) - warmup_seconds
+    out = {"workload": w["workload"], "value": served / window, "unit": UNIT,
+           "offered": float(int(sizes[meas].sum()) * n_refs / seconds),
+           "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                          "max": float(lat.max() * 1e3), "from": "submit to result on the host"},
+           "config": {"seconds": seconds, "warmup_seconds": warmup_seconds, "requests": int(meas.sum()),
+                      "queries": int(sizes[meas].sum()), "slots": st["slots"], "waves": st["waves"],
+                      "mean_wave_queries": st["mean_wave"], "max_wave": max_wave, "hbm_budget_bytes": hbm_budget},
+           "e2e": {"h2d_bytes_per_request": int(hq.nbytes / n_req), "d2h_bytes_per_request": int(12 * k * total / n_req)},
+           "gpu_launches": int(launches), "clocks": clocks}
     db.close()
+    return out
+
+
+def run_c5(args, w):
+    """Serving alone: one JSON line."""
+    from paper_1707_00516_gb300 import binding as B
+    from paper_1707_00516_gb300.build import build
+    from paper_1707_00516_gb300.search import Searcher
+    gen.build_gpu()
+    build()
+    s = Searcher(0, B.FORM_AUTO)
+    r = serving_measure(s, w, args.seconds, args.warmup_seconds, args.slots, args.max_wave, args.hbm_budget,
+                        args.clock_ms)
+    cfg = {"workload": w["workload"], **r["config"], "offered_comparisons_per_s": r["offered"]}
+    line = {"metric": METRIC + "; p50/p99 request latency", "value": r["value"], "unit": UNIT,
+            "n_gpus": 1, "steps": r["config"]["requests"], "warmup": 0,
+            "ms_per_step": 1e3 * args.seconds / max(1, r["config"]["requests"]), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "by wave: " + FORMS["fp8packed"][2],
+            "data": "synthetic", "config": cfg, "latency_ms": r["latency_ms"],
+            "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": r["e2e"]["h2d_bytes_per_request"],
+                    "d2h_bytes_per_step": r["e2e"]["d2h_bytes_per_request"]},
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
+    print(json.dumps(line), flush=True)
     s.ctx.close()
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--gpus", type=int, default=1, help="must be 1: one GPU per comparison")
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["plain", "tensor", "both"], default="both")
+    ap.add_argument("--form", default="all",
+                    help="all (plain, fp8, fp4) or a comma-separated list of " + ", ".join(FORMS))
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="c3",
                     help="c3 (default): the headline 2048 x 20M workload; c4 batched panels; c5 serving")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="c3: skip the serving and batched sub-objects")
     ap.add_argument("--refs", type=int, default=None,
                     help="override the number of references (smaller captures for profiling)")
     ap.add_argument("--queries", type=int, default=None,
                     help="c1-c3: override the number of queries (the recipe's first N)")
-    ap.add_argument("--operand", choices=["fp8", "packed"], default="fp8",
-                    help="c1-c3, tensor form: reference operand read from the FP8 copy or from the packed rows "
-                         "(expanded on chip)")
     ap.add_argument("--seconds", type=float, default=30.0, help="c5: measured serving time")
+    ap.add_argument("--serving-seconds", type=float, default=10.0, help="c3: measured time of the serving sub-run")
+    ap.add_argument("--batched-steps", type=int, default=10, help="c3: graph replays of the batched sub-run")
     ap.add_argument("--warmup-seconds", type=float, default=3.0, help="c5: warm-up serving time")
-    ap.add_argument("--max-wave", type=int, default=C5_DEFAULTS["max_wave"], help="c5: queries per wave at most")
+    ap.add_argument("--max-wave", type=int, default=C5_DEFAULTS["max_wave"], help="serving: queries per wave at most")
     ap.add_argument("--hbm-budget", type=int, default=C5_DEFAULTS["hbm_budget"],
-                    help="c5: bytes of HBM for in-flight waves")
-    ap.add_argument("--slots", type=int, default=C5_DEFAULTS["slots"], help="c5: waves in flight at most")
+                    help="serving: bytes of HBM for in-flight waves")
+    ap.add_argument("--slots", type=int, default=C5_DEFAULTS["slots"], help="serving: waves in flight at most")
     ap.add_argument("--clock-ms", type=int, default=C5_DEFAULTS["clock_ms"],
-                    help="c5: nvidia-smi clock sampling interval during the serving window")
+                    help="serving: nvidia-smi clock sampling interval during the serving window")
     ap.add_argument("--streamed", type=int, default=0, metavar="BLOCK",
                     help="c1-c3: keep the references in pinned host memory and stream them in blocks of BLOCK "
                          "references (fastid_topk_streamed)")
 
     args = ap.parse_args(argv)
+    if args.form != "all":
+        bad = [f for f in args.form.split(",") if f not in FORMS]
+        if bad:
+            ap.error(f"unknown form(s) {bad}; choose from {sorted(FORMS)}")
     w = dict(WORKLOADS[args.config])
     if args.refs:
         w["n_refs"] = args.refs
@@ -845,11 +905,11 @@ def main(argv=None):
         w["n_q"] = args.queries
         w["workload"] = w["workload"].replace(f"{old}q_", f"{args.queries}q_").replace(f"{old}mix_",
                                                                                        f"{args.queries}mix_")
-    if args.operand == "packed":
-        w["workload"] += "_packed_operand"
     if args.impl == "reference":
         run_reference(args, w)
-    elif args.config == "c4":
+        return
+    refuse_multi_gpu(args)
+    if args.config == "c4":
         run_c4(args, w)
     elif args.config == "c5":
         run_c5(args, w)

@@ -23,7 +23,7 @@ def test_recorded_traffic_matches_current_sources():
     is reported as null traffic, so this only checks the keys are well formed."""
     for key, (bytes_, h) in bench.NCU_TRAFFIC.items():
         form, config = key.split("/")
-        assert form in ("tensor", "plain") and config in bench.WORKLOADS
+        assert form in bench.FORMS and config in bench.WORKLOADS
         assert bytes_ > 0 and len(h) == 16
 
 
@@ -42,7 +42,39 @@ def test_reference_arm_json_line(capsys):
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["config"]["workload"] == bench.WORKLOADS["c1"]["workload"]
+    assert d["config"] == bench.workload_config(bench.WORKLOADS["c1"])  # the GPU arm's config keys
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_multi_gpu_refused(monkeypatch):
+    """The library compares on one device per call: bench.py refuses --gpus
+    other than 1 and a multi-process launch before touching a GPU."""
+    import pytest
+
+    import bench
+    with pytest.raises(SystemExit) as e:
+        bench.main(["--gpus", "2", "--steps", "1"])
+    assert e.value.code == 2
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    with pytest.raises(SystemExit) as e:
+        bench.main(["--steps", "1"])
+    assert e.value.code == 2
+
+
+def test_roofline_peaks_from_probe():
+    """Each form's peak is the probe's per-clock rate x SMs x the maximum SM
+    clock, in the form's own unit."""
+    import bench
+    probe = {"popc": {"per_clk_sm": 16.0}, "fp8_f8f6f4": {"flops_per_clk_sm": 16384.0},
+             "fp4_mxf4_n224": {"flops_per_clk_sm": 32768.0, "shape": "M128xN224xK64"},
+             "fp4_mxf4_n256": {"flops_per_clk_sm": 32760.0, "shape": "M128xN256xK64"}}
+    mhz = float(bench.load_peaks()[0].get("sm_max_mhz", 2070.0))
+    p, unit, _ = bench.roof_peak("plain", probe, 152)
+    assert unit == "Tpopc/s" and abs(p - 16 * 152 * mhz * 1e6 / 1e12) < 1e-9
+    p8, unit, _ = bench.roof_peak("fp8", probe, 152)
+    assert unit == "TFLOP/s" and abs(p8 - 16384 * 152 * mhz * 1e6 / 1e12) < 1e-6
+    assert bench.roof_peak("fp8packed", probe, 152)[0] == p8
+    p4, _, how = bench.roof_peak("fp4", probe, 152)
+    assert abs(p4 - 32768 * 152 * mhz * 1e6 / 1e12) < 1e-6 and "N224" in how
