@@ -513,7 +513,7 @@ def run_gpu(args, w):
         torch.cuda.empty_cache()
         line["serving"] = serving_measure(s, WORKLOADS["c5"], seconds=args.serving_seconds, warmup_seconds=2.0,
                                           slots=args.slots, max_wave=args.max_wave, hbm_budget=args.hbm_budget,
-                                          clock_ms=args.clock_ms)
+                                          clock_ms=args.clock_ms, server=args.server, parts=args.parts)
         torch.cuda.empty_cache()
         line["batched"] = batched_measure(s, WORKLOADS["c4"], steps=args.batched_steps, warmup=3, e2e=False,
                                           probe=probe)
@@ -757,7 +757,7 @@ def run_c4(args, w):
 # sampled once a second: the serving window is latency-measured, and with the
 # 200 ms sampling of the device-timed configs some runs showed a 94-124 ms
 # stall (p99 23-25 ms) that runs sampled once a second did not (p99 15.7 ms).
-C5_DEFAULTS = dict(slots=1, max_wave=256, hbm_budget=4 << 30, clock_ms=1000)
+C5_DEFAULTS = dict(server="sweep", parts=4, slots=1, max_wave=256, hbm_budget=4 << 30, clock_ms=1000)
 
 
 def c5_requests(w, seed: int, horizon: float):
@@ -776,19 +776,29 @@ def c5_requests(w, seed: int, horizon: float):
     return arrivals, sizes, rec
 
 
+def make_server(kind: str, ctx, db, k: int, threshold: int, parts: int, slots: int, max_wave: int,
+                hbm_budget: int):
+    """The serving layer under test: "sweep" (waves join a running pass over
+    the database's parts and share its launches) or "waves" (each wave is one
+    fastid_topk on a slot)."""
+    from paper_1707_00516_gb300.serve import Server, SweepServer
+    if kind == "sweep":
+        return SweepServer(ctx, db, k, threshold, parts=parts, capacity=max(4 * max_wave, 1024), max_wave=max_wave)
+    return Server(ctx, db, k, threshold, hbm_budget_bytes=hbm_budget, max_wave=max_wave, max_slots=slots)
+
+
 def serving_measure(s, w, seconds: float, warmup_seconds: float, slots: int, max_wave: int, hbm_budget: int,
-                    clock_ms: int, flags: int | None = None) -> dict:
+                    clock_ms: int, flags: int | None = None, server: str = "sweep", parts: int = 4) -> dict:
     """Poisson arrivals of query batches against a resident 20M database,
-    continuous batching (serve.Server), latency from submit to result on the
-    host.  Returns the serving figures."""
+    continuous batching (serve.SweepServer or serve.Server), latency from
+    submit to result on the host.  Returns the serving figures."""
     import torch
     from paper_1707_00516_gb300 import binding as B
-    from paper_1707_00516_gb300.serve import Server
     B.fastid_set_form(s.ctx, B.FORM_AUTO)
     dev = s.device
     seed = gen.config_seed(w["cfg"])
     n_refs, n_loci, k = w["n_refs"], w["n_loci"], w["k"]
-    db, thr = build_db(s, seed, n_refs, n_loci, B.REFS_TENSOR if flags is None else flags)
+    db, thr = build_db(s, seed, n_refs, n_loci, B.REFS_FP4 if flags is None else flags)
     thr_dev = torch.from_numpy(thr.view(np.int32)).to(dev)
     horizon = warmup_seconds + seconds
     arrivals, sizes, rec = c5_requests(w, seed, horizon)
@@ -798,7 +808,7 @@ def serving_measure(s, w, seconds: float, warmup_seconds: float, slots: int, max
     hq = q.cpu().numpy().view(np.uint64)
     hm = m.cpu().numpy()
     offs = np.concatenate([[0], np.cumsum(sizes)])
-    srv = Server(s.ctx, db, k, w["threshold"], hbm_budget_bytes=hbm_budget, max_wave=max_wave, max_slots=slots)
+    srv = make_server(server, s.ctx, db, k, w["threshold"], parts, slots, max_wave, hbm_budget)
     futs = []
     launches0 = None
     B.fastid_profile_read(s.ctx, reset=True)
@@ -828,7 +838,8 @@ def serving_measure(s, w, seconds: float, warmup_seconds: float, slots: int, max
            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                           "max": float(lat.max() * 1e3), "from": "submit to result on the host"},
            "config": {"seconds": seconds, "warmup_seconds": warmup_seconds, "requests": int(meas.sum()),
-                      "queries": int(sizes[meas].sum()), "slots": st["slots"], "waves": st["waves"],
+                      "queries": int(sizes[meas].sum()), "server": server, "slots": st["slots"],
+                      "steps": st.get("steps"), "waves": st["waves"],
                       "mean_wave_queries": st["mean_wave"], "max_wave": max_wave, "hbm_budget_bytes": hbm_budget},
            "e2e": {"h2d_bytes_per_request": int(hq.nbytes / n_req), "d2h_bytes_per_request": int(12 * k * total / n_req)},
            "gpu_launches": int(launches), "clocks": clocks}
@@ -845,7 +856,7 @@ def run_c5(args, w):
     build()
     s = Searcher(0, B.FORM_AUTO)
     r = serving_measure(s, w, args.seconds, args.warmup_seconds, args.slots, args.max_wave, args.hbm_budget,
-                        args.clock_ms)
+                        args.clock_ms, server=args.server, parts=args.parts)
     cfg = {"workload": w["workload"], **r["config"], "offered_comparisons_per_s": r["offered"]}
     line = {"metric": METRIC + "; p50/p99 request latency", "value": r["value"], "unit": UNIT,
             "n_gpus": 1, "steps": r["config"]["requests"], "warmup": 0,
@@ -882,7 +893,11 @@ def main(argv=None):
     ap.add_argument("--max-wave", type=int, default=C5_DEFAULTS["max_wave"], help="serving: queries per wave at most")
     ap.add_argument("--hbm-budget", type=int, default=C5_DEFAULTS["hbm_budget"],
                     help="serving: bytes of HBM for in-flight waves")
-    ap.add_argument("--slots", type=int, default=C5_DEFAULTS["slots"], help="serving: waves in flight at most")
+    ap.add_argument("--server", choices=["sweep", "waves"], default=C5_DEFAULTS["server"],
+                    help="serving: waves join a running pass over the database's parts (sweep) or run one "
+                         "fastid_topk each on a slot (waves)")
+    ap.add_argument("--parts", type=int, default=C5_DEFAULTS["parts"], help="serving (sweep): parts of the database")
+    ap.add_argument("--slots", type=int, default=C5_DEFAULTS["slots"], help="serving (waves): waves in flight at most")
     ap.add_argument("--clock-ms", type=int, default=C5_DEFAULTS["clock_ms"],
                     help="serving: nvidia-smi clock sampling interval during the serving window")
     ap.add_argument("--streamed", type=int, default=0, metavar="BLOCK",

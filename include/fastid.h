@@ -85,9 +85,10 @@ enum {
     FASTID_FORM_TENSOR_FP4_PACKED = 5 /* the FP4 tensor form with the reference operand always
                                       read as packed bits and expanded on chip            */
 };
-/* FASTID_FORM_AUTO: the tensor form; its reference operand is the FP8 copy when
- * the database has one and the call has more than 256 queries (two query
- * tiles), or more than 128 for fastid_topk with k > 16; else the packed rows. */
+/* FASTID_FORM_AUTO: the FP4 tensor form; its reference operand is the FP4 copy
+ * when the database has one and the call has more than 128 queries (one query
+ * tile), else the packed rows expanded on chip.  (Measured on GB300, the FP4
+ * packed rows are never slower than either FP8 operand.) */
 
 /* fastid_load_refs flags */
 enum {
@@ -120,7 +121,9 @@ const char *fastid_last_error(const fastid_ctx *ctx);
 /* Choose the compute form for later comparison calls (FASTID_FORM_*). */
 fastid_status fastid_set_form(fastid_ctx *ctx, int32_t form);
 
-/* Synchronise `stream`, read and clear the context's device status word.
+/* Synchronise `stream`, read and clear the context's device status word (one
+ * atomic read-and-clear on the device, ordered on `stream`, so a condition
+ * recorded meanwhile by a kernel on another stream is kept for the next call).
  * Returns FASTID_OK, FASTID_EOVERFLOW, FASTID_ETIMEOUT or FASTID_EDEVICE
  * (the most severe condition recorded since the last call), or ECUDA. */
 fastid_status fastid_sync_status(fastid_ctx *ctx, fastid_stream stream);
@@ -200,8 +203,25 @@ fastid_status fastid_save_refs(fastid_ctx *ctx, const fastid_refdb *db, const ch
 fastid_status fastid_load_refs_file(fastid_ctx *ctx, const char *path, uint32_t flags,
                                     fastid_refdb **out, fastid_stream stream);
 
-/* Synchronise the device and free a database.  NULL is accepted. */
+/* Synchronise the device and free a database.  NULL is accepted.  For a view
+ * (fastid_refs_view) only the handle is freed. */
 fastid_status fastid_free_refs(fastid_ctx *ctx, fastid_refdb *db);
+
+/*
+ * A database handle over rows [r_begin, r_begin + n_refs) of db, sharing db's
+ * memory (nothing is copied or allocated on the device): every comparison
+ * call on the view sees those references as indices 0 .. n_refs - 1, with
+ * the operand copies db has.  Together with fastid_topk_fold this splits one
+ * pass over a database into parts that may run in any order (the paper's
+ * blocked comparison of known profiles, Sec. III-C, over resident blocks);
+ * the serving layer uses it to let query batches join a running pass at any
+ * part boundary.  r_begin must be a multiple of FASTID_VIEW_ALIGN.  Free the
+ * view (fastid_free_refs) before db; db's rows must not change meanwhile.
+ * Errors: EINVAL (range, alignment, NULL), ENOMEM (host), ECUDA.
+ */
+#define FASTID_VIEW_ALIGN 256
+fastid_status fastid_refs_view(fastid_ctx *ctx, const fastid_refdb *db, int64_t r_begin, int64_t n_refs,
+                               fastid_refdb **out);
 
 /* Shape and footprint of a database; any output pointer may be NULL. */
 fastid_status fastid_refs_info(const fastid_refdb *db, int64_t *n_refs, int32_t *n_loci,
@@ -307,6 +327,24 @@ fastid_status fastid_compare_streamed(fastid_ctx *ctx, const uint64_t *refs_host
                                       int64_t capacity, int64_t *hit_q_dev, int64_t *hit_r_dev,
                                       uint32_t *hit_score_dev, int64_t *hit_count_dev,
                                       fastid_stream stream);
+
+/*
+ * Merge top-k lists of part of the references into running lists: for each
+ * query q, run[q] becomes the k smallest (score, reference index) pairs of
+ * run[q] and blk[q], blk's indices taken + ref_offset, ascending by score then
+ * index; empty slots are (0xFFFFFFFF, -1) on input and output.  With views
+ * over disjoint row ranges (fastid_refs_view) this reassembles fastid_topk
+ * over the union from its parts, in any order, exactly.
+ *  run_scores_dev  uint32 [n_q][k], run_idx_dev  int64 [n_q][k]  (in/out; an
+ *                  all-empty list is every byte 0xFF)
+ *  blk_scores_dev  uint32 [n_q][k], blk_idx_dev  int64 [n_q][k]  (as written
+ *                  by fastid_topk with the same k)
+ *  ref_offset      0 .. 2^31 - 1;  k 1 .. FASTID_MAX_K.
+ * Errors: EINVAL, ECUDA.
+ */
+fastid_status fastid_topk_fold(fastid_ctx *ctx, uint32_t *run_scores_dev, int64_t *run_idx_dev,
+                               const uint32_t *blk_scores_dev, const int64_t *blk_idx_dev, int64_t ref_offset,
+                               int64_t n_q, int32_t k, fastid_stream stream);
 
 /* ------------------------------------------------------------- diagnostics */
 /*

@@ -27,6 +27,7 @@ MAX_K = 32
 MAX_LOCI = 65536
 NO_THRESHOLD = 0xFFFFFFFF
 NOALLOC_SCRATCH_BYTES = 16 << 20
+VIEW_ALIGN = 256
 VARIANT_AUTO, VARIANT_TENSOR_N256, VARIANT_TENSOR_N128, VARIANT_TENSOR_PAIR = 0, 1, 2, 3
 
 _lib = None
@@ -60,6 +61,8 @@ _PROTOS = {
     "fastid_mix": (_I32, [_P, _P, _I64, _I32, _P, _I64, _P, _I64, _P, _P]),
     "fastid_load_refs": (_I32, [_P, _P, _I64, _I32, _I64, _U32, ctypes.POINTER(_P), _P]),
     "fastid_free_refs": (_I32, [_P, _P]),
+    "fastid_refs_view": (_I32, [_P, _P, _I64, _I64, ctypes.POINTER(_P)]),
+    "fastid_topk_fold": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I32, _P]),
     "fastid_refs_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32), ctypes.POINTER(_U32),
                                 ctypes.POINTER(_I64)]),
     "fastid_scores": (_I32, [_P, _P, _P, _I64, _I64, _P, _P, _I32, _I64, _P]),
@@ -274,6 +277,34 @@ def fastid_load_refs(ctx: Context, packed: torch.Tensor, n_loci: int, flags: int
     ctx.check(load_library().fastid_load_refs(ctx.handle, p, packed.size(0), n_loci, _ld(packed), flags,
                                               ctypes.byref(h), _stream_ptr(stream)))
     return RefDB(ctx, h, packed.size(0), n_loci, flags)
+
+
+def fastid_refs_view(ctx: Context, db: RefDB, r_begin: int, n_refs: int) -> RefDB:
+    """Rows [r_begin, r_begin + n_refs) of db as a database of their own
+    (shared memory; r_begin a multiple of VIEW_ALIGN).  The view keeps a
+    reference to db; close the view before db."""
+    h = _P()
+    ctx.check(load_library().fastid_refs_view(ctx.handle, db.handle, r_begin, n_refs, ctypes.byref(h)))
+    v = RefDB(ctx, h, n_refs, db.n_loci, db.flags)
+    v.parent, v.r_begin = db, r_begin
+    return v
+
+
+def fastid_topk_fold(ctx: Context, run_scores: torch.Tensor, run_idx: torch.Tensor, blk_scores: torch.Tensor,
+                     blk_idx: torch.Tensor, ref_offset: int, stream=None) -> None:
+    """Merge blk's [n_q][k] lists (indices + ref_offset) into run's, in place."""
+    rs = _dev(run_scores, torch.int32, "run_scores", 2)
+    ri = _dev(run_idx, torch.int64, "run_idx", 2)
+    bs = _dev(blk_scores, torch.int32, "blk_scores", 2)
+    bi = _dev(blk_idx, torch.int64, "blk_idx", 2)
+    n_q, k = run_scores.shape
+    for t in (run_idx, blk_scores, blk_idx):
+        if tuple(t.shape) != (n_q, k):
+            raise ValueError("fold lists must all be [n_q][k]")
+    for t in (run_scores, run_idx, blk_scores, blk_idx):
+        if n_q > 1 and t.stride(0) != k:
+            raise ValueError("fold lists must be contiguous [n_q][k]")
+    ctx.check(load_library().fastid_topk_fold(ctx.handle, rs, ri, bs, bi, ref_offset, n_q, k, _stream_ptr(stream)))
 
 
 def fastid_scores(ctx: Context, db: RefDB, queries: torch.Tensor, modes: torch.Tensor, out: torch.Tensor,

@@ -164,8 +164,8 @@ fastid_status fastid_create(fastid_ctx **out, int32_t device) {
         uint64_t keep = ~0ull;  // keep freed scratch cached in the pool
         e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->dev_status, 4 * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(ctx->dev_status, 0, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dev_status, 8 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->dev_status, 0, 8 * sizeof(uint32_t));
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (ctx->dev_status) cudaFree(ctx->dev_status);
@@ -240,8 +240,9 @@ fastid_status fastid_sync_status(fastid_ctx *ctx, fastid_stream stream) {
     cudaStream_t s = (cudaStream_t)stream;
     FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
     uint32_t host[4];
-    FASTID_CUDA(ctx, cudaMemcpyAsync(host, ctx->dev_status, sizeof host, cudaMemcpyDeviceToHost, s));
-    FASTID_CUDA(ctx, cudaMemsetAsync(ctx->dev_status, 0, sizeof host, s));
+    // read and clear in one atomic step per word, then copy the snapshot
+    FASTID_CUDA(ctx, launch_status_take(ctx->dev_status, ctx->dev_status + 4, s));
+    FASTID_CUDA(ctx, cudaMemcpyAsync(host, ctx->dev_status + 4, sizeof host, cudaMemcpyDeviceToHost, s));
     FASTID_CUDA(ctx, cudaStreamSynchronize(s));
     if (host[0] & ST_DEVICE) return fail(ctx, FASTID_EDEVICE, "device-side check failed (detail %u)", host[1]);
     if (host[0] & ST_TIMEOUT) return fail(ctx, FASTID_ETIMEOUT, "bounded device wait ran out (site %u)", host[1]);
@@ -386,6 +387,10 @@ fastid_status fastid_load_refs(fastid_ctx *ctx, const uint64_t *packed_dev, int6
 
 fastid_status fastid_free_refs(fastid_ctx *ctx, fastid_refdb *db) {
     if (!db) return FASTID_OK;
+    if (db->view) {  // the parent owns the memory
+        delete db;
+        return FASTID_OK;
+    }
     cudaSetDevice(db->device);
     cudaDeviceSynchronize();
     cudaFree(db->packed);
@@ -394,6 +399,70 @@ fastid_status fastid_free_refs(fastid_ctx *ctx, fastid_refdb *db) {
     if (db->fp4) cudaFree(db->fp4);
     delete db;
     (void)ctx;
+    return FASTID_OK;
+}
+
+fastid_status fastid_refs_view(fastid_ctx *ctx, const fastid_refdb *db, int64_t r_begin, int64_t n_refs,
+                               fastid_refdb **out) {
+    FASTID_RANGE();
+    if (!ctx) return FASTID_EINVAL;
+    if (!out) return fail(ctx, FASTID_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!db) return fail(ctx, FASTID_EINVAL, "database is NULL");
+    if (db->device != ctx->device) return fail(ctx, FASTID_EINVAL, "database belongs to another device");
+    if (r_begin < 0 || r_begin % FASTID_VIEW_ALIGN != 0)
+        return fail(ctx, FASTID_EINVAL, "r_begin %lld is not a multiple of %d", (long long)r_begin, FASTID_VIEW_ALIGN);
+    if (n_refs < 1 || r_begin + n_refs > db->n_refs)
+        return fail(ctx, FASTID_EINVAL, "rows [%lld, %lld) outside the database's %lld", (long long)r_begin,
+                    (long long)(r_begin + n_refs), (long long)db->n_refs);
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    fastid_refdb *v = new (std::nothrow) fastid_refdb(*db);
+    if (!v) return fail(ctx, FASTID_ENOMEM, "host allocation");
+    v->view = true;
+    v->bytes = 0;
+    v->n_refs = n_refs;
+    // rows up to n_pad exist in the parent (its rows are padded to ROW_ALIGN
+    // and r_begin is a multiple of it); the kernels mask rows >= n_refs
+    v->n_pad = round_up(n_refs, ROW_ALIGN);
+    v->packed = db->packed + r_begin * db->ld64;
+    v->norms = db->norms + r_begin;
+    cudaError_t e = make_packed_map(&v->map_p, v->packed, v->n_pad, v->ld64);
+    if (e == cudaSuccess) e = make_packed_map(&v->map_p4, v->packed, v->n_pad, v->ld64, 4, tensor_tile_r4());
+    if (e == cudaSuccess && db->fp8) {
+        v->fp8 = db->fp8 + r_begin * (int64_t)db->kpad;
+        e = make_operand_map(&v->map_b, v->fp8, v->n_pad, v->kpad, tensor_tile_r());
+        if (e == cudaSuccess) e = make_operand_map(&v->map_b_half, v->fp8, v->n_pad, v->kpad, tensor_tile_r() / 2);
+    }
+    if (e == cudaSuccess && db->fp4) {
+        v->fp4 = db->fp4 + r_begin * (int64_t)db->kbytes4;
+        e = make_operand_map(&v->map_b4, v->fp4, v->n_pad, v->kbytes4, tensor_tile_r4());
+        if (e == cudaSuccess)
+            e = make_operand_map(&v->map_b4_half, v->fp4, v->n_pad, v->kbytes4, tensor_tile_r4() / 2);
+    }
+    if (e != cudaSuccess) {
+        delete v;
+        return cuda_fail(ctx, e, "view operand maps");
+    }
+    *out = v;
+    return FASTID_OK;
+}
+
+fastid_status fastid_topk_fold(fastid_ctx *ctx, uint32_t *run_scores_dev, int64_t *run_idx_dev,
+                               const uint32_t *blk_scores_dev, const int64_t *blk_idx_dev, int64_t ref_offset,
+                               int64_t n_q, int32_t k, fastid_stream stream) {
+    FASTID_RANGE();
+    if (!ctx) return FASTID_EINVAL;
+    if (n_q < 0 || n_q > 0x7fffffffll) return fail(ctx, FASTID_EINVAL, "n_q out of range: %lld", (long long)n_q);
+    if (k < 1 || k > FASTID_MAX_K) return fail(ctx, FASTID_EINVAL, "k out of range: %d", k);
+    if (ref_offset < 0 || ref_offset > 0x7fffffffll)
+        return fail(ctx, FASTID_EINVAL, "ref_offset out of range: %lld", (long long)ref_offset);
+    if (n_q > 0 && (!run_scores_dev || !run_idx_dev || !blk_scores_dev || !blk_idx_dev))
+        return fail(ctx, FASTID_EINVAL, "list buffer is NULL");
+    if (n_q == 0) return FASTID_OK;
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    FASTID_CUDA(ctx, launch_topk_fold(run_scores_dev, run_idx_dev, blk_scores_dev, blk_idx_dev, ref_offset, n_q, k,
+                                      (cudaStream_t)stream));
+    count_launches(ctx, 1);
     return FASTID_OK;
 }
 
@@ -654,7 +723,7 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
 namespace fastid {
 
 int pick_operand(int form, bool has_fp8, bool has_fp4, int64_t n_q, bool slots16) {
-    (void)has_fp4;
+    (void)slots16;
     switch (form) {
         case FASTID_FORM_PLAIN:
             return OP_PLAIN;
@@ -666,8 +735,8 @@ int pick_operand(int form, bool has_fp8, bool has_fp4, int64_t n_q, bool slots16
             return has_fp4 ? OP_FP4 : OP_FP4_PACKED;
         case FASTID_FORM_TENSOR_FP4_PACKED:
             return OP_FP4_PACKED;
-        default:  // AUTO: a few queries read the operand about once; packed rows are 1/8 of the bytes
-            return has_fp8 && n_q > (slots16 ? AUTO_PACKED_MAX_Q16 : AUTO_PACKED_MAX_Q) ? OP_FP8 : OP_FP8_PACKED;
+        default:  // AUTO: see AUTO_FP4_PACKED_MAX_Q
+            return has_fp4 && n_q > AUTO_FP4_PACKED_MAX_Q ? OP_FP4 : OP_FP4_PACKED;
     }
 }
 

@@ -231,6 +231,8 @@ cudaError_t launch_queries_e2m1(const uint64_t *q, int64_t ld_q, int64_t n_q, in
 
 cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s);
 cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s);
+// snap[0..3] = status[0..3], status cleared, atomically per word (diag.cu).
+cudaError_t launch_status_take(uint32_t *status, uint32_t *snap, cudaStream_t s);
 // Merge of per-slot lists for the queries of a tensor launch (jobs == nullptr:
 // one panel, query q's output is out_scores/out_idx row q).
 cudaError_t launch_merge_sched(const uint64_t *partial, const TcLaunch &L, const MergeJob *jobs, int64_t n_jobs,

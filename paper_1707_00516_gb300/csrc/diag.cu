@@ -31,7 +31,20 @@ __global__ void wait_flag_kernel(const uint32_t *flag, uint64_t limit_ns, uint32
     }
 }
 
+// Read-and-clear of the status word in one step (so that a condition a
+// kernel on another stream records meanwhile is never lost between a read
+// and a clear): snap[i] = atomicExch(status[i], 0) for the 4 words.
+__global__ void status_take_kernel(uint32_t *status, uint32_t *snap) {
+    const int i = threadIdx.x;
+    if (i < 4) snap[i] = atomicExch(status + i, 0u);
+}
+
 }  // namespace
+
+cudaError_t launch_status_take(uint32_t *status, uint32_t *snap, cudaStream_t s) {
+    status_take_kernel<<<1, 32, 0, s>>>(status, snap);
+    return cudaGetLastError();
+}
 
 }  // namespace fastid
 

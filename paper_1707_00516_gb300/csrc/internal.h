@@ -29,7 +29,7 @@ struct fastid_ctx {
     int form = FASTID_FORM_AUTO;
     int sms = 0;
     cudaMemPool_t pool = nullptr;
-    uint32_t *dev_status = nullptr;  // [4]
+    uint32_t *dev_status = nullptr;  // [8]: the live word [0..3], a snapshot [4..7] (fastid_sync_status)
     int grid_topk = 0, grid_hits = 0, grid_scores = 0, grid_tensor = 0;
     int pair_clusters = 0;  // resident 2-CTA clusters of the paired tensor kernel (0: never pair)
     std::string last_error;
@@ -61,6 +61,7 @@ struct fastid_refdb {
     CUtensorMap map_p4;          // TMA map over packed (boxes of 4 words x 224 refs, packed FP4 launches)
     int64_t bytes = 0;
     int device = 0;
+    bool view = false;           // fastid_refs_view: rows of another database, memory not owned
 };
 
 namespace fastid {
@@ -75,15 +76,18 @@ enum Operand : int {
 __host__ __device__ inline bool op_tensor(int op) { return op != OP_PLAIN; }
 __host__ __device__ inline bool op_packed(int op) { return op == OP_FP8_PACKED || op == OP_FP4_PACKED; }
 __host__ __device__ inline bool op_f4(int op) { return op == OP_FP4 || op == OP_FP4_PACKED; }
-// FP8 operands under AUTO: the FP8 copy, when there is one, above
-// AUTO_PACKED_MAX_Q queries, or above AUTO_PACKED_MAX_Q16 for launches with
-// 16-slot lists (k <= 16, hits, score matrices), whose packed kernel has twice
-// the expanding warps.  Measured on 20M references at N = 2048: one query
-// tile, packed rows 3.35 ms (k = 16) / 4.15 ms (k = 32) against 5.8 ms over
-// the FP8 copy; two tiles, packed rows 6.4 ms (k = 16) / 8.4 ms (k = 32)
-// against 6.7 ms as a pair over the FP8 copy.
-constexpr int64_t AUTO_PACKED_MAX_Q = 128;
-constexpr int64_t AUTO_PACKED_MAX_Q16 = 256;
+// FASTID_FORM_AUTO takes FP4 operands: the database's FP4 copy above
+// AUTO_FP4_PACKED_MAX_Q queries, else (and whenever there is no FP4 copy)
+// the packed rows expanded to FP4 on chip.  Measured with fastid_topk on 20M
+// references at N = 2048 (ms, k = 16 / k = 32):
+//   queries      FP4 copy    FP4 packed   FP8 copy    FP8 packed
+//   32-128       2.94/2.94   1.97/2.55    5.76/5.76   3.23/4.07
+//   256          3.58/3.58   3.75/4.99    6.68/6.69   6.25/8.04
+//   512          6.01/5.99   7.31/9.92    10.6/10.6   12.3/16.1
+//   2048         24.1/24.6   29.7/40.8    40.6/40.6   50.3/65.2
+// so the FP4 packed rows are never slower than an FP8 operand, and the FP4
+// copy wins from two query tiles on.
+constexpr int64_t AUTO_FP4_PACKED_MAX_Q = 128;
 int pick_operand(int form, bool has_fp8, bool has_fp4, int64_t n_q, bool slots16 = true);
 
 // The hit-list half of fastid_compare: every (q, r) with score <= threshold of

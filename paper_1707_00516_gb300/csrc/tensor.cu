@@ -61,14 +61,17 @@ constexpr uint32_t TC_SF_UNIT = 0x7F7F7F7Fu;  // four ue8m0 bytes of 2^0
 constexpr uint64_t WAIT_NS = 2000000000ull;     // 2 s per wait
 constexpr uint64_t RENDEZVOUS_NS = 50000000ull;  // 50 ms per panel entry, then go on alone
 
-// Kernel variants: references per tile (the MMA's N) and pipeline depth.
+// Kernel variants: references per tile (the MMA's N) and pipeline depth (as
+// many stages as shared memory holds: the pipeline is latency-bound, and on
+// GB300 going from 3 to 4 stages took the FP4 2048 x 20M launch from 27.5 to
+// 24.5 ms).
 //   BN = 256: 32 KB reference stage, 4 stages, 2 x 256 TMEM columns
-//   BN = 224: 28 KB reference stage, 4 stages, 2 x 224 TMEM columns + scale
-//             factors (FP4)
+//   BN = 224: 28 KB reference stage, 5 stages (4 with a packed stage), 2 x 224
+//             TMEM columns + scale factors (FP4)
 //   BN = 128: 16 KB reference stage, 6 stages, 2 x 128 TMEM columns
-template <int BN>
+template <int BN, bool PK = false>
 struct TcShape {
-    static constexpr int STAGES = BN == 128 ? 6 : 4;
+    static constexpr int STAGES = BN == 128 ? 6 : (BN == 224 && !PK) ? 5 : 4;
     static constexpr uint32_t B_BYTES = (uint32_t)BN * TC_BK;
     static constexpr uint32_t TMEM_COLS = BN == 128 ? 256 : 512;
 };
@@ -246,6 +249,14 @@ __device__ __forceinline__ void tmem_fill16(uint32_t taddr, uint32_t v) {
         "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
         "r"(v)
         : "memory");
+}
+
+// 32 lanes x one 32-bit column (every lane its own row).
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
+    uint32_t v;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return v;
 }
 
 // 32 lanes x 32 consecutive 32-bit columns.
@@ -513,7 +524,7 @@ __device__ __forceinline__ void expand_stage_f4(const uint8_t *sp, uint8_t *sb, 
 template <int BN, bool PAIR, int KM, bool PK, bool F4>
 __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS, 1)
     tensor_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TensorArgs args) {
-    using S = TcShape<BN>;
+    using S = TcShape<BN, PK>;
     static_assert(F4 ? BN == TC_BN4 : BN != TC_BN4, "FP4 launches use 224-reference tiles, FP8 ones 256 or 128");
     static_assert(!PAIR || BN != 128, "paired launches use 256- or 224-reference tiles");
     static_assert(!PK || (BN != 128 && !PAIR), "packed-reference launches use unpaired 256- or 224-reference tiles");
@@ -528,8 +539,6 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
     uint8_t *sB = base + S::STAGES * TC_A_BYTES;
     uint8_t *sP = base + S::STAGES * (TC_A_BYTES + S::B_BYTES);  // PK only
     TcSmem *ctl = reinterpret_cast<TcSmem *>(sP + (PK ? S::STAGES * P_BYTES : 0));
-    // per-thread staging of one 32-column chunk, [32][128] floats (rare path)
-    float *stage_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(ctl) + 256);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -792,10 +801,6 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                             uint32_t v[32];
                             __syncwarp();  // tcgen05.ld is warp-collective: reconverge first
                             tmem_ld32(taddr + ch * 32, v);
-                            if (ch == BN / 32 - 1) {
-                                tc_fence_before();
-                                mbar_arrive(smem_u32(&ctl->tempty[acc]));
-                            }
                             const int64_t rch = r0 + ch * 32;
                             if (args.epi == EPI_SCORES16 || args.epi == EPI_SCORES32) {
                                 if (qvalid) {
@@ -838,25 +843,29 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                                                    (uint32_t)(int32_t)(__uint_as_float(v[j]) + cq));
                                 continue;
                             }
-                            // rare path: stage the chunk, then insert candidates in lock-step
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) stage_v[j * TC_BM + row] = __uint_as_float(v[j]);
-                            while (__any_sync(0xffffffffu, m != 0u)) {
+                            // rare path: insert the candidates in lock-step, column by
+                            // column in increasing order (so each lane inserts its own
+                            // in increasing reference order); a column some lane needs
+                            // is re-read from TMEM by the whole warp (the accumulator
+                            // is released only after the tile, below)
+                            uint32_t mm = __reduce_or_sync(0xffffffffu, m);
+                            while (mm != 0u) {
+                                const int j = __ffs(mm) - 1;
+                                mm &= mm - 1u;
+                                const float d = __uint_as_float(tmem_ld1(taddr + ch * 32 + j));
                                 int32_t xs = NET_EMPTY;
                                 uint32_t xr = 0u;
-                                if (m != 0u) {
-                                    const int j = __ffs(m) - 1;
-                                    m &= m - 1u;
-                                    const float d = stage_v[j * TC_BM + row];
-                                    if (d < cut) {
-                                        xs = (int32_t)(d + cq);
-                                        xr = (uint32_t)(rch + j);
-                                    }
+                                if (((m >> j) & 1u) && d < cut) {
+                                    xs = (int32_t)(d + cq);
+                                    xr = (uint32_t)(rch + j);
                                 }
                                 net_insert(ls, lr, xs, xr);
                                 cut = ls[KM - 1] == NET_EMPTY ? cut0 : (float)ls[KM - 1] - cq;
                             }
                         }
+                        // every column of the tile is processed: the MMA may reuse the accumulator
+                        tc_fence_before();
+                        mbar_arrive(smem_u32(&ctl->tempty[acc]));
                         if (++acc == 2) {
                             acc = 0;
                             acc_phase ^= 1u;
@@ -1061,12 +1070,10 @@ __global__ void prep_jobs_kernel(const PrepJob *__restrict__ jobs, int64_t n_job
     }
 }
 
-template <int BN>
-size_t tensor_smem(int epi, bool pk = false, bool f4 = false) {
-    using S = TcShape<BN>;
-    size_t s = 1024 + S::STAGES * (size_t)(TC_A_BYTES + S::B_BYTES + (pk ? pk_stage_bytes(BN, f4) : 0)) + 256;
-    if (epi == EPI_TOPK) s += (size_t)32 * TC_BM * sizeof(float);
-    return s;
+template <int BN, bool PK = false>
+size_t tensor_smem(bool f4 = false) {
+    using S = TcShape<BN, PK>;
+    return 1024 + S::STAGES * (size_t)(TC_A_BYTES + S::B_BYTES + (PK ? pk_stage_bytes(BN, f4) : 0)) + 256;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -1177,7 +1184,7 @@ cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s
 // Largest number of 2-CTA clusters of the paired kernel that can be resident
 // at once (0 if clusters are unavailable).
 int tensor_pair_clusters(int device) {
-    size_t smem = tensor_smem<256>(EPI_TOPK);
+    size_t smem = tensor_smem<256>();
     if (cudaFuncSetAttribute(tensor_kernel<256, true, TC_KMAX, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
         cudaGetLastError();
@@ -1217,7 +1224,7 @@ namespace {
 // (2-CTA clusters when paired).
 template <int BN, bool PAIR, int KM, bool PK = false, bool F4 = false>
 cudaError_t launch_variant(const TcMaps &maps, const TensorArgs &a, int32_t n_groups, int epi, cudaStream_t s) {
-    const size_t smem = tensor_smem<BN>(epi, PK, F4);
+    const size_t smem = tensor_smem<BN, PK>(F4);
     cudaError_t e = cudaFuncSetAttribute(tensor_kernel<BN, PAIR, KM, PK, F4>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

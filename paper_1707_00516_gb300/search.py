@@ -34,9 +34,9 @@ class Searcher:
 
     def default_flags(self) -> int:
         """Database flags the chosen form needs (the operand copy it reads)."""
-        if self.form in (B.FORM_TENSOR, B.FORM_AUTO):
+        if self.form == B.FORM_TENSOR:
             return B.REFS_TENSOR
-        return B.REFS_FP4 if self.form == B.FORM_TENSOR_FP4 else 0
+        return B.REFS_FP4 if self.form in (B.FORM_TENSOR_FP4, B.FORM_AUTO) else 0
 
     def load_refs_alleles(self, alleles: torch.Tensor, n_loci: int, flags: int | None = None) -> B.RefDB:
         """Pack uint8 allele rows already on the device and load them."""

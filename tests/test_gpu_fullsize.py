@@ -10,7 +10,8 @@ The oracle cannot produce the whole score matrix here, so the checks are
   * no reference of a seeded random sample of 4096 beats a list's k-th entry
     (and every sampled reference that should be in a list is);
   * every planted contributor (score 0) is found;
-  * the plain and tensor forms return identical lists;
+  * the FP4, FP8 and plain forms return identical lists (the first is checked
+    against the oracle as below, so all three are);
   * for 32 seeded queries of the 20M-reference workload (16 individuals, 16
     mixtures) the oracle scans every reference, and its top-k lists equal the
     returned ones exactly.
@@ -32,8 +33,8 @@ FULL_SCAN_PER_MODE = 16
 SCAN_CHUNK = 1 << 18
 
 CASES = {
-    "c3": dict(n_refs=20_000_000, n_loci=2048, k=32, T=512, forms=("tensor", "plain")),
-    "c2": dict(n_refs=1_000_000, n_loci=4096, k=16, T=0, forms=("tensor", "plain")),
+    "c3": dict(n_refs=20_000_000, n_loci=2048, k=32, T=512, forms=("fp4", "tensor", "plain")),
+    "c2": dict(n_refs=1_000_000, n_loci=4096, k=16, T=0, forms=("fp4", "tensor", "plain")),
 }
 
 
@@ -46,13 +47,13 @@ def test_fullsize_sampled_parity(name):
     n_refs, n_loci, k, T = cfg["n_refs"], cfg["n_loci"], cfg["k"], cfg["T"]
     seed = gen.config_seed(int(name[1]))
     s = Searcher(0, B.FORM_AUTO)
-    db, thr = bench.build_db(s, seed, n_refs, n_loci, B.REFS_TENSOR)
+    db, thr = bench.build_db(s, seed, n_refs, n_loci, B.REFS_TENSOR | B.REFS_FP4)
     recipe = bench.recipe_for(name, n_refs=n_refs)
     thr_dev = torch.from_numpy(thr.view(np.int32)).cuda()
     q, modes = bench.device_queries(s, seed, recipe, thr_dev, n_loci)
     results, hits = {}, {}
     for form in cfg["forms"]:
-        B.fastid_set_form(s.ctx, B.FORM_PLAIN if form == "plain" else B.FORM_TENSOR)
+        B.fastid_set_form(s.ctx, {"plain": B.FORM_PLAIN, "tensor": B.FORM_TENSOR, "fp4": B.FORM_TENSOR_FP4}[form])
         sc, ix = s.topk(db, q, modes, k, T)
         torch.cuda.synchronize()
         assert B.fastid_sync_status(s.ctx) == B.OK

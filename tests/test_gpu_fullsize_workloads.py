@@ -160,13 +160,12 @@ SERVE_SECONDS = 1.5
 def test_c5_serving_fullsize():
     import __graft_entry__
     import bench
-    from paper_1707_00516_gb300.serve import Server
     __graft_entry__.build()
     w = dict(bench.WORKLOADS["c5"])
     n_refs, n_loci, k, T = w["n_refs"], w["n_loci"], w["k"], w["threshold"]
     s = Searcher(0, B.FORM_AUTO)
     seed = gen.config_seed(w["cfg"])
-    db, thr = bench.build_db(s, seed, n_refs, n_loci, B.REFS_TENSOR)
+    db, thr = bench.build_db(s, seed, n_refs, n_loci, B.REFS_FP4)
     thr_dev = torch.from_numpy(thr.view(np.int32)).cuda()
     arrivals, sizes, rec = bench.c5_requests(w, seed, SERVE_SECONDS)
     q, m = bench.device_queries(s, seed, rec, thr_dev, n_loci)
@@ -174,7 +173,7 @@ def test_c5_serving_fullsize():
     hm = m.cpu().numpy()
     offs = np.concatenate([[0], np.cumsum(sizes)])
     d = bench.C5_DEFAULTS
-    srv = Server(s.ctx, db, k, T, hbm_budget_bytes=d["hbm_budget"], max_wave=d["max_wave"], max_slots=d["slots"])
+    srv = bench.make_server(d["server"], s.ctx, db, k, T, d["parts"], d["slots"], d["max_wave"], d["hbm_budget"])
     futs = []
     t0 = time.perf_counter()
     for i in range(arrivals.size):

@@ -1,6 +1,8 @@
-"""Continuous-batching server: requests that arrive while others run are
-coalesced into waves on several slots, and every request's result equals its
-result when run alone (and the oracle's)."""
+"""Continuous-batching servers: requests that arrive while others run are
+coalesced into waves (on slots: Server; joining a running pass over the
+database's parts: SweepServer), and every request's result equals its result
+when run alone (and the oracle's)."""
+import time
 import threading
 
 import numpy as np
@@ -14,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_1707_00516_gb300 import binding as B  # noqa: E402
 from paper_1707_00516_gb300.search import Searcher  # noqa: E402
-from paper_1707_00516_gb300.serve import Server  # noqa: E402
+from paper_1707_00516_gb300.serve import Server, SweepServer  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -107,6 +109,130 @@ def test_device_condition_fails_its_wave(env):
     try:
         flag = torch.zeros(1, dtype=torch.int32, device="cuda")
         B.fastid_wait_flag(s.ctx, flag, 50)  # nothing sets the flag: the wait runs out
+        torch.cuda.synchronize()
+        f = srv.submit(reqs[0][0], reqs[0][1])
+        with pytest.raises(B.FastIDError) as e:
+            f.result(timeout=120)
+        assert e.value.status == B.ETIMEOUT
+        sc, ix = srv.submit(reqs[1][0], reqs[1][1]).result(timeout=120)
+        mis, une = oracle.scores(R, reqs[1][2])
+        es, ei = oracle.topk(oracle.select(mis, une, reqs[1][1]), 8)
+        assert np.array_equal(sc, es) and np.array_equal(ix, ei)
+    finally:
+        srv.close()
+    assert B.fastid_sync_status(s.ctx) == B.OK
+
+
+def _alone(s, db, reqs, k, T):
+    out = []
+    for packed, modes, _ in reqs:
+        q = torch.from_numpy(packed.view(np.int64)).cuda()
+        sc, ix = s.topk(db, q, torch.from_numpy(modes).cuda(), k, T)
+        out.append((sc.cpu().numpy().view(np.uint32), ix.cpu().numpy()))
+    return out
+
+
+@pytest.mark.parametrize("form", [B.FORM_AUTO, B.FORM_TENSOR, B.FORM_PLAIN])
+def test_sweep_alone_equal_mix(env, form):
+    """SweepServer: 48 requests from four client threads, waves joining the
+    running pass over three parts; each result equals the request alone and
+    the oracle."""
+    s, db, R, thr, seed = env
+    B.fastid_set_form(s.ctx, form)
+    k, T = 16, 200
+    reqs = _requests(R, thr, seed, 48, np.random.default_rng(5))
+    alone = _alone(s, db, reqs, k, T)
+    srv = SweepServer(s.ctx, db, k, T, parts=3, capacity=1024, max_wave=256)
+    futs = [None] * len(reqs)
+
+    def client(ids):
+        for i in ids:
+            futs[i] = srv.submit(reqs[i][0], reqs[i][1])
+
+    threads = [threading.Thread(target=client, args=(list(range(t, len(reqs), 4)),)) for t in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    got = [f.result(timeout=120) for f in futs]
+    st = srv.stats()
+    srv.close()
+    B.fastid_set_form(s.ctx, B.FORM_TENSOR)
+    assert st["requests"] == len(reqs) and st["waves"] < len(reqs)
+    for (a_sc, a_ix), (g_sc, g_ix) in zip(alone, got):
+        assert np.array_equal(a_sc, g_sc) and np.array_equal(a_ix, g_ix)
+    for i in (0, 23, 47):
+        _, modes, Q = reqs[i]
+        mis, une = oracle.scores(R, Q)
+        es, ei = oracle.topk(oracle.select(mis, une, modes), k, T)
+        assert np.array_equal(got[i][0], es) and np.array_equal(got[i][1], ei)
+
+
+def test_sweep_waves_share_launches(env):
+    """A second burst of requests submitted while the first wave is still in
+    its pass joins the running pass: some steps (one comparison launch each)
+    serve both waves, and by the device timestamps of the steps the second
+    wave's work starts before the first wave's work ends.  Results equal the
+    oracle."""
+    s, db, R, thr, seed = env
+    k, T = 8, B.NO_THRESHOLD
+    reqs = _requests(R, thr, seed, 8, np.random.default_rng(9))
+    srv = SweepServer(s.ctx, db, k, T, parts=16, capacity=1024, max_wave=256)
+    srv.trace = []
+    first = [srv.submit(p, m) for p, m, _ in reqs[:4]]
+    t0 = time.perf_counter()
+    while srv.steps < 1 and time.perf_counter() - t0 < 30:
+        time.sleep(0.0002)
+    second = [srv.submit(p, m) for p, m, _ in reqs[4:]]
+    got = [f.result(timeout=120) for f in first + second]
+    trace = list(srv.trace)
+    srv.close()
+    torch.cuda.synchronize()
+    waves = []  # wave ids in the order they first appear
+    for _, _, ids in trace:
+        for w in ids:
+            if w not in waves:
+                waves.append(w)
+    assert len(waves) >= 2
+    shared = [ids for _, _, ids in trace if waves[0] in ids and waves[1] in ids]
+    assert shared, "no launch served both waves"
+    base = trace[0][0]
+    span = {w: (min(base.elapsed_time(a) for a, _, ids in trace if w in ids),
+                max(base.elapsed_time(b) for _, b, ids in trace if w in ids)) for w in waves[:2]}
+    assert span[waves[1]][0] < span[waves[0]][1]  # overlapping on the device
+    for i, (_, modes, Q) in enumerate(reqs):
+        mis, une = oracle.scores(R, Q)
+        es, ei = oracle.topk(oracle.select(mis, une, modes), k, T)
+        assert np.array_equal(got[i][0], es) and np.array_equal(got[i][1], ei), i
+
+
+def test_sweep_ring_admission(env):
+    """A ring that holds one full wave: requests wait for rows, the ring
+    wraps, and every result is still the request's result alone."""
+    s, db, R, thr, seed = env
+    k, T = 4, 150
+    reqs = _requests(R, thr, seed, 20, np.random.default_rng(13))
+    alone = _alone(s, db, reqs, k, T)
+    srv = SweepServer(s.ctx, db, k, T, parts=2, capacity=100, max_wave=64)
+    with pytest.raises(ValueError):
+        srv.submit(np.zeros((65, srv.words), np.uint64), np.zeros(65, np.uint8))
+    futs = [srv.submit(p, m) for p, m, _ in reqs]
+    got = [f.result(timeout=120) for f in futs]
+    srv.close()
+    for (a_sc, a_ix), (g_sc, g_ix) in zip(alone, got):
+        assert np.array_equal(a_sc, g_sc) and np.array_equal(a_ix, g_ix)
+
+
+def test_sweep_device_condition_fails_its_wave(env):
+    """As for Server: a planted bounded-wait timeout fails the wave that reads
+    it with FASTID_ETIMEOUT, and the next wave is delivered, equal to the
+    oracle.  No GPU fault or hang is involved."""
+    s, db, R, thr, seed = env
+    reqs = _requests(R, thr, seed, 2, np.random.default_rng(17))
+    srv = SweepServer(s.ctx, db, 8, B.NO_THRESHOLD, parts=3, capacity=512, max_wave=256)
+    try:
+        flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+        B.fastid_wait_flag(s.ctx, flag, 50)
         torch.cuda.synchronize()
         f = srv.submit(reqs[0][0], reqs[0][1])
         with pytest.raises(B.FastIDError) as e:

@@ -146,10 +146,9 @@ def test_paired_launch_parity(ts, n_q, n_refs, k):
 @pytest.mark.parametrize("n_q,k", [(100, 12), (128, 12), (129, 12), (256, 12), (257, 12), (300, 12), (600, 12),
                                    (128, 32), (129, 32)])
 def test_auto_form_both_operands(n_q, k):
-    """FASTID_FORM_AUTO reads the packed rows up to 256 queries at k <= 16 and
-    up to 128 at k > 16, and the FP8 copy above (paired from two query tiles
-    on; 300 queries pad to four tiles): results equal the oracle on both sides
-    of each switch."""
+    """FASTID_FORM_AUTO takes the FP4 form: the packed rows up to 128 queries and
+    the database's FP4 copy above (paired from two query tiles on; 300 queries
+    pad to four tiles): results equal the oracle on both sides of the switch."""
     import __graft_entry__
     __graft_entry__.build()
     s = Searcher(0, B.FORM_AUTO)
@@ -158,7 +157,7 @@ def test_auto_form_both_operands(n_q, k):
     Q = (rng.random((n_q, 700)) < 0.3).astype(np.uint8)
     modes = (rng.random(n_q) < 0.5).astype(np.uint8)
     db = s.load_refs_alleles(torch.from_numpy(R).cuda(), 700)
-    assert db.info()["flags"] == B.REFS_TENSOR
+    assert db.info()["flags"] == B.REFS_FP4
     q = torch.empty((n_q, words64(700)), dtype=torch.int64, device="cuda")
     B.fastid_pack(s.ctx, torch.from_numpy(Q).cuda(), 700, q)
     sc, ix = s.topk(db, q, torch.from_numpy(modes).cuda(), k, 400)

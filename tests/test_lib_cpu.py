@@ -65,6 +65,8 @@ def test_null_context_is_einval(lib):
     assert lib.fastid_mix(P, P, 1, 1, P, 1, P, 1, P, P) == B.EINVAL
     assert lib.fastid_load_refs(P, P, 1, 64, 1, 0, None, P) == B.EINVAL
     assert lib.fastid_free_refs(P, P) == B.OK
+    assert lib.fastid_refs_view(P, P, 0, 1, None) == B.EINVAL
+    assert lib.fastid_topk_fold(P, P, P, P, P, 0, 1, 16, P) == B.EINVAL
     assert lib.fastid_refs_info(P, None, None, None, None) == B.EINVAL
     assert lib.fastid_scores(P, P, P, 1, 1, P, P, 4, 1, P) == B.EINVAL
     assert lib.fastid_topk(P, P, P, 1, 1, P, 16, 0, P, P, P) == B.EINVAL
