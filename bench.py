@@ -662,7 +662,8 @@ def batched_measure(s, w, steps: int, warmup: int, e2e: bool = True, probe: dict
     seed, sizes, panels = _c4_batches(w)
     dbs, thrs = [], []
     for p, n_loci in enumerate(w["panels"]):
-        db, thr = build_db(s, seed + 10 * p, w["n_refs"], n_loci, B.REFS_TENSOR, chunk=(1 << 28) // n_loci)
+        db, thr = build_db(s, seed + 10 * p, w["n_refs"], n_loci, B.REFS_TENSOR | B.REFS_FP4,
+                           chunk=(1 << 28) // n_loci)
         dbs.append(db)
         thrs.append(torch.from_numpy(thr.view(np.int32)).to(dev))
     tuner = Autotuner()
@@ -698,19 +699,21 @@ def batched_measure(s, w, steps: int, warmup: int, e2e: bool = True, probe: dict
     value = pairs * steps / (total_ms / 1e3)
     from paper_1707_00516_gb300 import peaks as P
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak, unit, how = roof_peak("fp8", probe if probe is not None else P.measure(), n_sms)
+    fp4 = bs.variant in (B.VARIANT_TENSOR_FP4, B.VARIANT_TENSOR_FP4_PAIR)
+    peak, unit, how = roof_peak("fp4" if fp4 else "fp8", probe if probe is not None else P.measure(), n_sms)
     achieved = flops * steps / (total_ms / 1e3) / 1e12
     info = bs.plan.info()
+    tune_ms = tuner.last_timings or tuner._cache.get(tuner.key(bs.dbs, bs.batches, w["k"]), {}).get("ms", {})
     out = {"workload": w["workload"], "value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
            "ms_per_step": total_ms / steps,
            "batch_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                                 "note": "every batch of a step completes with its graph replay"},
            "config": {"n_batches": int(len(sizes)), "n_queries": int(sum(sizes)), "panels": list(w["panels"]),
                       "n_refs_per_panel": w["n_refs"], "k": w["k"], "variant": int(bs.variant),
-                      "autotune_ms": {str(k): v for k, v in tuner.last_timings.items()}, "grid": info["grid"],
+                      "autotune_ms": {str(k): v for k, v in tune_ms.items()}, "grid": info["grid"],
                       "units": info["n_units"],
                       "launch": "one persistent launch per step, CUDA graph replay (prep + compare + merge)"},
-           "dtype": FORMS["fp8"][2], "gpu_launches": 3 * steps,
+           "dtype": FORMS["fp4" if fp4 else "fp8"][2], "gpu_launches": 3 * steps,
            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": unit,
                         "frac": achieved / peak, "traffic": None, "peak_source": how,
                         "kernel": "tensor_kernel over 4 panels (whole graph time incl. prep and merge)"},

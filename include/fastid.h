@@ -375,11 +375,13 @@ fastid_status fastid_wait_flag(fastid_ctx *ctx, const uint32_t *flag_dev, int32_
  * fastid_plan_replay launches that graph.  Between runs the caller may change
  * the contents (not the addresses or sizes) of the batch buffers.
  *
- * Every panel must have been loaded with FASTID_REFS_TENSOR; at most 8 panels.
+ * FP8 variants need every panel loaded with FASTID_REFS_TENSOR, FP4 variants
+ * with FASTID_REFS_FP4 (EUNSUPPORTED otherwise); at most 8 panels.
  * Batch queries use the packed layout of fastid_topk; out_scores/out_idx are
- * [n_q][k] as in fastid_topk.  variant picks the reference-tile width of the
- * compare kernel (FASTID_VARIANT_*; the autotuner in the Python package
- * chooses it per workload).  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA.
+ * [n_q][k] as in fastid_topk.  variant picks the operand encoding and the
+ * reference-tile shape of the compare kernel (FASTID_VARIANT_*; the autotuner
+ * in the Python package chooses it per workload).  fastid_plan_info reports
+ * the variant AUTO resolved to.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA.
  */
 typedef struct fastid_plan fastid_plan;
 
@@ -394,10 +396,13 @@ typedef struct {
 } fastid_batch;
 
 enum {
-    FASTID_VARIANT_AUTO = 0,        /* the library's default (N256)            */
-    FASTID_VARIANT_TENSOR_N256 = 1, /* 128 x 256 tiles, 4-stage pipeline       */
-    FASTID_VARIANT_TENSOR_N128 = 2, /* 128 x 128 tiles, 6-stage pipeline       */
-    FASTID_VARIANT_TENSOR_PAIR = 3  /* 2-CTA clusters on tile pairs sharing reference stages */
+    FASTID_VARIANT_AUTO = 0,        /* FP4_PAIR when every panel has its FP4 copy,
+                                       else N256                               */
+    FASTID_VARIANT_TENSOR_N256 = 1, /* FP8, 128 x 256 tiles, 4-stage pipeline  */
+    FASTID_VARIANT_TENSOR_N128 = 2, /* FP8, 128 x 128 tiles, 6-stage pipeline  */
+    FASTID_VARIANT_TENSOR_PAIR = 3, /* FP8, 2-CTA clusters on tile pairs sharing reference stages */
+    FASTID_VARIANT_TENSOR_FP4 = 4,  /* FP4 (block-scaled e2m1), 128 x 224 tiles, 5-stage pipeline */
+    FASTID_VARIANT_TENSOR_FP4_PAIR = 5 /* FP4, 2-CTA clusters on tile pairs                     */
 };
 
 fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs, int32_t n_panels,

@@ -28,7 +28,8 @@ MAX_LOCI = 65536
 NO_THRESHOLD = 0xFFFFFFFF
 NOALLOC_SCRATCH_BYTES = 16 << 20
 VIEW_ALIGN = 256
-VARIANT_AUTO, VARIANT_TENSOR_N256, VARIANT_TENSOR_N128, VARIANT_TENSOR_PAIR = 0, 1, 2, 3
+(VARIANT_AUTO, VARIANT_TENSOR_N256, VARIANT_TENSOR_N128, VARIANT_TENSOR_PAIR, VARIANT_TENSOR_FP4,
+ VARIANT_TENSOR_FP4_PAIR) = range(6)
 
 _lib = None
 _lock = threading.Lock()

@@ -72,12 +72,12 @@ constexpr int TC_TILE_Q = 128;
 struct PrepJob {
     const uint64_t *src;   // packed query row
     const uint8_t *mode;   // its mode byte
-    uint8_t *dst;          // e4m3 operand row [kpad]
+    uint8_t *dst;          // operand row [kpad bytes]: e4m3, or e2m1 when f4
     float *qc;             // its c_q
     int32_t n_words;
     int32_t n_loci;
-    int32_t kpad;
-    int32_t pad_;
+    int32_t kpad;          // operand row bytes
+    int32_t f4;            // 1: FP4 (e2m1) operand
 };
 
 // Batched form: one query's merge of per-slot lists into its output row.

@@ -28,6 +28,7 @@ struct fastid_plan {
     fastid_ctx *ctx = nullptr;
     int32_t n_panels = 0;
     int32_t bn = 256;
+    int32_t variant = FASTID_VARIANT_TENSOR_N256;  // as resolved from AUTO
     int32_t k = 0;
     uint32_t threshold = 0;
     int64_t n_queries = 0;
@@ -83,18 +84,27 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
         return perr(ctx, FASTID_EINVAL, "n_panels must be in 1..8 with a database per panel");
     if (n_batches < 0 || (n_batches > 0 && !batches)) return perr(ctx, FASTID_EINVAL, "bad batch list");
     if (k < 1 || k > FASTID_MAX_K) return perr(ctx, FASTID_EINVAL, "k out of range");
-    if (variant != FASTID_VARIANT_AUTO && variant != FASTID_VARIANT_TENSOR_N256 &&
-        variant != FASTID_VARIANT_TENSOR_N128 && variant != FASTID_VARIANT_TENSOR_PAIR)
+    if (variant < FASTID_VARIANT_AUTO || variant > FASTID_VARIANT_TENSOR_FP4_PAIR)
         return perr(ctx, FASTID_EINVAL, "unknown variant");
-    if (variant == FASTID_VARIANT_TENSOR_PAIR && ctx->pair_clusters < 1)
-        return perr(ctx, FASTID_EUNSUPPORTED, "paired launches need 2-CTA clusters");
+    bool all_fp8 = true, all_fp4 = true;
     for (int p = 0; p < n_panels; ++p) {
         if (!dbs[p]) return perr(ctx, FASTID_EINVAL, "database is NULL");
         if (dbs[p]->device != ctx->device) return perr(ctx, FASTID_EINVAL, "database belongs to another device");
-        if (!dbs[p]->fp8)
-            return perr(ctx, FASTID_EUNSUPPORTED, "batched plans use the tensor form: load every panel with "
-                                                  "FASTID_REFS_TENSOR");
+        all_fp8 = all_fp8 && dbs[p]->fp8;
+        all_fp4 = all_fp4 && dbs[p]->fp4;
     }
+    if (variant == FASTID_VARIANT_AUTO)  // the FP4 copies when every panel has one, paired when clusters run
+        variant = all_fp4 ? (ctx->pair_clusters > 0 ? FASTID_VARIANT_TENSOR_FP4_PAIR : FASTID_VARIANT_TENSOR_FP4)
+                          : FASTID_VARIANT_TENSOR_N256;
+    const bool f4 = variant == FASTID_VARIANT_TENSOR_FP4 || variant == FASTID_VARIANT_TENSOR_FP4_PAIR;
+    if ((variant == FASTID_VARIANT_TENSOR_PAIR || variant == FASTID_VARIANT_TENSOR_FP4_PAIR) && ctx->pair_clusters < 1)
+        return perr(ctx, FASTID_EUNSUPPORTED, "paired launches need 2-CTA clusters");
+    if (f4 && !all_fp4)
+        return perr(ctx, FASTID_EUNSUPPORTED, "FP4 plan variants read the FP4 copy: load every panel with "
+                                              "FASTID_REFS_FP4");
+    if (!f4 && !all_fp8)
+        return perr(ctx, FASTID_EUNSUPPORTED, "FP8 plan variants read the FP8 copy: load every panel with "
+                                              "FASTID_REFS_TENSOR");
     for (int b = 0; b < n_batches; ++b) {
         const fastid_batch &B = batches[b];
         if (B.panel < 0 || B.panel >= n_panels) return perr(ctx, FASTID_EINVAL, "batch panel out of range");
@@ -110,11 +120,14 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     if (!P) return perr(ctx, FASTID_ENOMEM, "host allocation");
     P->ctx = ctx;
     P->n_panels = n_panels;
-    P->bn = variant == FASTID_VARIANT_TENSOR_N128 ? 128 : 256;
+    P->bn = f4 ? tensor_tile_r4() : variant == FASTID_VARIANT_TENSOR_N128 ? 128 : 256;
+    P->variant = variant;
     P->k = k;
     P->threshold = threshold;
     const int BN = P->bn;
-    const int pair = variant == FASTID_VARIANT_TENSOR_PAIR ? 1 : 0;
+    const int pair = (variant == FASTID_VARIANT_TENSOR_PAIR || variant == FASTID_VARIANT_TENSOR_FP4_PAIR) ? 1 : 0;
+    // operand row bytes of each panel (FP8: a byte per locus; FP4: two loci a byte)
+    auto kbytes = [&](int p) { return (int64_t)(f4 ? dbs[p]->kbytes4 : dbs[p]->kpad); };
     const int64_t tq = (int64_t)TC_TILE_Q * (pair ? 2 : 1);  // operand rows per tile (pair)
 
     // Rows of each panel's operand: its batches' queries, in batch order.
@@ -124,13 +137,14 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     for (int p = 0; p < n_panels; ++p) {
         rows_pad[p] = rup(std::max<int64_t>(rows[p], 1), tq);
         n_qq[p] = rows[p] > 0 ? rows_pad[p] / tq : 0;
-        n_rt[p] = dbs[p]->n_pad / BN;
-        tile_bytes[p] = (int64_t)BN * dbs[p]->kpad;
+        n_rt[p] = (dbs[p]->n_pad + BN - 1) / BN;
+        tile_bytes[p] = (int64_t)BN * kbytes(p);
         P->n_queries += rows[p];
     }
     TcLaunch &L = P->launch;
     memset(&L, 0, sizeof L);
     L.pair = pair;
+    L.f4 = f4 ? 1 : 0;
     L.n_groups = make_tensor_schedule(n_panels, n_qq.data(), n_rt.data(), tile_bytes.data(),
                                       pair ? ctx->pair_clusters : ctx->grid_tensor, pair ? 2 : 1, L.sched,
                                       L.order, &L.n_slots);
@@ -152,7 +166,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     std::vector<size_t> o_a(n_panels), o_qc(n_panels);
     int64_t n_prep = 0;
     for (int p = 0; p < n_panels; ++p) {
-        o_a[p] = take((size_t)rows_pad[p] * dbs[p]->kpad);
+        o_a[p] = take((size_t)rows_pad[p] * kbytes(p));
         o_qc[p] = take((size_t)rows_pad[p] * sizeof(float));
         n_prep += rows_pad[p];
     }
@@ -185,12 +199,12 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
                 PrepJob &j = prep[prep_base[p] + r];
                 j.src = nullptr;
                 j.mode = nullptr;
-                j.dst = W + o_a[p] + (size_t)r * dbs[p]->kpad;
+                j.dst = W + o_a[p] + (size_t)r * kbytes(p);
                 j.qc = reinterpret_cast<float *>(W + o_qc[p]) + r;
                 j.n_words = dbs[p]->n_words64;
                 j.n_loci = dbs[p]->n_loci;
-                j.kpad = dbs[p]->kpad;
-                j.pad_ = 0;
+                j.kpad = (int32_t)kbytes(p);
+                j.f4 = f4 ? 1 : 0;
             }
         for (int b = 0; b < n_batches; ++b) {
             const fastid_batch &B = batches[b];
@@ -222,9 +236,10 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     // Launch description.
     L.n_panels = n_panels;
     for (int p = 0; p < n_panels; ++p) {
-        e = make_operand_map(&L.map_a[p], W + o_a[p], rows_pad[p], dbs[p]->kpad, TC_TILE_Q);
+        e = make_operand_map(&L.map_a[p], W + o_a[p], rows_pad[p], (int32_t)kbytes(p), TC_TILE_Q);
         if (e == cudaSuccess)
-            e = make_operand_map(&L.map_b[p], dbs[p]->fp8, dbs[p]->n_pad, dbs[p]->kpad, pair ? BN / 2 : BN);
+            e = make_operand_map(&L.map_b[p], f4 ? dbs[p]->fp4 : dbs[p]->fp8, dbs[p]->n_pad, (int32_t)kbytes(p),
+                                 pair ? BN / 2 : BN);
         if (e != cudaSuccess) {
             free_plan(P);
             return pcuda(ctx, e, "tensor maps");
@@ -232,7 +247,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
         L.n_refs[p] = dbs[p]->n_refs;
         L.n_q[p] = rows[p];
         L.n_rt[p] = n_rt[p];
-        L.kpad[p] = dbs[p]->kpad;
+        L.kpad[p] = (int32_t)kbytes(p);
         L.qconst[p] = reinterpret_cast<const float *>(W + o_qc[p]);
     }
     L.k = k;
@@ -338,9 +353,7 @@ fastid_status fastid_plan_info(const fastid_plan *plan, int64_t *n_queries, int6
         *n_units = u;
     }
     if (grid) *grid = (int32_t)plan->n_ctas;
-    if (variant)
-        *variant = plan->launch.pair ? FASTID_VARIANT_TENSOR_PAIR
-                                     : (plan->bn == 128 ? FASTID_VARIANT_TENSOR_N128 : FASTID_VARIANT_TENSOR_N256);
+    if (variant) *variant = plan->variant;
     if (workspace_bytes) *workspace_bytes = plan->work_bytes;
     return FASTID_OK;
 }

@@ -1066,7 +1066,10 @@ __global__ void prep_jobs_kernel(const PrepJob *__restrict__ jobs, int64_t n_job
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_jobs; j += warps_total) {
         const PrepJob jb = jobs[j];
         const bool mis = jb.src != nullptr && *jb.mode == FASTID_MODE_MISMATCH;
-        encode_query_row(jb.src, mis, jb.n_words, jb.n_loci, jb.kpad, jb.dst, jb.qc, lane);
+        if (jb.f4)
+            encode_query_row_f4(jb.src, mis, jb.n_words, jb.n_loci, jb.kpad, jb.dst, jb.qc, lane);
+        else
+            encode_query_row(jb.src, mis, jb.n_words, jb.n_loci, jb.kpad, jb.dst, jb.qc, lane);
     }
 }
 

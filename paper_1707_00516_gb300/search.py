@@ -60,6 +60,15 @@ class Searcher:
         B.fastid_mix(self.ctx, src_packed, w, offsets, q)
         return q
 
+    def tune_form(self, db: B.RefDB, queries: torch.Tensor, modes: torch.Tensor, k: int,
+                  threshold: int = B.NO_THRESHOLD, tuner=None) -> int:
+        """Measure (or recall) the fastest form for calls like this one and
+        make it the context's form (tune.FormTuner)."""
+        from .tune import FormTuner
+        self.form = (tuner or FormTuner()).choose(self.ctx, db, queries, modes, k, threshold)
+        B.fastid_set_form(self.ctx, self.form)
+        return self.form
+
     def topk(self, db: B.RefDB, queries: torch.Tensor, modes: torch.Tensor, k: int,
              threshold: int = B.NO_THRESHOLD):
         n_q = queries.shape[0]

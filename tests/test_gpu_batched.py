@@ -26,7 +26,7 @@ def setup():
         seed = 900 + i
         thr = gen.maf_thresholds(seed, n_loci)
         R = gen.allele_rows(seed, gen.STREAM_DB, np.arange(n_refs), thr)
-        db = s.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci)
+        db = s.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci, flags=B.REFS_TENSOR | B.REFS_FP4)
         panels.append((R, db, thr, seed))
     yield s, panels
     for _, db, _, _ in panels:
@@ -72,7 +72,8 @@ def _check(panels, batches, k, T):
         assert np.array_equal(ix.cpu().numpy(), ei)
 
 
-@pytest.mark.parametrize("variant", [B.VARIANT_TENSOR_N256, B.VARIANT_TENSOR_N128, B.VARIANT_TENSOR_PAIR])
+@pytest.mark.parametrize("variant", [B.VARIANT_TENSOR_N256, B.VARIANT_TENSOR_N128, B.VARIANT_TENSOR_PAIR,
+                                     B.VARIANT_TENSOR_FP4, B.VARIANT_TENSOR_FP4_PAIR])
 @pytest.mark.parametrize("k,T", [(16, B.NO_THRESHOLD), (32, 40), (17, B.NO_THRESHOLD), (3, 25)])
 def test_plan_run_matches_oracle(setup, variant, k, T):
     s, panels = setup
@@ -80,7 +81,7 @@ def test_plan_run_matches_oracle(setup, variant, k, T):
     batches = _make_batches(s, panels, sizes, k, salt=11 + variant)
     plan = B.Plan(s.ctx, [p[1] for p in panels], [b[:5] for b in batches], k, T, variant)
     info = plan.info()
-    assert info["n_queries"] == sum(sizes)
+    assert info["n_queries"] == sum(sizes) and info["variant"] == variant
     plan.run()
     torch.cuda.synchronize()
     assert B.fastid_sync_status(s.ctx) == B.OK
@@ -94,6 +95,7 @@ def test_plan_graph_replay_with_new_contents(setup):
     sizes = [33, 200, 1, 90]
     batches = _make_batches(s, panels, sizes, k, salt=5)
     plan = B.Plan(s.ctx, [p[1] for p in panels], [b[:5] for b in batches], k)
+    assert plan.info()["variant"] == B.VARIANT_TENSOR_FP4_PAIR  # AUTO: every panel has its FP4 copy
     plan.capture()
     plan.replay()
     torch.cuda.synchronize()
@@ -119,3 +121,32 @@ def test_plan_needs_tensor_copy(setup):
         B.Plan(s.ctx, [db_plain], [], 8)
     assert e.value.status == B.EUNSUPPORTED
     db_plain.close()
+    db_fp8 = s.load_refs_alleles(torch.from_numpy(R).cuda(), R.shape[1], flags=B.REFS_TENSOR)
+    for v in (B.VARIANT_TENSOR_FP4, B.VARIANT_TENSOR_FP4_PAIR):
+        with pytest.raises(B.FastIDError) as e:
+            B.Plan(s.ctx, [db_fp8], [], 8, variant=v)
+        assert e.value.status == B.EUNSUPPORTED
+    assert B.Plan(s.ctx, [db_fp8], [], 8).info()["variant"] == B.VARIANT_TENSOR_N256
+    db_fp8.close()
+
+
+def test_form_tuner_choice_is_exact(setup, tmp_path):
+    """FormTuner times every form the database supports for these calls,
+    caches the fastest, and the chosen form's results equal the oracle."""
+    from paper_1707_00516_gb300.tune import FormTuner, forms_for
+    s, panels = setup
+    R, db, thr, seed = panels[2]
+    k, T = 16, B.NO_THRESHOLD
+    batches = _make_batches(s, panels, [300], k, salt=21, panel_ids=[2])
+    _, q, m, sc, ix, Q, modes = batches[0]
+    tuner = FormTuner(cache_path=str(tmp_path / "tune.json"))
+    f = s.tune_form(db, q, m, k, T, tuner=tuner)
+    assert set(tuner.last_timings) == set(forms_for(db)) and f == min(tuner.last_timings,
+                                                                          key=tuner.last_timings.get)
+    again = FormTuner(cache_path=str(tmp_path / "tune.json"))
+    assert again.choose(s.ctx, db, q, m, k, T) == f and again.last_timings == {}  # from the cache
+    got_s, got_i = s.topk(db, q, m, k, T)
+    mis, une = oracle.scores(R, Q)
+    es, ei = oracle.topk(oracle.select(mis, une, modes), k, T)
+    assert np.array_equal(got_s.cpu().numpy().view(np.uint32), es) and np.array_equal(got_i.cpu().numpy(), ei)
+    B.fastid_set_form(s.ctx, B.FORM_TENSOR)

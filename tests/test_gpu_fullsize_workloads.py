@@ -111,7 +111,7 @@ def test_c4_batched_fullsize():
     seed, sizes, panels = bench._c4_batches(w)
     dbs, thrs, thr_devs = [], [], []
     for p, n_loci in enumerate(w["panels"]):
-        db, thr = bench.build_db(s, seed + 10 * p, w["n_refs"], n_loci, B.REFS_TENSOR, chunk=(1 << 28) // n_loci)
+        db, thr = bench.build_db(s, seed + 10 * p, w["n_refs"], n_loci, B.REFS_TENSOR | B.REFS_FP4, chunk=(1 << 28) // n_loci)
         dbs.append(db)
         thrs.append(thr)
         thr_devs.append(torch.from_numpy(thr.view(np.int32)).cuda())
