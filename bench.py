@@ -514,6 +514,12 @@ def run_gpu(args, w):
         line["serving"] = serving_measure(s, WORKLOADS["c5"], seconds=args.serving_seconds, warmup_seconds=2.0,
                                           slots=args.slots, max_wave=args.max_wave, hbm_budget=args.hbm_budget,
                                           clock_ms=args.clock_ms, server=args.server, parts=args.parts)
+        if args.server == "sweep":  # the same requests with one wave in flight at a time, for comparison
+            alt = serving_measure(s, WORKLOADS["c5"], seconds=args.serving_seconds, warmup_seconds=2.0, slots=1,
+                                  max_wave=args.max_wave, hbm_budget=args.hbm_budget, clock_ms=args.clock_ms,
+                                  server="waves")
+            line["serving"]["one_wave_in_flight"] = {"value": alt["value"], "latency_ms": alt["latency_ms"],
+                                                     "config": alt["config"], "clocks": alt["clocks"]}
         torch.cuda.empty_cache()
         line["batched"] = batched_measure(s, WORKLOADS["c4"], steps=args.batched_steps, warmup=3, e2e=False,
                                           probe=probe)
@@ -754,13 +760,17 @@ def run_c4(args, w):
 # Serving workload (configuration 5)
 # ----------------------------------------------------------------------------
 
-# Serving defaults: one wave in flight (a wave of up to 128 queries costs about
-# the same as a wave of one, so arrivals are best coalesced into the next wave)
-# of at most 256 queries (two query tiles), in a 4 GB budget.  Clocks are
-# sampled once a second: the serving window is latency-measured, and with the
-# 200 ms sampling of the device-timed configs some runs showed a 94-124 ms
-# stall (p99 23-25 ms) that runs sampled once a second did not (p99 15.7 ms).
-C5_DEFAULTS = dict(server="sweep", parts=4, slots=1, max_wave=256, hbm_budget=4 << 30, clock_ms=1000)
+# Serving defaults: waves join a running pass over the database's two halves
+# and share its launches (serve.SweepServer, parts=2), waves of at most 256
+# queries (two query tiles).  Measured at 200 requests/s against 20M x 2048
+# (FP4 AUTO, 10 s): p50 / p99 3.07 / 7.88 ms with 2 parts, 3.61 / 8.31 with 4,
+# 4.61 / 9.43 with 8; one wave in flight at a time (serve.Server, one slot)
+# 2.53 / 6.49 ms -- splitting a pass adds per-launch costs that earlier joining
+# does not repay at this load, and the line reports both.  The waves server's
+# budget is 4 GB.  Clocks are sampled once a second: the serving window is
+# latency-measured, and with the 200 ms sampling of the device-timed configs
+# some runs showed a 94-124 ms stall that runs sampled once a second did not.
+C5_DEFAULTS = dict(server="sweep", parts=2, slots=1, max_wave=256, hbm_budget=4 << 30, clock_ms=1000)
 
 
 def c5_requests(w, seed: int, horizon: float):

@@ -118,6 +118,14 @@ fastid_status fastid_destroy(fastid_ctx *ctx);
 /* Message describing the last failure on ctx ("" if none). */
 const char *fastid_last_error(const fastid_ctx *ctx);
 
+/* Device memory the context's calls take: the number of stream-ordered
+ * scratch allocations made from its memory pool since creation, and the
+ * pool's bytes in use and reserved now (any output may be NULL).  A
+ * diagnostic: it shows, for instance, that fastid_topk_noalloc takes none.
+ * Errors: EINVAL, ECUDA. */
+fastid_status fastid_memory_info(fastid_ctx *ctx, int64_t *pool_allocs, int64_t *pool_used_bytes,
+                                 int64_t *pool_reserved_bytes);
+
 /* Choose the compute form for later comparison calls (FASTID_FORM_*). */
 fastid_status fastid_set_form(fastid_ctx *ctx, int32_t form);
 
@@ -346,6 +354,23 @@ fastid_status fastid_topk_fold(fastid_ctx *ctx, uint32_t *run_scores_dev, int64_
                                const uint32_t *blk_scores_dev, const int64_t *blk_idx_dev, int64_t ref_offset,
                                int64_t n_q, int32_t k, fastid_stream stream);
 
+/*
+ * fastid_topk merged into running lists instead of written: for each query
+ * q, run[q] becomes the k smallest (score, reference index) pairs of run[q]
+ * and of this call's top-k against db, this call's indices taken + ref_offset
+ * (fastid_topk then fastid_topk_fold in one call, without the intermediate
+ * lists).  A pass over a database split into views (fastid_refs_view) is
+ * this call once per view, in any order, into the same lists.
+ *  ref_offset  0 .. 2^31 - 1 - db's reference count.
+ *  run_scores_dev uint32 [n_q][k], run_idx_dev int64 [n_q][k]: in/out, empty
+ *              slots (0xFFFFFFFF, -1) (an all-empty list is every byte 0xFF).
+ *  The other arguments are fastid_topk's.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+fastid_status fastid_topk_accumulate(fastid_ctx *ctx, const fastid_refdb *db, int64_t ref_offset,
+                                     const uint64_t *queries_dev, int64_t ld_q, int64_t n_q,
+                                     const uint8_t *modes_dev, int32_t k, uint32_t threshold,
+                                     uint32_t *run_scores_dev, int64_t *run_idx_dev, fastid_stream stream);
+
 /* ------------------------------------------------------------- diagnostics */
 /*
  * The library's bounded device wait, on a flag the caller owns: a one-thread
@@ -439,7 +464,11 @@ fastid_status fastid_plan_destroy(fastid_plan *plan);
  *  - The first call on a device looks up the array's device address there
  *    (and may make CUDA load that device code); make that first call before
  *    any stream capture.  The array stays resident on every device that used
- *    it until the process exits.
+ *    it until the process exits.  The address is kept per device, so after
+ *    cudaDeviceReset (or anything else that destroys the device's primary
+ *    context) later calls are invalid.
+ *  - While profiling is on (fastid_profile), the call records events around
+ *    its compare kernel like fastid_topk.
  *  - Every call uses the same array and it keeps the last call's contents
  *    (nothing in it needs to start at zero).  Calls whose kernels overlap on
  *    the GPU -- on different streams or host threads, or with different

@@ -172,3 +172,20 @@ def hits(score_rows: np.ndarray, threshold: int, ref_ids=None, query_ids=None):
     rid = rr.astype(np.int64) if ref_ids is None else np.asarray(ref_ids, np.int64)[rr]
     order = np.lexsort((rid, qid))
     return qid[order], rid[order], sc[order]
+
+
+def mixture_vs_mixture(known: np.ndarray, unknown: np.ndarray, threads: int = 0):
+    """Mixture-to-mixture comparison.  Sec. I names comparing mixtures with
+    mixtures as a use of the method but gives no score; the reading taken
+    here applies Eq. 1 with the known mixture K in the reference role:
+
+        containment[u, k] = sum_l AND(XOR(K_l, U_l), K_l)  (= popc(K AND NOT U))
+
+    the known mixture's minor alleles the unknown mixture U does not carry --
+    0 exactly when K's allele set lies inside U's, as it does whenever every
+    contributor of K also contributed to U -- and the symmetric
+    mismatch[u, k] = sum_l XOR(K_l, U_l) = containment(K, U) + containment(U, K).
+    known uint8 [n_k, N], unknown uint8 [n_u, N] (0/1, mixtures or
+    individuals).  Returns (containment, mismatch), uint32 [n_u, n_k]."""
+    mis, une = scores(known, unknown, threads)
+    return une, mis

@@ -53,6 +53,7 @@ _PROTOS = {
     "fastid_create": (_I32, [ctypes.POINTER(_P), _I32]),
     "fastid_destroy": (_I32, [_P]),
     "fastid_last_error": (ctypes.c_char_p, [_P]),
+    "fastid_memory_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "fastid_set_form": (_I32, [_P, _I32]),
     "fastid_sync_status": (_I32, [_P, _P]),
     "fastid_profile": (_I32, [_P, _I32]),
@@ -64,6 +65,7 @@ _PROTOS = {
     "fastid_free_refs": (_I32, [_P, _P]),
     "fastid_refs_view": (_I32, [_P, _P, _I64, _I64, ctypes.POINTER(_P)]),
     "fastid_topk_fold": (_I32, [_P, _P, _P, _P, _P, _I64, _I64, _I32, _P]),
+    "fastid_topk_accumulate": (_I32, [_P, _P, _I64, _P, _I64, _I64, _P, _I32, _U32, _P, _P, _P]),
     "fastid_refs_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32), ctypes.POINTER(_U32),
                                 ctypes.POINTER(_I64)]),
     "fastid_scores": (_I32, [_P, _P, _P, _I64, _I64, _P, _P, _I32, _I64, _P]),
@@ -223,6 +225,13 @@ def fastid_profile_read(ctx: Context, reset: bool = True) -> dict:
     return {"main_ms": ms.value, "main_launches": ml.value, "all_launches": al.value}
 
 
+def fastid_memory_info(ctx: Context) -> dict:
+    """{'pool_allocs', 'pool_used_bytes', 'pool_reserved_bytes'} of the context."""
+    a, u, r = _I64(), _I64(), _I64()
+    ctx.check(load_library().fastid_memory_info(ctx.handle, ctypes.byref(a), ctypes.byref(u), ctypes.byref(r)))
+    return {"pool_allocs": a.value, "pool_used_bytes": u.value, "pool_reserved_bytes": r.value}
+
+
 def fastid_save_refs(ctx: Context, db: RefDB, path: str) -> None:
     ctx.check(load_library().fastid_save_refs(ctx.handle, db.handle, os.fsencode(path)))
 
@@ -306,6 +315,25 @@ def fastid_topk_fold(ctx: Context, run_scores: torch.Tensor, run_idx: torch.Tens
         if n_q > 1 and t.stride(0) != k:
             raise ValueError("fold lists must be contiguous [n_q][k]")
     ctx.check(load_library().fastid_topk_fold(ctx.handle, rs, ri, bs, bi, ref_offset, n_q, k, _stream_ptr(stream)))
+
+
+def fastid_topk_accumulate(ctx: Context, db: RefDB, ref_offset: int, queries: torch.Tensor, modes: torch.Tensor,
+                           k: int, threshold: int, run_scores: torch.Tensor, run_idx: torch.Tensor,
+                           stream=None) -> None:
+    """fastid_topk against db merged into run's [n_q][k] lists (indices +
+    ref_offset), in place."""
+    q = _dev(queries, torch.int64, "queries", 2)
+    m = _dev(modes, torch.uint8, "modes", 1)
+    s = _dev(run_scores, torch.int32, "run_scores", 2)
+    i = _dev(run_idx, torch.int64, "run_idx", 2)
+    n_q = queries.size(0)
+    if modes.numel() != n_q or tuple(run_scores.shape) != (n_q, k) or tuple(run_idx.shape) != (n_q, k):
+        raise ValueError("modes / running lists do not match n_q x k")
+    for t in (run_scores, run_idx):
+        if n_q > 1 and t.stride(0) != k:
+            raise ValueError("running lists must be contiguous [n_q][k]")
+    ctx.check(load_library().fastid_topk_accumulate(ctx.handle, db.handle, ref_offset, q, _ld(queries), n_q, m, k,
+                                                    threshold, s, i, _stream_ptr(stream)))
 
 
 def fastid_scores(ctx: Context, db: RefDB, queries: torch.Tensor, modes: torch.Tensor, out: torch.Tensor,

@@ -48,7 +48,10 @@ struct Scratch {
     cudaStream_t s;
     void *p = nullptr;
     Scratch(fastid_ctx *c, cudaStream_t st) : ctx(c), s(st) {}
-    cudaError_t alloc(size_t bytes) { return cudaMallocFromPoolAsync(&p, bytes < 256 ? 256 : bytes, ctx->pool, s); }
+    cudaError_t alloc(size_t bytes) {
+        ++ctx->pool_allocs;
+        return cudaMallocFromPoolAsync(&p, bytes < 256 ? 256 : bytes, ctx->pool, s);
+    }
     ~Scratch() {
         if (p) cudaFreeAsync(p, s);
     }
@@ -81,32 +84,6 @@ fastid_status check_query_args(fastid_ctx *ctx, const fastid_refdb *db, const ui
     if (db->device != ctx->device) return fail(ctx, FASTID_EINVAL, "database belongs to another device");
     return FASTID_OK;
 }
-
-// Events around one main compare kernel (only while profiling).
-struct MainTimer {
-    fastid_ctx *ctx;
-    cudaStream_t s;
-    cudaEvent_t e1 = nullptr;
-    MainTimer(fastid_ctx *c, cudaStream_t st) : ctx(c), s(st) {
-        if (!ctx->profile) return;
-        if (ctx->events_used == ctx->events.size()) {
-            cudaEvent_t a, b;
-            if (cudaEventCreate(&a) != cudaSuccess) return;
-            if (cudaEventCreate(&b) != cudaSuccess) {
-                cudaEventDestroy(a);
-                return;
-            }
-            ctx->events.emplace_back(a, b);
-        }
-        auto &pr = ctx->events[ctx->events_used++];
-        cudaEventRecord(pr.first, s);
-        e1 = pr.second;
-    }
-    void done() {
-        if (e1) cudaEventRecord(e1, s);
-        e1 = nullptr;
-    }
-};
 
 void count_launches(fastid_ctx *ctx, int64_t n) { ctx->launches += n; }
 
@@ -224,6 +201,19 @@ fastid_status fastid_profile_read(fastid_ctx *ctx, double *main_ms, int64_t *mai
 }
 
 const char *fastid_last_error(const fastid_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+fastid_status fastid_memory_info(fastid_ctx *ctx, int64_t *pool_allocs, int64_t *pool_used_bytes,
+                                 int64_t *pool_reserved_bytes) {
+    if (!ctx) return FASTID_EINVAL;
+    if (pool_allocs) *pool_allocs = ctx->pool_allocs;
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    uint64_t used = 0, reserved = 0;
+    FASTID_CUDA(ctx, cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    FASTID_CUDA(ctx, cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+    if (pool_used_bytes) *pool_used_bytes = (int64_t)used;
+    if (pool_reserved_bytes) *pool_reserved_bytes = (int64_t)reserved;
+    return FASTID_OK;
+}
 
 fastid_status fastid_set_form(fastid_ctx *ctx, int32_t form) {
     if (!ctx) return FASTID_EINVAL;
@@ -641,10 +631,9 @@ fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_
                           int64_t n_q, const uint8_t *modes_dev, int32_t k, uint32_t threshold,
                           uint32_t *out_scores_dev, int64_t *out_idx_dev, fastid_stream stream) {
     FASTID_RANGE();
-    fastid_status st = check_query_args(ctx, db, queries_dev, ld_q, n_q, modes_dev);
+    fastid_status st = fastid::check_topk_args(ctx, db, queries_dev, ld_q, n_q, modes_dev, k, out_scores_dev,
+                                               out_idx_dev);
     if (st) return st;
-    if (k < 1 || k > FASTID_MAX_K) return fail(ctx, FASTID_EINVAL, "k out of range: %d", k);
-    if (n_q > 0 && (!out_scores_dev || !out_idx_dev)) return fail(ctx, FASTID_EINVAL, "output is NULL");
     int tensor;
     if ((st = pick_form(ctx, db, n_q, &tensor, k <= 16))) return st;
     if (n_q == 0) return FASTID_OK;
@@ -686,6 +675,65 @@ fastid_status fastid_topk(fastid_ctx *ctx, const fastid_refdb *db, const uint64_
     return FASTID_OK;
 }
 
+fastid_status fastid_topk_accumulate(fastid_ctx *ctx, const fastid_refdb *db, int64_t ref_offset,
+                                     const uint64_t *queries_dev, int64_t ld_q, int64_t n_q, const uint8_t *modes_dev,
+                                     int32_t k, uint32_t threshold, uint32_t *run_scores_dev, int64_t *run_idx_dev,
+                                     fastid_stream stream) {
+    FASTID_RANGE();
+    fastid_status st = fastid::check_topk_args(ctx, db, queries_dev, ld_q, n_q, modes_dev, k, run_scores_dev,
+                                               run_idx_dev);
+    if (st) return st;
+    if (ref_offset < 0 || ref_offset + db->n_refs > 0x7fffffffll)
+        return fail(ctx, FASTID_EINVAL, "ref_offset out of range: %lld", (long long)ref_offset);
+    int op;
+    if ((st = pick_form(ctx, db, n_q, &op, k <= 16))) return st;
+    if (n_q == 0) return FASTID_OK;
+    FASTID_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch scr(ctx, s);
+    if (op) {
+        TensorPrep tp;
+        size_t xo;
+        if ((st = prepare_tensor(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, EXTRA_TOPK, k, &xo, &tp, op)))
+            return st;
+        uint64_t *partial = at<uint64_t>(scr.p, xo);
+        tp.L.epi = EPI_TOPK;
+        tp.L.threshold = clamp_threshold(threshold, db->n_loci);
+        tp.L.k = k;
+        tp.L.partial = partial;
+        MainTimer tm(ctx, s);
+        FASTID_CUDA(ctx, launch_tensor_multi(256, tp.L, s));
+        tm.done();
+        FASTID_CUDA(ctx, launch_merge_sched(partial, tp.L, nullptr, n_q, run_scores_dev, run_idx_dev, s, true,
+                                            ref_offset));
+        count_launches(ctx, 2);
+        return FASTID_OK;
+    }
+    // plain form: the call's lists in scratch, then folded
+    const int64_t n_q_pad = round_up(n_q, PL_TQ);
+    Partition part = make_partition((int32_t)(n_q_pad / PL_TQ), db->n_pad / PL_TR, ctx->grid_topk);
+    const size_t partial_elems = (size_t)part.grid * part.max_seg * PL_TQ * k;
+    PreparedQueries pq;
+    size_t xo;
+    if ((st = prepare(ctx, db, queries_dev, ld_q, n_q, modes_dev, s, scr, partial_elems * 8 + (size_t)n_q * k * 12 + 512,
+                      &xo, &pq)))
+        return st;
+    uint64_t *partial = at<uint64_t>(scr.p, xo);
+    uint8_t *lists = reinterpret_cast<uint8_t *>(partial + partial_elems);
+    lists += (256 - reinterpret_cast<uintptr_t>(lists) % 256) % 256;
+    uint32_t *blk_s = reinterpret_cast<uint32_t *>(lists);
+    int64_t *blk_i = reinterpret_cast<int64_t *>(lists + (((size_t)n_q * k * 4 + 255) & ~size_t(255)));
+    MainTimer tm(ctx, s);
+    FASTID_CUDA(ctx, launch_plain(EPI_TOPK, (const uint32_t *)db->packed, db->norms, db->n_refs, db->ld64 * 2,
+                                  db->n_words64 * 2, pq.q32, pq.coef, n_q, threshold, k, nullptr, 0, 0, nullptr,
+                                  nullptr, nullptr, nullptr, partial, part, ctx->dev_status, s));
+    tm.done();
+    FASTID_CUDA(ctx, launch_topk_merge(partial, part, n_q, k, blk_s, blk_i, s));
+    FASTID_CUDA(ctx, launch_topk_fold(run_scores_dev, run_idx_dev, blk_s, blk_i, ref_offset, n_q, k, s));
+    count_launches(ctx, 3);
+    return FASTID_OK;
+}
+
 fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev, int64_t ld_q,
                              int64_t n_q, const uint8_t *modes_dev, uint32_t threshold, int64_t capacity,
                              int64_t *hit_q_dev, int64_t *hit_r_dev, uint32_t *hit_score_dev,
@@ -721,6 +769,36 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
 }  // extern "C"
 
 namespace fastid {
+
+fastid_status check_topk_args(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q, int64_t ld_q, int64_t n_q,
+                              const uint8_t *modes, int32_t k, const void *out_scores, const void *out_idx) {
+    fastid_status st = check_query_args(ctx, db, q, ld_q, n_q, modes);
+    if (st) return st;
+    if (k < 1 || k > FASTID_MAX_K) return fail(ctx, FASTID_EINVAL, "k out of range: %d", k);
+    if (n_q > 0 && (!out_scores || !out_idx)) return fail(ctx, FASTID_EINVAL, "output is NULL");
+    return FASTID_OK;
+}
+
+MainTimer::MainTimer(fastid_ctx *c, cudaStream_t st) : ctx(c), s(st) {
+    if (!ctx->profile) return;
+    if (ctx->events_used == ctx->events.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return;
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return;
+        }
+        ctx->events.emplace_back(a, b);
+    }
+    auto &pr = ctx->events[ctx->events_used++];
+    cudaEventRecord(pr.first, s);
+    e1 = pr.second;
+}
+
+void MainTimer::done() {
+    if (e1) cudaEventRecord(e1, s);
+    e1 = nullptr;
+}
 
 int pick_operand(int form, bool has_fp8, bool has_fp4, int64_t n_q, bool slots16) {
     (void)slots16;

@@ -234,9 +234,12 @@ cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s
 // snap[0..3] = status[0..3], status cleared, atomically per word (diag.cu).
 cudaError_t launch_status_take(uint32_t *status, uint32_t *snap, cudaStream_t s);
 // Merge of per-slot lists for the queries of a tensor launch (jobs == nullptr:
-// one panel, query q's output is out_scores/out_idx row q).
+// one panel, query q's output is out_scores/out_idx row q).  accumulate:
+// merge into the output lists (reference indices + ref_offset) instead of
+// overwriting them.
 cudaError_t launch_merge_sched(const uint64_t *partial, const TcLaunch &L, const MergeJob *jobs, int64_t n_jobs,
-                               uint32_t *out_scores, int64_t *out_idx, cudaStream_t s);
+                               uint32_t *out_scores, int64_t *out_idx, cudaStream_t s, bool accumulate = false,
+                               int64_t ref_offset = 0);
 // Fold one streamed block's [n_q][k] lists (indices + offset) into the
 // running [n_q][k] lists.
 cudaError_t launch_topk_fold(uint32_t *run_s, int64_t *run_i, const uint32_t *blk_s, const int64_t *blk_i,

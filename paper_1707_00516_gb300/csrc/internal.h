@@ -38,6 +38,7 @@ struct fastid_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     size_t events_used = 0;
     int64_t launches = 0;
+    int64_t pool_allocs = 0;  // stream-ordered scratch allocations from `pool` (fastid_memory_info)
 };
 
 struct fastid_refdb {
@@ -89,6 +90,22 @@ __host__ __device__ inline bool op_f4(int op) { return op == OP_FP4 || op == OP_
 // copy wins from two query tiles on.
 constexpr int64_t AUTO_FP4_PACKED_MAX_Q = 128;
 int pick_operand(int form, bool has_fp8, bool has_fp4, int64_t n_q, bool slots16 = true);
+
+// Argument checks of the top-k entry points (fastid_topk, fastid_topk_noalloc,
+// fastid_topk_accumulate): the shared query arguments, k, and the two output
+// buffers.  Sets ctx->last_error and returns EINVAL on a bad argument.
+fastid_status check_topk_args(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *q, int64_t ld_q, int64_t n_q,
+                              const uint8_t *modes, int32_t k, const void *out_scores, const void *out_idx);
+
+// Events around one main compare kernel on stream `st`, recorded only while
+// profiling is on (fastid_profile); no device memory is allocated.
+struct MainTimer {
+    fastid_ctx *ctx;
+    cudaStream_t s;
+    cudaEvent_t e1 = nullptr;
+    MainTimer(fastid_ctx *c, cudaStream_t st);
+    void done();
+};
 
 // The hit-list half of fastid_compare: every (q, r) with score <= threshold of
 // this call is appended at atomicAdd(count) (stored while < capacity),

@@ -15,7 +15,9 @@
 // and keeps it; that lookup may also make CUDA load this file's device code on
 // the device (lazy module loading), so the first call on a device should come
 // before any stream capture.  The array then stays resident on every device that has
-// used it until the process exits.
+// used it until the process exits.  The kept address belongs to the device's
+// primary context: after cudaDeviceReset (or anything else that destroys that
+// context) it is stale, and later calls must not be made.
 //
 // All calls share the array and it keeps whatever the last call left in it.
 // Nothing in it needs to start at zero: every word a call reads was written
@@ -70,14 +72,9 @@ extern "C" fastid_status fastid_topk_noalloc(fastid_ctx *ctx, const fastid_refdb
                                              fastid_stream stream) {
     FASTID_RANGE();
     using namespace fastid;
-    if (!ctx) return FASTID_EINVAL;
-    if (!db) return set_error(ctx, FASTID_EINVAL, "database is NULL");
-    if (n_q < 0 || n_q > 0x7fffffffll) return set_error(ctx, FASTID_EINVAL, "n_q out of range");
-    if (n_q > 0 && (!queries_dev || !modes_dev)) return set_error(ctx, FASTID_EINVAL, "queries or modes is NULL");
-    if (ld_q < db->n_words64) return set_error(ctx, FASTID_EINVAL, "ld_q smaller than the database's word count");
-    if (db->device != ctx->device) return set_error(ctx, FASTID_EINVAL, "database belongs to another device");
-    if (k < 1 || k > FASTID_MAX_K) return set_error(ctx, FASTID_EINVAL, "k out of range");
-    if (n_q > 0 && (!out_scores_dev || !out_idx_dev)) return set_error(ctx, FASTID_EINVAL, "output is NULL");
+    // the same argument checks and messages as fastid_topk
+    fastid_status st0 = check_topk_args(ctx, db, queries_dev, ld_q, n_q, modes_dev, k, out_scores_dev, out_idx_dev);
+    if (st0 != FASTID_OK) return st0;
     if (n_q == 0) return FASTID_OK;
 
     // Scratch layout: padded queries, coefficients, per-segment top-k lists.
@@ -109,9 +106,11 @@ extern "C" fastid_status fastid_topk_noalloc(fastid_ctx *ctx, const fastid_refdb
 
     e = launch_query_prep(queries_dev, ld_q, n_q, db->n_words64, modes_dev, q32, n_q_pad, ld32, coef, s);
     if (e != cudaSuccess) return cuda_error(ctx, e, "query preparation");
+    MainTimer tm(ctx, s);  // profiling events, as around fastid_topk's compare kernel
     e = launch_plain(EPI_TOPK, (const uint32_t *)db->packed, db->norms, db->n_refs, ld32, db->n_words64 * 2, q32,
                      coef, n_q, threshold, k, nullptr, 0, 0, nullptr, nullptr, nullptr, nullptr, partial, part,
                      ctx->dev_status, s);
+    tm.done();
     if (e != cudaSuccess) return cuda_error(ctx, e, "plain compare kernel");
     e = launch_topk_merge(partial, part, n_q, k, out_scores_dev, out_idx_dev, s);
     if (e != cudaSuccess) return cuda_error(ctx, e, "top-k merge");

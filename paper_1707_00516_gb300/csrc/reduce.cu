@@ -76,6 +76,10 @@ struct MergeSched {
     TcSched sc[TC_MAXP];
     int64_t n_slots;   // slots in partial (checked by debug builds)
     uint32_t *status;  // the context's status word
+    // accumulate: merge into the output lists instead of overwriting them,
+    // this launch's reference indices taken + ref_offset
+    int32_t accumulate;
+    int64_t ref_offset;
 };
 
 // Debug builds (FASTID_DEBUG) check every slot a merge reads against the
@@ -132,6 +136,16 @@ __global__ void topk_merge_sched_kernel(const uint64_t *__restrict__ partial, co
         const int64_t slot = (int64_t)sc.slot0 + (int64_t)sc.a * sc.b * cpg * sc.tpx + (t * cpg + rank) * sc.t_tpx + lt;
         uint64_t v = lane < k && merge_slot_ok(M, slot) ? partial[(slot * k + lane) * TC_TILE_Q + ql] : KEY_EMPTY;
         acc = warp_merge32(acc, v, lane);
+    }
+    if (M.accumulate) {
+        // keys are (score << 32) | r: the offset moves r, never the score (r + offset < 2^32)
+        if (acc != KEY_EMPTY) acc += (uint64_t)M.ref_offset;
+        uint64_t run = KEY_EMPTY;
+        if (lane < k) {
+            const int64_t ri = jb.out_i[lane];
+            if (ri >= 0) run = make_key(jb.out_s[lane], (uint32_t)ri);
+        }
+        acc = warp_merge32(acc, run, lane);
     }
     if (lane < k) {
         jb.out_s[lane] = acc == KEY_EMPTY ? 0xFFFFFFFFu : (uint32_t)(acc >> 32);
@@ -332,9 +346,12 @@ cudaError_t launch_topk_merge_tile(const uint64_t *partial, const Partition &par
 }
 
 cudaError_t launch_merge_sched(const uint64_t *partial, const TcLaunch &L, const MergeJob *jobs, int64_t n_jobs,
-                               uint32_t *out_scores, int64_t *out_idx, cudaStream_t s) {
+                               uint32_t *out_scores, int64_t *out_idx, cudaStream_t s, bool accumulate,
+                               int64_t ref_offset) {
     if (n_jobs == 0) return cudaSuccess;
     MergeSched M;
+    M.accumulate = accumulate ? 1 : 0;
+    M.ref_offset = ref_offset;
     M.n_panels = L.n_panels;
     M.pair = L.pair;
     M.k = L.k;

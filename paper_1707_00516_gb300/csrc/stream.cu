@@ -71,7 +71,10 @@ struct StreamState {
     }
     void *take(size_t bytes, cudaError_t &e) {
         void *p = nullptr;
-        if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&p, bytes < 256 ? 256 : bytes, ctx->pool, s);
+        if (e == cudaSuccess) {
+            ++ctx->pool_allocs;
+            e = cudaMallocFromPoolAsync(&p, bytes < 256 ? 256 : bytes, ctx->pool, s);
+        }
         return e == cudaSuccess ? p : nullptr;
     }
     void *take_extra(size_t bytes, cudaError_t &e) {

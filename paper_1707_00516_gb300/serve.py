@@ -224,9 +224,9 @@ class SweepServer:
     The database is split into `parts` row ranges (fastid_refs_view).  While
     any request is in flight, a dispatcher thread runs one *step* after
     another on its stream: a step compares ONE part against the queries of
-    every active wave -- in one fastid_topk launch over the ring rows they
-    occupy -- and folds the part's lists into each query's running list
-    (fastid_topk_fold, an exact (score, reference) merge).  Requests that
+    every active wave -- one fastid_topk_accumulate over the ring rows they
+    occupy: one comparison launch, whose merge folds the part's lists into
+    each query's running list (an exact (score, reference) merge).  Requests that
     arrive meanwhile are admitted together, as one new wave, into the next
     step, whichever part that is: a pass may start at any part boundary and
     wrap round.  A wave leaves after `parts` steps, having met every part
@@ -268,8 +268,6 @@ class SweepServer:
         self.d_m = torch.zeros(C, dtype=torch.uint8, device=dev)
         self.run_s = torch.empty((C, k), dtype=torch.int32, device=dev)
         self.run_i = torch.empty((C, k), dtype=torch.int64, device=dev)
-        self.seg_s = torch.empty((C, k), dtype=torch.int32, device=dev)
-        self.seg_i = torch.empty((C, k), dtype=torch.int64, device=dev)
         self.h_q = torch.empty((C, self.words), dtype=torch.int64, pin_memory=True)
         self.h_m = torch.empty(C, dtype=torch.uint8, pin_memory=True)
         self.h_s = torch.empty((C, k), dtype=torch.int32, pin_memory=True)
@@ -432,10 +430,9 @@ class SweepServer:
                     if ev0 is not None:
                         ev0.record(self.stream)
                     for a, b in self._spans(active):
-                        B.fastid_topk(self.ctx, self.views[part], self.d_q[a:b], self.d_m[a:b], self.k,
-                                      self.threshold, self.seg_s[a:b], self.seg_i[a:b], stream=self.stream)
-                        B.fastid_topk_fold(self.ctx, self.run_s[a:b], self.run_i[a:b], self.seg_s[a:b],
-                                           self.seg_i[a:b], r0, stream=self.stream)
+                        B.fastid_topk_accumulate(self.ctx, self.views[part], r0, self.d_q[a:b], self.d_m[a:b],
+                                                 self.k, self.threshold, self.run_s[a:b], self.run_i[a:b],
+                                                 stream=self.stream)
                     ev = torch.cuda.Event(enable_timing=self.trace is not None)
                     ev.record(self.stream)
                     if ev0 is not None:

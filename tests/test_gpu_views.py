@@ -1,4 +1,5 @@
-"""Row-range views of a database and the fold of per-part top-k lists: the
+"""Row-range views of a database and the fold of per-part top-k lists
+(fastid_topk_fold, and fastid_topk_accumulate which fuses the two): the
 parts of one pass, compared in any order and folded, give exactly the
 oracle's top-k over the whole database, in every compute form."""
 import numpy as np
@@ -46,15 +47,21 @@ def test_views_folded_equal_whole(case, form, k, T):
     n_q = Q.shape[0]
     run_s = torch.full((n_q, k), -1, dtype=torch.int32, device="cuda")
     run_i = torch.full((n_q, k), -1, dtype=torch.int64, device="cuda")
+    acc_s = run_s.clone()
+    acc_i = run_i.clone()
     for p in (2, 0, 1):
         sc, ix = s.topk(views[p], q, m, k, T)
         B.fastid_topk_fold(s.ctx, run_s, run_i, sc, ix, bounds[p][0])
+    for p in (1, 2, 0):  # the fused form, another order
+        B.fastid_topk_accumulate(s.ctx, views[p], bounds[p][0], q, m, k, T, acc_s, acc_i)
     whole_s, whole_i = s.topk(db, q, m, k, T)
     torch.cuda.synchronize()
     assert B.fastid_sync_status(s.ctx) == B.OK
     es, ei = oracle.topk(exp, k, T)
     assert np.array_equal(run_s.cpu().numpy().view(np.uint32), es)
     assert np.array_equal(run_i.cpu().numpy(), ei)
+    assert np.array_equal(acc_s.cpu().numpy().view(np.uint32), es)
+    assert np.array_equal(acc_i.cpu().numpy(), ei)
     assert np.array_equal(whole_s.cpu().numpy().view(np.uint32), es)
     assert np.array_equal(whole_i.cpu().numpy(), ei)
     # a view's own hit list and full matrix, indices relative to the view

@@ -67,11 +67,13 @@ def test_null_context_is_einval(lib):
     assert lib.fastid_free_refs(P, P) == B.OK
     assert lib.fastid_refs_view(P, P, 0, 1, None) == B.EINVAL
     assert lib.fastid_topk_fold(P, P, P, P, P, 0, 1, 16, P) == B.EINVAL
+    assert lib.fastid_topk_accumulate(P, P, 0, P, 1, 1, P, 16, 0, P, P, P) == B.EINVAL
     assert lib.fastid_refs_info(P, None, None, None, None) == B.EINVAL
     assert lib.fastid_scores(P, P, P, 1, 1, P, P, 4, 1, P) == B.EINVAL
     assert lib.fastid_topk(P, P, P, 1, 1, P, 16, 0, P, P, P) == B.EINVAL
     assert lib.fastid_compare(P, P, P, 1, 1, P, 0, 0, P, P, P, P, P) == B.EINVAL
     assert lib.fastid_last_error(P) == b""
+    assert lib.fastid_memory_info(P, None, None, None) == B.EINVAL
 
 
 def test_library_missing_fails_loudly(tmp_path, monkeypatch):

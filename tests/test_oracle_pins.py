@@ -217,3 +217,33 @@ def test_hits_against_python():
     q, r, v = oracle.hits(s, 1)
     exp = [(a, b, int(s[a, b])) for a in range(9) for b in range(40) if s[a, b] <= 1]
     assert list(zip(q.tolist(), r.tolist(), v.tolist())) == exp
+
+
+# --- mixture to mixture (Sec. I; Eq. 1 with a known mixture as reference) ----
+
+def test_mixture_pairs_hand_worked(golden_dir):
+    for line in open(os.path.join(golden_dir, "mixture_pairs.txt")):
+        line = line.split("#", 1)[0].split(";", 1)[0].strip()
+        if not line:
+            continue
+        k, u, mis, cont = line.split()
+        c, m = oracle.mixture_vs_mixture(_profile(k)[None], _profile(u)[None])
+        assert (m[0, 0], c[0, 0]) == (int(mis), int(cont)), line
+
+
+def test_mixture_containment_by_contributor_sets():
+    """Brute force over every pair of contributor subsets of a small pool:
+    whenever K's contributors are a subset of U's the containment score is 0;
+    the mismatch is the two one-sided scores' sum."""
+    rng = np.random.default_rng(77)
+    pool = (rng.random((5, 40)) < 0.3).astype(np.uint8)
+    subsets = [s for n in range(1, 6) for s in itertools.combinations(range(5), n)]
+    mixes = np.stack([np.bitwise_or.reduce(pool[list(s)], axis=0) for s in subsets])
+    cont, mis = oracle.mixture_vs_mixture(mixes, mixes)
+    for iu, su in enumerate(subsets):
+        for ik, sk in enumerate(subsets):
+            if set(sk) <= set(su):
+                assert cont[iu, ik] == 0
+            assert mis[iu, ik] == cont[iu, ik] + cont[ik, iu]
+            # brute force over loci
+            assert cont[iu, ik] == int(np.sum((mixes[ik] == 1) & (mixes[iu] == 0)))

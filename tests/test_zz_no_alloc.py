@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import gen
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -26,7 +27,7 @@ def env():
     thr = gen.maf_thresholds(seed, n_loci)
     R = gen.allele_rows(seed, gen.STREAM_DB, np.arange(n_refs), thr)
     db = s.load_refs_alleles(torch.from_numpy(R).cuda(), n_loci)
-    yield B, s, db, thr, n_refs, n_loci, seed
+    yield B, s, db, thr, n_refs, n_loci, seed, R
     db.close()
     s.ctx.close()
 
@@ -47,7 +48,7 @@ def _run(B, fn, s, db, q, modes, k, T):
 
 
 def test_noalloc_matches_topk_on_consecutive_calls(env):
-    B, s, db, thr, n_refs, n_loci, seed = env
+    B, s, db, thr, n_refs, n_loci, seed, R = env
     # two different query sets, so the second call runs over the first call's
     # leftovers in the shared array
     rec_a = gen.concat_recipes(gen.recipe_individuals(150, n_refs, n_loci, seed, n_planted=40),
@@ -63,10 +64,44 @@ def test_noalloc_matches_topk_on_consecutive_calls(env):
         for j in range(rec.n_queries):
             for r in rec.planted(j):
                 assert r in got_ix[j]
+    # the second call ran over the first call's leftovers: check it against
+    # the oracle directly as well
+    Q = oracle.mix(gen.source_alleles(rec_b, thr), rec_b.offsets)
+    mis, une = oracle.scores(R, Q)
+    es, ei = oracle.topk(oracle.select(mis, une, rec_b.modes), 16, 60)
+    assert np.array_equal(got_sc.view(np.uint32), es)
+    assert np.array_equal(got_ix, ei)
+
+
+def test_noalloc_allocates_nothing(env):
+    """After the first call on the device (which looks up the array's
+    address), calls take nothing from the context's memory pool and leave
+    the device's free memory unchanged, while fastid_topk does take pool
+    scratch."""
+    B, s, db, thr, n_refs, n_loci, seed, R = env
+    rec = gen.recipe_mixtures(200, n_refs, n_loci, seed, 2, 5, salt=0xA1)
+    q, modes = _queries(s, rec, thr, n_loci)
+    sc = torch.empty((q.shape[0], 32), dtype=torch.int32, device="cuda")
+    ix = torch.empty((q.shape[0], 32), dtype=torch.int64, device="cuda")
+    B.fastid_topk_noalloc(s.ctx, db, q, modes, 32, B.NO_THRESHOLD, sc, ix)
+    torch.cuda.synchronize()
+    before = B.fastid_memory_info(s.ctx)
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        B.fastid_topk_noalloc(s.ctx, db, q, modes, 32, B.NO_THRESHOLD, sc, ix)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    after = B.fastid_memory_info(s.ctx)
+    assert after["pool_allocs"] == before["pool_allocs"]
+    assert after["pool_used_bytes"] == before["pool_used_bytes"]
+    assert free1 == free0
+    B.fastid_topk(s.ctx, db, q, modes, 32, B.NO_THRESHOLD, sc, ix)
+    torch.cuda.synchronize()
+    assert B.fastid_memory_info(s.ctx)["pool_allocs"] > after["pool_allocs"]
 
 
 def test_noalloc_rejects_oversized_request(env):
-    B, s, db, thr, n_refs, n_loci, seed = env
+    B, s, db, thr, n_refs, n_loci, seed, R = env
     # 70,000 padded queries x 1024 bits of loci = 8.96 MB of padded queries
     # alone, plus the lists: over the fixed 16 MiB
     n_q = 70000
