@@ -503,6 +503,7 @@ def run_gpu(args, w):
                             "popc_per_clk_sm": probe["popc"]["per_clk_sm"],
                             "lop3_per_clk_sm": probe["lop3"]["per_clk_sm"],
                             "and_popc_iadd3_popc_per_clk_sm": probe["and_popc_add"]["per_clk_sm"],
+                            "harley_seal_word_pairs_per_clk_sm": probe["harley_seal"]["per_clk_sm"],
                             "b1_mma_bit_macs_per_clk_sm": probe["b1_and_popc"]["bit_macs_per_clk_sm"]}}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, recipe, thr)
@@ -705,7 +706,8 @@ def batched_measure(s, w, steps: int, warmup: int, e2e: bool = True, probe: dict
     value = pairs * steps / (total_ms / 1e3)
     from paper_1707_00516_gb300 import peaks as P
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp4 = bs.variant in (B.VARIANT_TENSOR_FP4, B.VARIANT_TENSOR_FP4_PAIR)
+    from paper_1707_00516_gb300.tune import FP4_VARIANTS
+    fp4 = bs.variant in FP4_VARIANTS
     peak, unit, how = roof_peak("fp4" if fp4 else "fp8", probe if probe is not None else P.measure(), n_sms)
     achieved = flops * steps / (total_ms / 1e3) / 1e12
     info = bs.plan.info()

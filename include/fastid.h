@@ -427,7 +427,11 @@ enum {
     FASTID_VARIANT_TENSOR_N128 = 2, /* FP8, 128 x 128 tiles, 6-stage pipeline  */
     FASTID_VARIANT_TENSOR_PAIR = 3, /* FP8, 2-CTA clusters on tile pairs sharing reference stages */
     FASTID_VARIANT_TENSOR_FP4 = 4,  /* FP4 (block-scaled e2m1), 128 x 224 tiles, 5-stage pipeline */
-    FASTID_VARIANT_TENSOR_FP4_PAIR = 5 /* FP4, 2-CTA clusters on tile pairs                     */
+    FASTID_VARIANT_TENSOR_FP4_PAIR = 5, /* FP4, 2-CTA clusters on tile pairs                    */
+    FASTID_VARIANT_TENSOR_PAIR_2SM = 6, /* FP8 tile pairs as one 2-SM MMA (tcgen05 cta_group::2,
+                                           M = 256): each CTA holds half of every reference
+                                           stage, 7 stages                                    */
+    FASTID_VARIANT_TENSOR_FP4_PAIR_2SM = 7 /* FP4 tile pairs as one 2-SM MMA                   */
 };
 
 fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs, int32_t n_panels,

@@ -29,7 +29,7 @@ NO_THRESHOLD = 0xFFFFFFFF
 NOALLOC_SCRATCH_BYTES = 16 << 20
 VIEW_ALIGN = 256
 (VARIANT_AUTO, VARIANT_TENSOR_N256, VARIANT_TENSOR_N128, VARIANT_TENSOR_PAIR, VARIANT_TENSOR_FP4,
- VARIANT_TENSOR_FP4_PAIR) = range(6)
+ VARIANT_TENSOR_FP4_PAIR, VARIANT_TENSOR_PAIR_2SM, VARIANT_TENSOR_FP4_PAIR_2SM) = range(8)
 
 _lib = None
 _lock = threading.Lock()

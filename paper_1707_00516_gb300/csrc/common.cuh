@@ -123,6 +123,7 @@ struct TcLaunch {
     int32_t pair;  // 2-CTA clusters sharing reference stages (groups are clusters, tiles are pairs)
     int32_t pk;    // packed references expanded on chip (map_b over the packed rows; FP8 queries at half scale)
     int32_t f4;    // block-scaled FP4 operands (224-reference tiles); else FP8
+    int32_t cg2;   // paired launches: one 2-SM MMA per pair (cta_group::2); else multicast stages
     CUtensorMap map_a[TC_MAXP];
     CUtensorMap map_b[TC_MAXP];
     int64_t n_refs[TC_MAXP];

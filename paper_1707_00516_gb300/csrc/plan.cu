@@ -84,7 +84,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
         return perr(ctx, FASTID_EINVAL, "n_panels must be in 1..8 with a database per panel");
     if (n_batches < 0 || (n_batches > 0 && !batches)) return perr(ctx, FASTID_EINVAL, "bad batch list");
     if (k < 1 || k > FASTID_MAX_K) return perr(ctx, FASTID_EINVAL, "k out of range");
-    if (variant < FASTID_VARIANT_AUTO || variant > FASTID_VARIANT_TENSOR_FP4_PAIR)
+    if (variant < FASTID_VARIANT_AUTO || variant > FASTID_VARIANT_TENSOR_FP4_PAIR_2SM)
         return perr(ctx, FASTID_EINVAL, "unknown variant");
     bool all_fp8 = true, all_fp4 = true;
     for (int p = 0; p < n_panels; ++p) {
@@ -96,8 +96,11 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     if (variant == FASTID_VARIANT_AUTO)  // the FP4 copies when every panel has one, paired when clusters run
         variant = all_fp4 ? (ctx->pair_clusters > 0 ? FASTID_VARIANT_TENSOR_FP4_PAIR : FASTID_VARIANT_TENSOR_FP4)
                           : FASTID_VARIANT_TENSOR_N256;
-    const bool f4 = variant == FASTID_VARIANT_TENSOR_FP4 || variant == FASTID_VARIANT_TENSOR_FP4_PAIR;
-    if ((variant == FASTID_VARIANT_TENSOR_PAIR || variant == FASTID_VARIANT_TENSOR_FP4_PAIR) && ctx->pair_clusters < 1)
+    const bool f4 = variant == FASTID_VARIANT_TENSOR_FP4 || variant == FASTID_VARIANT_TENSOR_FP4_PAIR ||
+                    variant == FASTID_VARIANT_TENSOR_FP4_PAIR_2SM;
+    const bool paired = variant == FASTID_VARIANT_TENSOR_PAIR || variant == FASTID_VARIANT_TENSOR_FP4_PAIR ||
+                        variant == FASTID_VARIANT_TENSOR_PAIR_2SM || variant == FASTID_VARIANT_TENSOR_FP4_PAIR_2SM;
+    if (paired && ctx->pair_clusters < 1)
         return perr(ctx, FASTID_EUNSUPPORTED, "paired launches need 2-CTA clusters");
     if (f4 && !all_fp4)
         return perr(ctx, FASTID_EUNSUPPORTED, "FP4 plan variants read the FP4 copy: load every panel with "
@@ -125,7 +128,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     P->k = k;
     P->threshold = threshold;
     const int BN = P->bn;
-    const int pair = (variant == FASTID_VARIANT_TENSOR_PAIR || variant == FASTID_VARIANT_TENSOR_FP4_PAIR) ? 1 : 0;
+    const int pair = paired ? 1 : 0;
     // operand row bytes of each panel (FP8: a byte per locus; FP4: two loci a byte)
     auto kbytes = [&](int p) { return (int64_t)(f4 ? dbs[p]->kbytes4 : dbs[p]->kpad); };
     const int64_t tq = (int64_t)TC_TILE_Q * (pair ? 2 : 1);  // operand rows per tile (pair)
@@ -144,6 +147,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
     TcLaunch &L = P->launch;
     memset(&L, 0, sizeof L);
     L.pair = pair;
+    L.cg2 = variant == FASTID_VARIANT_TENSOR_PAIR_2SM || variant == FASTID_VARIANT_TENSOR_FP4_PAIR_2SM ? 1 : 0;
     L.f4 = f4 ? 1 : 0;
     L.n_groups = make_tensor_schedule(n_panels, n_qq.data(), n_rt.data(), tile_bytes.data(),
                                       pair ? ctx->pair_clusters : ctx->grid_tensor, pair ? 2 : 1, L.sched,

@@ -69,10 +69,12 @@ constexpr uint64_t RENDEZVOUS_NS = 50000000ull;  // 50 ms per panel entry, then 
 //   BN = 224: 28 KB reference stage, 5 stages (4 with a packed stage), 2 x 224
 //             TMEM columns + scale factors (FP4)
 //   BN = 128: 16 KB reference stage, 6 stages, 2 x 128 TMEM columns
-template <int BN, bool PK = false>
+//   CG2 (2-SM MMA, see tensor_kernel): each CTA holds half of every reference
+//             stage, 7 stages (FP8 32 KB, FP4 30 KB a stage)
+template <int BN, bool PK = false, bool CG2 = false>
 struct TcShape {
-    static constexpr int STAGES = BN == 128 ? 6 : (BN == 224 && !PK) ? 5 : 4;
-    static constexpr uint32_t B_BYTES = (uint32_t)BN * TC_BK;
+    static constexpr int STAGES = CG2 ? 7 : BN == 128 ? 6 : (BN == 224 && !PK) ? 5 : 4;
+    static constexpr uint32_t B_BYTES = (uint32_t)(CG2 ? BN / 2 : BN) * TC_BK;
     static constexpr uint32_t TMEM_COLS = BN == 128 ? 256 : 512;
 };
 
@@ -221,25 +223,45 @@ __device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t ctamask) {
         : "memory");
 }
 
-__device__ __forceinline__ void tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
+// ---- 2-SM (cta_group::2) forms: the MMA of a CTA pair issued by its even
+// CTA, M = 256 rows (128 in each CTA's shared memory and TMEM), the
+// reference operand split along N (half in each CTA's shared memory) ----
+
+// Address of the same shared-memory object in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// Arrive on an mbarrier of (possibly) another CTA of the cluster, release
+// ordering at cluster scope (bar: a shared::cluster address).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// TMA load into this CTA's shared memory whose completion counts on the
+// mbarrier `bar` of either CTA of the pair (a shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_cg2(uint32_t dst, const CUtensorMap *map, uint32_t bar, int32_t x,
+                                                int32_t y) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
 
-// Block-scaled FP4: scale factors of A and B read from TMEM at sfa / sfb.
-__device__ __forceinline__ void tc_mma_f4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+// Arrive on the mbarrier at the same offset in every CTA of ctamask when this
+// thread's prior cta_group::2 tcgen05 operations complete.
+__device__ __forceinline__ void tc_commit_cg2_mc(uint32_t bar, uint16_t ctamask) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %6, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(ctamask)
         : "memory");
+}
+
+__device__ __forceinline__ void tc_commit_cg2(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 // 32 lanes x 16 consecutive 32-bit columns, every column the value v.
@@ -249,6 +271,55 @@ __device__ __forceinline__ void tmem_fill16(uint32_t taddr, uint32_t v) {
         "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
         "r"(v)
         : "memory");
+}
+
+// The 4 MMAs of one 128-byte K stage into accumulator d: operand descriptors
+// +0, +2, +4, +6 (32 bytes of K each in the address field), the first MMA
+// accumulating only when acc != 0, the others always; one asm block with its
+// predicates set once.  At FP4 speed a stage is ~450 cycles of MMA work, and
+// the issuing thread's own instruction path per stage (waits, descriptors,
+// issue, commit) bounds the MMA rate, so it is kept this short.
+template <bool F4, bool CG2>
+__device__ __forceinline__ void mma_stage4(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t sfa,
+                                           uint32_t sfb, uint32_t acc) {
+    const uint64_t a1 = ad + 2u, a2 = ad + 4u, a3 = ad + 6u, b1 = bd + 2u, b2 = bd + 4u, b3 = bd + 6u;
+    if constexpr (F4) {
+#define FASTID_MMA4_F4(CG)                                                                                         \
+    asm volatile("{\n\t.reg .pred p, q;\n\t"                                                                    \
+                 "setp.ne.b32 p, %12, 0;\n\t"                                                                  \
+                 "setp.ne.b32 q, %12, 0xFFFFFFFF;\n\t"                                                         \
+                 "tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %1, %5, %9, [%10], [%11], p;\n\t" \
+                 "tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %2, %6, %9, [%10], [%11], q;\n\t" \
+                 "tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %3, %7, %9, [%10], [%11], q;\n\t" \
+                 "tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %4, %8, %9, [%10], [%11], q;\n\t}" \
+                 ::"r"(d), "l"(ad), "l"(a1), "l"(a2), "l"(a3), "l"(bd), "l"(b1), "l"(b2), "l"(b3), "r"(idesc),      \
+                 "r"(sfa), "r"(sfb), "r"(acc)                                                                     \
+                 : "memory")
+        if constexpr (CG2)
+            FASTID_MMA4_F4("2");
+        else
+            FASTID_MMA4_F4("1");
+#undef FASTID_MMA4_F4
+    } else {
+        (void)sfa;
+        (void)sfb;
+#define FASTID_MMA4_F8(CG)                                                                                         \
+    asm volatile("{\n\t.reg .pred p, q;\n\t"                                                                    \
+                 "setp.ne.b32 p, %10, 0;\n\t"                                                                  \
+                 "setp.ne.b32 q, %10, 0xFFFFFFFF;\n\t"                                                         \
+                 "tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %1, %5, %9, p;\n\t"                          \
+                 "tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %2, %6, %9, q;\n\t"                          \
+                 "tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %3, %7, %9, q;\n\t"                          \
+                 "tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %4, %8, %9, q;\n\t}"                         \
+                 ::"r"(d), "l"(ad), "l"(a1), "l"(a2), "l"(a3), "l"(bd), "l"(b1), "l"(b2), "l"(b3), "r"(idesc),      \
+                 "r"(acc)                                                                                         \
+                 : "memory")
+        if constexpr (CG2)
+            FASTID_MMA4_F8("2");
+        else
+            FASTID_MMA4_F8("1");
+#undef FASTID_MMA4_F8
+    }
 }
 
 // 32 lanes x one 32-bit column (every lane its own row).
@@ -521,10 +592,20 @@ __device__ __forceinline__ void expand_stage_f4(const uint8_t *sp, uint8_t *sb, 
 // of every reference stage into both CTAs' shared memory.
 // PK: packed reference operand expanded on chip (see expand_stage).
 // F4: block-scaled FP4 operands (kind::mxf4, BN = 224); else FP8 (BN = 256 or 128).
-template <int BN, bool PAIR, int KM, bool PK, bool F4>
+// CG2 (with PAIR): the pair's MMA is one 2-SM tcgen05.mma (cta_group::2, M =
+// 256) issued by the even CTA: each CTA loads its own query tile and HALF of
+// every reference stage into its own shared memory (no multicast), the
+// tensor cores of both SMs read both halves, and each CTA's TMEM receives
+// its own 128 query rows x BN references.  A stage then costs each SM 16 KB
+// of queries + BN/2 references' bytes instead of the whole reference stage,
+// which leaves room for 7 stages.  Both CTAs' loads complete on the even
+// CTA's full barrier; its commits release both CTAs' stages and accumulators;
+// both epilogues release an accumulator on the even CTA's barrier.
+template <int BN, bool PAIR, int KM, bool PK, bool F4, bool CG2 = false>
 __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS, 1)
     tensor_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TensorArgs args) {
-    using S = TcShape<BN, PK>;
+    using S = TcShape<BN, PK, CG2>;
+    static_assert(!CG2 || (PAIR && !PK), "2-SM MMA launches are paired, over an operand copy");
     static_assert(F4 ? BN == TC_BN4 : BN != TC_BN4, "FP4 launches use 224-reference tiles, FP8 ones 256 or 128");
     static_assert(!PAIR || BN != 128, "paired launches use 256- or 224-reference tiles");
     static_assert(!PK || (BN != 128 && !PAIR), "packed-reference launches use unpaired 256- or 224-reference tiles");
@@ -551,23 +632,32 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
     if (tid == 0) {
         for (int s = 0; s < S::STAGES; ++s) {
             mbar_init(smem_u32(&ctl->full[s]), 1);
-            mbar_init(smem_u32(&ctl->empty[s]), PAIR ? 2 : 1);  // both CTAs' MMAs release a paired stage
+            // multicast pairs: both CTAs' MMAs release a stage; 2-SM pairs: the even CTA's MMA
+            mbar_init(smem_u32(&ctl->empty[s]), (PAIR && !CG2) ? 2 : 1);
             if (PK) mbar_init(smem_u32(&ctl->bfull[s]), pk_threads(KM));  // every expanding thread
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl->tfull[a]), 1);
-            mbar_init(smem_u32(&ctl->tempty[a]), 128);
+            mbar_init(smem_u32(&ctl->tempty[a]), CG2 ? 256 : 128);  // 2-SM: both CTAs' epilogues
         }
         mbar_init(smem_u32(&ctl->done), 1);
         ctl->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&ctl->tmem_base)),
-                     "r"(S::TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (CG2) {  // one warp of each CTA of the pair, together: the same columns in both
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&ctl->tmem_base)),
+                         "r"(S::TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&ctl->tmem_base)),
+                         "r"(S::TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -590,8 +680,19 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
+        // Per stage: one wait for the slot (inline when it is already free),
+        // the expected bytes, the loads at stage offsets from the first slot and
+        // coordinates fixed per reference tile (a short path, like the MMA
+        // issuer's, so that the producer keeps up at FP4 speed).
         if (lane == 0) {
-            int stage = 0;
+            const uint32_t full0 = smem_u32(&ctl->full[0]), empty0 = smem_u32(&ctl->empty[0]);
+            const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB), sP0 = smem_u32(sP);
+            // this CTA's reference rows of a (paired) tile start at rt * BN + boff
+            const int32_t boff = PAIR ? rank * (BN / 2) : 0;
+            // bytes landing on a full barrier: 2-SM pairs count both CTAs' loads
+            // on the even CTA's; multicast pairs both halves on each CTA's
+            constexpr uint32_t TX = CG2 ? 2 * (TC_A_BYTES + S::B_BYTES) : TC_A_BYTES + (PK ? P_BYTES : S::B_BYTES);
+            uint32_t stage = 0;
             uint32_t phase = 0;
             int64_t issued = 0;
             bool ok = true;
@@ -600,39 +701,49 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                 const GroupWork W = group_work(args, wg, p, PAIR ? 2 : 1, rank);
                 if (pi > 0 && args.arrive) panel_rendezvous(args.arrive + pi, W.q_lo < W.q_hi);
                 if (W.q_lo >= W.q_hi) continue;
-                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[p])) : "memory");
-                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[p])) : "memory");
+                const CUtensorMap *ma = &maps.a[p];
+                const CUtensorMap *mb = &maps.b[p];
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(ma)) : "memory");
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(mb)) : "memory");
                 const int n_kb = args.panel[p].n_kb;
                 const bool pf = args.panel[p].sc.pf != 0 && W.q_hi - W.q_lo == 1;
                 for (int64_t rc = W.r_lo; rc < W.r_hi && ok; rc += W.chunk) {
                     const int64_t re = min(rc + W.chunk, W.r_hi);
                     for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
-                        const int64_t qt = PAIR ? 2 * (int64_t)qq + rank : qq;
+                        const int32_t ya = (int32_t)((PAIR ? 2 * (int64_t)qq + rank : (int64_t)qq) * TC_BM);
                         for (int64_t rt = rc; rt < re && ok; ++rt) {
+                            const int32_t yb = (int32_t)(rt * BN) + boff;
+                            // A group with one query tile streams its slice once: fetch the
+                            // next reference tile into L2 while this one is consumed, so the
+                            // group that reaches a tile first does not wait on DRAM (where
+                            // the schedule enables it, see TcSched::pf).
+                            const bool pft = !PK && pf && rt + 1 < W.r_hi;
                             for (int kb = 0; kb < n_kb; ++kb) {
-                                ok = mbar_wait(smem_u32(&ctl->empty[stage]), phase ^ 1u, abort_flag, args.status, 1);
-                                if (!ok) break;
-                                const uint32_t fb = smem_u32(&ctl->full[stage]);
-                                mbar_expect_tx(fb, TC_A_BYTES + (PK ? P_BYTES : S::B_BYTES));
-                                tma_load_2d(smem_u32(sA + stage * TC_A_BYTES), &maps.a[p], fb, kb * TC_BK,
-                                            (int32_t)(qt * TC_BM));
-                                if (PK)  // the stage's loci as packed words (2 FP8, 4 FP4) x BN references
-                                    tma_load_2d(smem_u32(sP + stage * P_BYTES), &maps.b[p], fb, kb * (F4 ? 4 : 2),
-                                                (int32_t)(rt * BN));
-                                else if (PAIR)
-                                    tma_load_2d_mc(smem_u32(sB + stage * S::B_BYTES + rank * (S::B_BYTES / 2)),
-                                                   &maps.b[p], fb, kb * TC_BK, (int32_t)(rt * BN + rank * (BN / 2)),
-                                                   (uint16_t)0x3);
-                                else
-                                    tma_load_2d(smem_u32(sB + stage * S::B_BYTES), &maps.b[p], fb, kb * TC_BK,
-                                                (int32_t)(rt * BN));
-                                // A group with one query tile streams its slice once: fetch the
-                                // next reference tile into L2 while this one is consumed, so the
-                                // group that reaches a tile first does not wait on DRAM (where
-                                // the schedule enables it, see TcSched::pf).
-                                if (!PK && pf && rt + 1 < W.r_hi)
-                                    tma_prefetch_2d(&maps.b[p], kb * TC_BK,
-                                                    (int32_t)((rt + 1) * BN + (PAIR ? rank * (BN / 2) : 0)));
+                                const uint32_t eb = empty0 + 8u * stage;
+                                if (!mbar_try_wait(eb, phase ^ 1u)) {
+                                    ok = mbar_wait(eb, phase ^ 1u, abort_flag, args.status, 1);
+                                    if (!ok) break;
+                                }
+                                const uint32_t fb = full0 + 8u * stage;
+                                const int32_t x = kb * TC_BK;
+                                if (CG2) {
+                                    // both CTAs' bytes complete on the even CTA's full barrier
+                                    const uint32_t fb0 = mapa_rank(fb, 0);
+                                    if (rank == 0) mbar_expect_tx(fb, TX);
+                                    tma_load_2d_cg2(sA0 + stage * TC_A_BYTES, ma, fb0, x, ya);
+                                    tma_load_2d_cg2(sB0 + stage * S::B_BYTES, mb, fb0, x, yb);
+                                } else {
+                                    mbar_expect_tx(fb, TX);
+                                    tma_load_2d(sA0 + stage * TC_A_BYTES, ma, fb, x, ya);
+                                    if (PK)  // the stage's loci as packed words (2 FP8, 4 FP4) x BN references
+                                        tma_load_2d(sP0 + stage * P_BYTES, mb, fb, kb * (F4 ? 4 : 2), yb);
+                                    else if (PAIR)  // this CTA's half, into both CTAs
+                                        tma_load_2d_mc(sB0 + stage * S::B_BYTES + rank * (S::B_BYTES / 2), mb, fb, x, yb,
+                                                       (uint16_t)0x3);
+                                    else
+                                        tma_load_2d(sB0 + stage * S::B_BYTES, mb, fb, x, yb);
+                                }
+                                if (pft) tma_prefetch_2d(mb, x, yb + BN);
                                 ++issued;
                                 if (++stage == S::STAGES) {
                                     stage = 0;
@@ -646,7 +757,9 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
             // Drain: the last fill of every stage has landed before the CTA
             // exits (fill n used stage n % S in phase (n / S) & 1).
             for (int64_t n = issued - 1; n >= 0 && n >= issued - S::STAGES; --n) {
-                mbar_drain(smem_u32(&ctl->full[n % S::STAGES]), (uint32_t)((n / S::STAGES) & 1), args.status, 2);
+                // (2-SM pairs: the even CTA's full barriers count both CTAs' fills)
+                if (!CG2 || rank == 0)
+                    mbar_drain(smem_u32(&ctl->full[n % S::STAGES]), (uint32_t)((n / S::STAGES) & 1), args.status, 2);
                 // paired: both MMAs' releases of this stage (the peer's arrive
                 // remotely) have landed before the CTA exits
                 if (PAIR)
@@ -654,10 +767,19 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
-            constexpr uint32_t idesc = F4 ? idesc_mxf4(TC_BM, BN) : idesc_f8(TC_BM, BN);
-            int stage = 0;
+        // ---------------- MMA issuer (2-SM pairs: the even CTA's) ----------------
+        // Per stage: one barrier wait (inline when the stage is already full),
+        // the stage's descriptors as constant offsets from the first stage's,
+        // four MMAs in one asm block, one commit (see mma_stage4).
+        if (lane == 0 && (!CG2 || rank == 0)) {
+            constexpr int MM = CG2 ? 2 * TC_BM : TC_BM;
+            constexpr uint32_t idesc = F4 ? idesc_mxf4(MM, BN) : idesc_f8(MM, BN);
+            constexpr uint32_t A_STEP = TC_A_BYTES >> 4, B_STEP = S::B_BYTES >> 4;  // descriptor units a stage
+            const uint64_t ad0 = sw128_desc(smem_u32(sA)), bd0 = sw128_desc(smem_u32(sB));
+            const uint32_t full0 = smem_u32(&ctl->full[0]), empty0 = smem_u32(&ctl->empty[0]);
+            const uint32_t bfull0 = smem_u32(&ctl->bfull[0]);
+            const uint32_t sfa = tmem_base + TC_SF_COL, sfb = tmem_base + TC_SF_COL + 16;
+            uint32_t stage = 0;
             uint32_t phase = 0;
             int acc = 0;
             uint32_t acc_phase = 0;
@@ -671,37 +793,44 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                     const int64_t re = min(rc + W.chunk, W.r_hi);
                     for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
                         for (int64_t rt = rc; rt < re && ok; ++rt) {
-                            ok = mbar_wait(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, abort_flag, args.status, 3);
-                            if (!ok) break;
-                            tc_fence_after();
+                            const uint32_t tempty = smem_u32(&ctl->tempty[acc]);
+                            if (!mbar_try_wait(tempty, acc_phase ^ 1u)) {
+                                ok = mbar_wait(tempty, acc_phase ^ 1u, abort_flag, args.status, 3);
+                                if (!ok) break;
+                            }
+                            tc_fence_after();  // the epilogue's reads of this accumulator come first
                             const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
                             for (int kb = 0; kb < n_kb; ++kb) {
-                                ok = mbar_wait(smem_u32(&ctl->full[stage]), phase, abort_flag, args.status, 4);
-                                if (ok && PK)
-                                    ok = mbar_wait(smem_u32(&ctl->bfull[stage]), phase, abort_flag, args.status, 8);
-                                if (!ok) break;
-                                tc_fence_after();
-                                const uint64_t ad = sw128_desc(smem_u32(sA + stage * TC_A_BYTES));
-                                const uint64_t bd = sw128_desc(smem_u32(sB + stage * S::B_BYTES));
-#pragma unroll
-                                for (int kk = 0; kk < TC_BK / 32; ++kk) {  // 32 bytes of K per MMA: +2 in the address field
-                                    if (F4)  // K = 64 e2m1
-                                        tc_mma_f4(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, tmem_base + TC_SF_COL,
-                                                  tmem_base + TC_SF_COL + 16, (kb | kk) != 0);
-                                    else  // K = 32 e4m3
-                                        tc_mma_f8(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
+                                const uint32_t fb = full0 + 8u * stage;
+                                if (!mbar_try_wait(fb, phase)) {
+                                    ok = mbar_wait(fb, phase, abort_flag, args.status, 4);
+                                    if (!ok) break;
                                 }
-                                if (PAIR)
-                                    tc_commit_mc(smem_u32(&ctl->empty[stage]), (uint16_t)0x3);
+                                if (PK && !mbar_try_wait(bfull0 + 8u * stage, phase)) {
+                                    ok = mbar_wait(bfull0 + 8u * stage, phase, abort_flag, args.status, 8);
+                                    if (!ok) break;
+                                }
+                                // (the stage's operands were written by TMA, or by the expanding
+                                // warps behind an async-proxy fence, and are ordered by the barrier)
+                                mma_stage4<F4, CG2>(d_tmem, ad0 + stage * A_STEP, bd0 + stage * B_STEP, idesc, sfa,
+                                                    sfb, kb != 0);
+                                const uint32_t eb = empty0 + 8u * stage;
+                                if (CG2)
+                                    tc_commit_cg2_mc(eb, (uint16_t)0x3);
+                                else if (PAIR)
+                                    tc_commit_mc(eb, (uint16_t)0x3);
                                 else
-                                    tc_commit(smem_u32(&ctl->empty[stage]));
+                                    tc_commit(eb);
                                 if (++stage == S::STAGES) {
                                     stage = 0;
                                     phase ^= 1u;
                                 }
                             }
                             if (!ok) break;
-                            tc_commit(smem_u32(&ctl->tfull[acc]));
+                            if (CG2)  // both CTAs' accumulators are full
+                                tc_commit_cg2_mc(smem_u32(&ctl->tfull[acc]), (uint16_t)0x3);
+                            else
+                                tc_commit(smem_u32(&ctl->tfull[acc]));
                             if (++acc == 2) {
                                 acc = 0;
                                 acc_phase ^= 1u;
@@ -711,7 +840,10 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                 }
             }
             // Drain: a commit completes after every MMA this thread issued.
-            tc_commit(smem_u32(&ctl->done));
+            if (CG2)
+                tc_commit_cg2(smem_u32(&ctl->done));
+            else
+                tc_commit(smem_u32(&ctl->done));
             mbar_drain(smem_u32(&ctl->done), 0, args.status, 5);
         }
     } else if (PK && warp >= 6) {
@@ -865,7 +997,10 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                         }
                         // every column of the tile is processed: the MMA may reuse the accumulator
                         tc_fence_before();
-                        mbar_arrive(smem_u32(&ctl->tempty[acc]));
+                        if (CG2)  // on the even CTA's barrier
+                            mbar_arrive_cluster(mapa_rank(smem_u32(&ctl->tempty[acc]), 0));
+                        else
+                            mbar_arrive(smem_u32(&ctl->tempty[acc]));
                         if (++acc == 2) {
                             acc = 0;
                             acc_phase ^= 1u;
@@ -882,8 +1017,12 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
     if (PAIR) cluster_sync();  // neither CTA leaves while the other may still address it
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(S::TMEM_COLS)
-                     : "memory");
+        if (CG2)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(S::TMEM_COLS)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(S::TMEM_COLS)
+                         : "memory");
     }
 }
 
@@ -1073,9 +1212,9 @@ __global__ void prep_jobs_kernel(const PrepJob *__restrict__ jobs, int64_t n_job
     }
 }
 
-template <int BN, bool PK = false>
+template <int BN, bool PK = false, bool CG2 = false>
 size_t tensor_smem(bool f4 = false) {
-    using S = TcShape<BN, PK>;
+    using S = TcShape<BN, PK, CG2>;
     return 1024 + S::STAGES * (size_t)(TC_A_BYTES + S::B_BYTES + (PK ? pk_stage_bytes(BN, f4) : 0)) + 256;
 }
 
@@ -1223,12 +1362,12 @@ int tensor_grid_target(int device) {
 
 namespace {
 
-// One launch of tensor_kernel<BN, PAIR, KM, PK, F4> over n_groups work groups
-// (2-CTA clusters when paired).
-template <int BN, bool PAIR, int KM, bool PK = false, bool F4 = false>
+// One launch of tensor_kernel<BN, PAIR, KM, PK, F4, CG2> over n_groups work
+// groups (2-CTA clusters when paired).
+template <int BN, bool PAIR, int KM, bool PK = false, bool F4 = false, bool CG2 = false>
 cudaError_t launch_variant(const TcMaps &maps, const TensorArgs &a, int32_t n_groups, int epi, cudaStream_t s) {
-    const size_t smem = tensor_smem<BN, PK>(F4);
-    cudaError_t e = cudaFuncSetAttribute(tensor_kernel<BN, PAIR, KM, PK, F4>,
+    const size_t smem = tensor_smem<BN, PK, CG2>(F4);
+    cudaError_t e = cudaFuncSetAttribute(tensor_kernel<BN, PAIR, KM, PK, F4, CG2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
@@ -1244,7 +1383,7 @@ cudaError_t launch_variant(const TcMaps &maps, const TensorArgs &a, int32_t n_gr
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = PAIR ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, tensor_kernel<BN, PAIR, KM, PK, F4>, maps, a);
+    return cudaLaunchKernelEx(&cfg, tensor_kernel<BN, PAIR, KM, PK, F4, CG2>, maps, a);
 }
 
 }  // namespace
@@ -1289,6 +1428,9 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
             return k16 ? launch_variant<TC_BN4, false, 16, true, true>(maps, a, L.n_groups, L.epi, s)
                        : launch_variant<TC_BN4, false, 32, true, true>(maps, a, L.n_groups, L.epi, s);
         }
+        if (L.pair && L.cg2)
+            return k16 ? launch_variant<TC_BN4, true, 16, false, true, true>(maps, a, L.n_groups, L.epi, s)
+                       : launch_variant<TC_BN4, true, 32, false, true, true>(maps, a, L.n_groups, L.epi, s);
         if (L.pair) return k16 ? launch_variant<TC_BN4, true, 16, false, true>(maps, a, L.n_groups, L.epi, s)
                                : launch_variant<TC_BN4, true, 32, false, true>(maps, a, L.n_groups, L.epi, s);
         return k16 ? launch_variant<TC_BN4, false, 16, false, true>(maps, a, L.n_groups, L.epi, s)
@@ -1300,6 +1442,9 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
         return k16 ? launch_variant<256, false, 16, true>(maps, a, L.n_groups, L.epi, s)
                    : launch_variant<256, false, 32, true>(maps, a, L.n_groups, L.epi, s);
     }
+    if (L.pair && L.cg2)
+        return k16 ? launch_variant<256, true, 16, false, false, true>(maps, a, L.n_groups, L.epi, s)
+                   : launch_variant<256, true, 32, false, false, true>(maps, a, L.n_groups, L.epi, s);
     if (L.pair) return k16 ? launch_variant<256, true, 16>(maps, a, L.n_groups, L.epi, s)
                            : launch_variant<256, true, 32>(maps, a, L.n_groups, L.epi, s);
     if (bn == 128) return k16 ? launch_variant<128, false, 16>(maps, a, L.n_groups, L.epi, s)

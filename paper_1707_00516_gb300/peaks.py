@@ -5,8 +5,9 @@
 * the tensor pipe: tcgen05 ``kind::f8f6f4`` (e4m3, M 128 x N 256 x K 32) and
   block-scaled ``kind::mxf4`` (e2m1 with unit ue8m0 scale factors, M 128 x
   N 224 and 256 x K 64), operands in shared memory, one CTA per SM;
-* the integer pipes: POPC alone, LOP3 alone, and the plain form's inner
-  sequence (AND, POPC, one 3-input add per two words);
+* the integer pipes: POPC alone, LOP3 alone, the plain form's inner
+  sequence (AND, POPC, one 3-input add per two words), and the same count
+  by a carry-save (Harley-Seal) tree, in word pairs;
 * the binary tensor-core path: ``mma.sync m16n8k256 b1 AND + POPC``.
 
 Each rate is reported per second (CUDA events, at the clock the probe ran
@@ -35,8 +36,9 @@ def load():
         if _lib is None:
             lib = ctypes.CDLL(_build.build_peaks())
             lib.fastid_peaks_mma.restype = ctypes.c_int
-            lib.fastid_peaks_mma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _D, _D, _D]
+            lib.fastid_peaks_mma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _D, _D,
+                                             _D]
             lib.fastid_peaks_alu.restype = ctypes.c_int
             lib.fastid_peaks_alu.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
             lib.fastid_peaks_b1.restype = ctypes.c_int
@@ -68,7 +70,7 @@ def mma_check(f4: bool, n: int, a_vals: np.ndarray, b_vals: np.ndarray) -> np.nd
     assert a.shape == (128, K_BYTES) and b.shape == (n, K_BYTES)
     d = np.zeros((128, n), dtype=np.float32)
     ms, clk, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-    rc = lib.fastid_peaks_mma(int(f4), n, 1, 1, a.ctypes.data, b.ctypes.data, d.ctypes.data, ctypes.byref(ms),
+    rc = lib.fastid_peaks_mma(int(f4), n, 1, 1, 1, 0, a.ctypes.data, b.ctypes.data, d.ctypes.data, ctypes.byref(ms),
                               ctypes.byref(clk), ctypes.byref(mhz))
     if rc != 0:
         raise RuntimeError(f"fastid_peaks_mma returned {rc}")
@@ -89,22 +91,29 @@ def measure(target_ms: float = 40.0) -> dict:
     import torch
     n_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
-    def mma(f4, n, kmma):
+    def mma(f4, n, kmma, nst=1, sync=0):
         def run(iters):
             ms, clk, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-            rc = lib.fastid_peaks_mma(int(f4), n, iters, 0, None, None, None, ctypes.byref(ms), ctypes.byref(clk),
-                                      ctypes.byref(mhz))
+            rc = lib.fastid_peaks_mma(int(f4), n, iters, 0, nst, sync, None, None, None, ctypes.byref(ms),
+                                      ctypes.byref(clk), ctypes.byref(mhz))
             if rc != 0:
                 raise RuntimeError(f"fastid_peaks_mma({f4}, {n}) returned {rc}")
             return ms.value, clk.value, mhz.value
         ms, clk, mhz, iters = _calibrated(run, target_ms, 2000)
         flops_cta = 2.0 * 128 * n * kmma * 4 * iters
         return {"tflops": flops_cta * n_sms / (ms / 1e3) / 1e12, "flops_per_clk_sm": flops_cta / clk,
-                "sm_mhz": mhz, "ms": ms, "shape": f"M128xN{n}xK{kmma}"}
+                "sm_mhz": mhz, "ms": ms, "shape": f"M128xN{n}xK{kmma}", "stages": nst, "sync": sync}
 
     out["fp8_f8f6f4"] = mma(False, 256, 32)
     out["fp4_mxf4_n224"] = mma(True, 224, 64)
     out["fp4_mxf4_n256"] = mma(True, 256, 64)
+    # the operands cycled through four stages of shared memory, as the
+    # comparison kernel's pipeline holds them
+    out["fp8_f8f6f4_4stages"] = mma(False, 256, 32, 4)
+    out["fp4_mxf4_n224_4stages"] = mma(True, 224, 64, 4)
+    # and with the per-stage barrier wait and commit of the kernel's MMA thread
+    out["fp8_f8f6f4_4stages_sync"] = mma(False, 256, 32, 4, 7)
+    out["fp4_mxf4_n224_4stages_sync"] = mma(True, 224, 64, 4, 7)
 
     def alu(op, name):
         def run(iters):
@@ -121,6 +130,7 @@ def measure(target_ms: float = 40.0) -> dict:
     out["popc"] = alu(0, "POPC")
     out["lop3"] = alu(1, "LOP3")
     out["and_popc_add"] = alu(2, "POPC in AND + POPC + IADD3/2")
+    out["harley_seal"] = alu(3, "word pairs counted by AND + carry-save tree + POPC/8")
 
     def b1():
         def run(iters):

@@ -120,38 +120,47 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 struct ProbeCtl {
     uint64_t done;
+    uint64_t stage_bar;  // sync probes: committed to every round
+    uint64_t ready_bar;  // sync probes: completed once, then waited on every round
     uint32_t tmem_base;
 };
 
 // One CTA: operands A [128][128 B] and B [N][128 B] (K-major rows, bytes as
 // the MMA kind reads them) copied into shared memory in the 128-byte swizzle,
-// then `iters` rounds of 4 MMAs over the 128 bytes of K into one TMEM
-// accumulator.  d_out (optional, [128][N] f32) receives the accumulator.
+// nst times at distinct addresses (stages, as the comparison kernel's ring
+// holds them), then `iters` rounds of 4 MMAs over the 128 bytes of K of
+// stage it % nst into one TMEM accumulator.  sync (bits): after each round's
+// 4 MMAs the issuing thread also waits on an mbarrier phase that has already
+// completed (1), fences (2) and commits to an mbarrier (4) -- 7 is the
+// per-stage work of the comparison kernel's MMA thread without its data.  d_out (optional, [128][N] f32) receives the accumulator.
 // cyc[2 * blockIdx.x] = SM clocks of the MMA loop, cyc[2 * blockIdx.x + 1] =
 // its nanoseconds.  A wait that runs out sets *status = 1.
 template <bool F4, int N>
 __global__ void __launch_bounds__(192, 1)
-    mma_probe_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b, int iters,
+    mma_probe_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b, int iters, int nst, int sync,
                      float *__restrict__ d_out, unsigned long long *__restrict__ cyc, uint32_t *status) {
     extern __shared__ uint8_t smem_raw[];
+    constexpr int STAGE = (PM + N) * ROWB;  // a multiple of 1024
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-    uint8_t *sA = base;
-    uint8_t *sB = base + PM * ROWB;
-    ProbeCtl *ctl = reinterpret_cast<ProbeCtl *>(sB + N * ROWB);
+    ProbeCtl *ctl = reinterpret_cast<ProbeCtl *>(base + nst * STAGE);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    for (int i = tid; i < (PM + N) * 8; i += blockDim.x) {
-        const int row = i >> 3, c = i & 7;
+    for (int i = tid; i < nst * (PM + N) * 8; i += blockDim.x) {
+        const int st = i / ((PM + N) * 8), j = i - st * (PM + N) * 8;
+        const int row = j >> 3, c = j & 7;
         const bool isa = row < PM;
         const int r = isa ? row : row - PM;
         const uint4 v = *reinterpret_cast<const uint4 *>((isa ? a : b) + (size_t)r * ROWB + c * 16);
-        *reinterpret_cast<uint4 *>((isa ? sA : sB) + r * ROWB + ((c ^ (r & 7)) << 4)) = v;
+        *reinterpret_cast<uint4 *>(base + st * STAGE + (isa ? 0 : PM * ROWB) + r * ROWB + ((c ^ (r & 7)) << 4)) = v;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ctl->done)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ctl->stage_bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ctl->ready_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ctl->ready_bar)) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -173,10 +182,11 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 1 && lane == 0) {
-        const uint64_t ad = sw128_desc(smem_u32(sA)), bd = sw128_desc(smem_u32(sB));
         const long long c0 = clock64();
         const uint64_t n0 = globaltimer();
         for (int it = 0; it < iters; ++it) {
+            const uint8_t *sA = base + (it % nst) * STAGE;
+            const uint64_t ad = sw128_desc(smem_u32(sA)), bd = sw128_desc(smem_u32(sA + PM * ROWB));
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per MMA: +2 in the address field
                 if (F4)
@@ -185,6 +195,15 @@ __global__ void __launch_bounds__(192, 1)
                 else
                     mma_f8(tmem, ad + 2u * kk, bd + 2u * kk, idesc_f8(PM, N), (it | kk) != 0);
             }
+            if (sync & 1) {  // phase 0 of ready_bar completed at set-up: the wait succeeds at once
+                while (!mbar_try_wait(smem_u32(&ctl->ready_bar), 0)) {
+                }
+            }
+            if (sync & 2) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (sync & 4)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&ctl->stage_bar))
+                             : "memory");
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&ctl->done))
@@ -245,7 +264,28 @@ __global__ void fill_kernel(uint8_t *p, size_t n, bool f4) {
 //         plain form's inner sequence: 2 AND, 2 POPC, 1 IADD3 per two words;
 //         the accumulator stands in for the operand loads so that nothing
 //         is loop-invariant)
-// Counted elements: op 0 POPC, op 1 LOP3, op 2 POPC.
+//   op 3: the same count by a carry-save (Harley-Seal) tree over 8 ANDed
+//         words at a time, for 4 (reference, query) pairs: per 8 words 8
+//         AND, 7 carry-save adders (2 LOP3 each: sum 0x96, majority 0xE8),
+//         one POPC of the eights and one add; the pair's `fours` word stands
+//         in for the operand loads
+// Counted elements: op 0 POPC, op 1 LOP3, op 2 POPC, op 3 word pairs.
+__device__ __forceinline__ uint32_t lop3_sum(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t lop3_maj(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm volatile("lop3.b32 %0, %1, %2, %3, 0xE8;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+// carry-save adder: (hi, lo) = a + b + c bitwise
+__device__ __forceinline__ void csa(uint32_t &hi, uint32_t &lo, uint32_t a, uint32_t b, uint32_t c) {
+    hi = lop3_maj(a, b, c);
+    lo = lop3_sum(a, b, c);
+}
+
 template <int OP>
 __global__ void __launch_bounds__(1024) alu_probe_kernel(uint32_t seed, int iters, uint32_t *out,
                                                          unsigned long long *cyc) {
@@ -276,6 +316,36 @@ __global__ void __launch_bounds__(1024) alu_probe_kernel(uint32_t seed, int iter
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) res += x[j];
+    } else if (OP == 3) {
+        uint32_t ones[4], twos[4], fours[4], tot[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            ones[p] = x[p];
+            twos[p] = x[p + 4];
+            fours[p] = x[p] ^ x[7 - p];
+            tot[p] = 0;
+        }
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                uint32_t w[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) asm volatile("and.b32 %0, %1, %2;" : "=r"(w[i]) : "r"(x[i]), "r"(fours[p]));
+                uint32_t tA, tB, fA, fB, e;
+                csa(tA, ones[p], ones[p], w[0], w[1]);
+                csa(tB, ones[p], ones[p], w[2], w[3]);
+                csa(fA, twos[p], twos[p], tA, tB);
+                csa(tA, ones[p], ones[p], w[4], w[5]);
+                csa(tB, ones[p], ones[p], w[6], w[7]);
+                csa(fB, twos[p], twos[p], tA, tB);
+                csa(e, fours[p], fours[p], fA, fB);
+                uint32_t pe;
+                asm volatile("popc.b32 %0, %1;" : "=r"(pe) : "r"(e));
+                tot[p] += pe;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p) res += 8 * tot[p] + 4 * __popc(fours[p]) + 2 * __popc(twos[p]) + __popc(ones[p]);
     } else {
         uint32_t acc[4][4];
 #pragma unroll
@@ -374,10 +444,12 @@ int finish_timing(cudaEvent_t e0, cudaEvent_t e1, const unsigned long long *d_cy
 }
 
 template <bool F4, int N>
-int run_mma(int iters, int grid, const uint8_t *a_host, const uint8_t *b_host, float *d_host, Timed *t) {
+int run_mma(int iters, int grid, int nst, int sync, const uint8_t *a_host, const uint8_t *b_host, float *d_host,
+            Timed *t) {
     auto kern = mma_probe_kernel<F4, N>;
     // > half of the SM's shared memory: one CTA per SM (each holds all 512 TMEM columns)
-    const size_t smem = 1024 + (size_t)(PM + N) * ROWB + 64 < 120 * 1024 ? 120 * 1024 : 1024 + (PM + N) * ROWB + 64;
+    const size_t need = 1024 + (size_t)nst * (PM + N) * ROWB + 64;
+    const size_t smem = need < 120 * 1024 ? 120 * 1024 : need;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
     uint8_t *a = nullptr, *b = nullptr;
     float *d = nullptr;
@@ -399,7 +471,7 @@ int run_mma(int iters, int grid, const uint8_t *a_host, const uint8_t *b_host, f
     }
     if (cudaMemset(status, 0, 4) || cudaEventCreate(&e0) || cudaEventCreate(&e1)) goto out;
     cudaEventRecord(e0);
-    kern<<<grid, 192, smem>>>(a, b, iters, d, cyc, status);
+    kern<<<grid, 192, smem>>>(a, b, iters, nst, sync, d, cyc, status);
     cudaEventRecord(e1);
     if (cudaGetLastError() != cudaSuccess || finish_timing(e0, e1, cyc, grid, t)) goto out;
     if (cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost)) goto out;
@@ -433,23 +505,26 @@ int sms() {
 extern "C" {
 
 // One tcgen05 MMA probe launch.  f4: 0 kind::f8f6f4 (n = 256), 1 kind::mxf4
-// (n = 224 or 256).  grid <= 0: one CTA per SM.  a_host [128][128] and b_host
+// (n = 224 or 256).  nst: operand stages cycled through (1 .. 4; 1 re-reads
+// the same shared memory every round).  sync, per round of 4 MMAs: bit 0 a
+// wait on a completed mbarrier phase, bit 1 a tcgen05 fence, bit 2 a commit.
+// grid <= 0: one CTA per SM.  a_host [128][128] and b_host
 // [n][128] operand bytes (both NULL: filled on the device); d_host [128][n]
 // (optional, grid must be 1) receives D.  Outputs: event ms, median clocks
 // and MHz of the MMA loop over CTAs.  Returns 0, 1 (CUDA error or bad
 // arguments) or 2 (the completion wait ran out).
-int fastid_peaks_mma(int f4, int n, int iters, int grid, const uint8_t *a_host, const uint8_t *b_host,
-                     float *d_host, double *ms, double *clocks, double *mhz) {
+int fastid_peaks_mma(int f4, int n, int iters, int grid, int nst, int sync, const uint8_t *a_host,
+                     const uint8_t *b_host, float *d_host, double *ms, double *clocks, double *mhz) {
     if (grid <= 0) grid = sms();
-    if (iters < 1 || (d_host && grid != 1) || (!a_host) != (!b_host)) return 1;
+    if (iters < 1 || nst < 1 || nst > 4 || (d_host && grid != 1) || (!a_host) != (!b_host)) return 1;
     Timed t;
     int rc;
     if (!f4 && n == 256)
-        rc = run_mma<false, 256>(iters, grid, a_host, b_host, d_host, &t);
+        rc = run_mma<false, 256>(iters, grid, nst, sync, a_host, b_host, d_host, &t);
     else if (f4 && n == 224)
-        rc = run_mma<true, 224>(iters, grid, a_host, b_host, d_host, &t);
+        rc = run_mma<true, 224>(iters, grid, nst, sync, a_host, b_host, d_host, &t);
     else if (f4 && n == 256)
-        rc = run_mma<true, 256>(iters, grid, a_host, b_host, d_host, &t);
+        rc = run_mma<true, 256>(iters, grid, nst, sync, a_host, b_host, d_host, &t);
     else
         return 1;
     if (ms) *ms = t.ms;
@@ -462,7 +537,7 @@ int fastid_peaks_mma(int f4, int n, int iters, int grid, const uint8_t *a_host, 
 // CTAs of 1024 threads per SM.  *elements: counted operations of the launch.
 int fastid_peaks_alu(int op, int iters, int blocks_per_sm, double *ms, double *clocks, double *mhz,
                      double *elements) {
-    if (op < 0 || op > 2 || iters < 1 || blocks_per_sm < 1) return 1;
+    if (op < 0 || op > 3 || iters < 1 || blocks_per_sm < 1) return 1;
     const int grid = sms() * blocks_per_sm, threads = 1024;
     uint32_t *out = nullptr;
     unsigned long long *cyc = nullptr;
@@ -476,6 +551,7 @@ int fastid_peaks_alu(int op, int iters, int blocks_per_sm, double *ms, double *c
     if (op == 0) alu_probe_kernel<0><<<grid, threads>>>(12345u, iters, out, cyc);
     if (op == 1) alu_probe_kernel<1><<<grid, threads>>>(12345u, iters, out, cyc);
     if (op == 2) alu_probe_kernel<2><<<grid, threads>>>(12345u, iters, out, cyc);
+    if (op == 3) alu_probe_kernel<3><<<grid, threads>>>(12345u, iters, out, cyc);
     cudaEventRecord(e1);
     if (cudaGetLastError() != cudaSuccess || finish_timing(e0, e1, cyc, grid, &t)) goto out;
     if (elements) *elements = (double)grid * threads * (double)iters * 32.0;

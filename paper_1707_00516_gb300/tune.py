@@ -1,6 +1,7 @@
 """Autotuner for batched plans: picks the compare kernel's variant -- operand
 encoding (FP8 or block-scaled FP4 copy) and tile shape (128 x 256, 128 x 128,
-2-CTA pairs; FP4 128 x 224 single or paired) -- by timing each candidate plan
+2-CTA pairs sharing reference stages by multicast or as one 2-SM MMA; FP4
+128 x 224 single or paired either way) -- by timing each candidate plan
 the panels support on the device, and caches the winner.
 
 The cache is a JSON file keyed by the GPU name, the panels' loci counts,
@@ -20,8 +21,8 @@ import torch
 from . import binding as B
 
 CANDIDATES = (B.VARIANT_TENSOR_N256, B.VARIANT_TENSOR_N128, B.VARIANT_TENSOR_PAIR, B.VARIANT_TENSOR_FP4,
-              B.VARIANT_TENSOR_FP4_PAIR)
-FP4_VARIANTS = (B.VARIANT_TENSOR_FP4, B.VARIANT_TENSOR_FP4_PAIR)
+              B.VARIANT_TENSOR_FP4_PAIR, B.VARIANT_TENSOR_PAIR_2SM, B.VARIANT_TENSOR_FP4_PAIR_2SM)
+FP4_VARIANTS = (B.VARIANT_TENSOR_FP4, B.VARIANT_TENSOR_FP4_PAIR, B.VARIANT_TENSOR_FP4_PAIR_2SM)
 
 
 def supported(variant: int, dbs) -> bool:

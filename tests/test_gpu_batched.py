@@ -73,7 +73,8 @@ def _check(panels, batches, k, T):
 
 
 @pytest.mark.parametrize("variant", [B.VARIANT_TENSOR_N256, B.VARIANT_TENSOR_N128, B.VARIANT_TENSOR_PAIR,
-                                     B.VARIANT_TENSOR_FP4, B.VARIANT_TENSOR_FP4_PAIR])
+                                     B.VARIANT_TENSOR_FP4, B.VARIANT_TENSOR_FP4_PAIR, B.VARIANT_TENSOR_PAIR_2SM,
+                                     B.VARIANT_TENSOR_FP4_PAIR_2SM])
 @pytest.mark.parametrize("k,T", [(16, B.NO_THRESHOLD), (32, 40), (17, B.NO_THRESHOLD), (3, 25)])
 def test_plan_run_matches_oracle(setup, variant, k, T):
     s, panels = setup
