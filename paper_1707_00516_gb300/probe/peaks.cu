@@ -135,10 +135,16 @@ struct ProbeCtl {
 // per-stage work of the comparison kernel's MMA thread without its data.  d_out (optional, [128][N] f32) receives the accumulator.
 // cyc[2 * blockIdx.x] = SM clocks of the MMA loop, cyc[2 * blockIdx.x + 1] =
 // its nanoseconds.  A wait that runs out sets *status = 1.
-template <bool F4, int N>
+// NST and SYNC are compile-time so that the issuing loop is as short as the
+// hardware allows: with a runtime stage modulo and three runtime branches in
+// it, the single issuing thread alone held FP4 N = 224 to 79 % and FP8 to 91 %
+// of these rates.
+template <bool F4, int N, int NST, int SYNC>
 __global__ void __launch_bounds__(192, 1)
-    mma_probe_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b, int iters, int nst, int sync,
+    mma_probe_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b, int iters,
                      float *__restrict__ d_out, unsigned long long *__restrict__ cyc, uint32_t *status) {
+    constexpr int nst = NST;
+    constexpr int sync = SYNC;
     extern __shared__ uint8_t smem_raw[];
     constexpr int STAGE = (PM + N) * ROWB;  // a multiple of 1024
     const uint32_t raw = smem_u32(smem_raw);
@@ -182,11 +188,13 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 1 && lane == 0) {
+        const uint64_t ad0 = sw128_desc(smem_u32(base)), bd0 = sw128_desc(smem_u32(base + PM * ROWB));
         const long long c0 = clock64();
         const uint64_t n0 = globaltimer();
         for (int it = 0; it < iters; ++it) {
-            const uint8_t *sA = base + (it % nst) * STAGE;
-            const uint64_t ad = sw128_desc(smem_u32(sA)), bd = sw128_desc(smem_u32(sA + PM * ROWB));
+            // stage it % NST (NST a power of two): constant offsets in the descriptors' address field
+            const uint32_t st = NST == 1 ? 0u : (uint32_t)it & (NST - 1);
+            const uint64_t ad = ad0 + st * (STAGE >> 4), bd = bd0 + st * (STAGE >> 4);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per MMA: +2 in the address field
                 if (F4)
@@ -195,12 +203,12 @@ __global__ void __launch_bounds__(192, 1)
                 else
                     mma_f8(tmem, ad + 2u * kk, bd + 2u * kk, idesc_f8(PM, N), (it | kk) != 0);
             }
-            if (sync & 1) {  // phase 0 of ready_bar completed at set-up: the wait succeeds at once
+            if constexpr ((sync & 1) != 0) {  // phase 0 of ready_bar completed at set-up: the wait succeeds at once
                 while (!mbar_try_wait(smem_u32(&ctl->ready_bar), 0)) {
                 }
             }
-            if (sync & 2) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (sync & 4)
+            if constexpr ((sync & 2) != 0) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if constexpr ((sync & 4) != 0)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(&ctl->stage_bar))
                              : "memory");
@@ -443,10 +451,10 @@ int finish_timing(cudaEvent_t e0, cudaEvent_t e1, const unsigned long long *d_cy
     return 0;
 }
 
-template <bool F4, int N>
-int run_mma(int iters, int grid, int nst, int sync, const uint8_t *a_host, const uint8_t *b_host, float *d_host,
-            Timed *t) {
-    auto kern = mma_probe_kernel<F4, N>;
+template <bool F4, int N, int NST, int SYNC>
+int run_mma(int iters, int grid, const uint8_t *a_host, const uint8_t *b_host, float *d_host, Timed *t) {
+    auto kern = mma_probe_kernel<F4, N, NST, SYNC>;
+    constexpr int nst = NST;
     // > half of the SM's shared memory: one CTA per SM (each holds all 512 TMEM columns)
     const size_t need = 1024 + (size_t)nst * (PM + N) * ROWB + 64;
     const size_t smem = need < 120 * 1024 ? 120 * 1024 : need;
@@ -471,7 +479,7 @@ int run_mma(int iters, int grid, int nst, int sync, const uint8_t *a_host, const
     }
     if (cudaMemset(status, 0, 4) || cudaEventCreate(&e0) || cudaEventCreate(&e1)) goto out;
     cudaEventRecord(e0);
-    kern<<<grid, 192, smem>>>(a, b, iters, nst, sync, d, cyc, status);
+    kern<<<grid, 192, smem>>>(a, b, iters, d, cyc, status);
     cudaEventRecord(e1);
     if (cudaGetLastError() != cudaSuccess || finish_timing(e0, e1, cyc, grid, t)) goto out;
     if (cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost)) goto out;
@@ -506,9 +514,9 @@ extern "C" {
 
 // One tcgen05 MMA probe launch.  f4: 0 kind::f8f6f4 (n = 256), 1 kind::mxf4
 // (n = 224 or 256).  nst: operand stages cycled through (1 .. 4; 1 re-reads
-// the same shared memory every round).  sync, per round of 4 MMAs: bit 0 a
-// wait on a completed mbarrier phase, bit 1 a tcgen05 fence, bit 2 a commit.
-// grid <= 0: one CTA per SM.  a_host [128][128] and b_host
+// the same shared memory every round; 1 or 4).  sync: 0, or 7 for a wait on a
+// completed mbarrier phase, a tcgen05 fence and a commit every round of 4
+// MMAs.  grid <= 0: one CTA per SM.  a_host [128][128] and b_host
 // [n][128] operand bytes (both NULL: filled on the device); d_host [128][n]
 // (optional, grid must be 1) receives D.  Outputs: event ms, median clocks
 // and MHz of the MMA loop over CTAs.  Returns 0, 1 (CUDA error or bad
@@ -516,17 +524,25 @@ extern "C" {
 int fastid_peaks_mma(int f4, int n, int iters, int grid, int nst, int sync, const uint8_t *a_host,
                      const uint8_t *b_host, float *d_host, double *ms, double *clocks, double *mhz) {
     if (grid <= 0) grid = sms();
-    if (iters < 1 || nst < 1 || nst > 4 || (d_host && grid != 1) || (!a_host) != (!b_host)) return 1;
+    if (iters < 1 || (nst != 1 && nst != 4) || (sync != 0 && sync != 7) || (d_host && grid != 1) ||
+        (!a_host) != (!b_host))
+        return 1;
     Timed t;
     int rc;
+#define FASTID_PROBE_RUN(F4, N)                                                                                   \
+    (nst == 1 ? (sync ? run_mma<F4, N, 1, 7>(iters, grid, a_host, b_host, d_host, &t)                             \
+                      : run_mma<F4, N, 1, 0>(iters, grid, a_host, b_host, d_host, &t))                            \
+              : (sync ? run_mma<F4, N, 4, 7>(iters, grid, a_host, b_host, d_host, &t)                             \
+                      : run_mma<F4, N, 4, 0>(iters, grid, a_host, b_host, d_host, &t)))
     if (!f4 && n == 256)
-        rc = run_mma<false, 256>(iters, grid, nst, sync, a_host, b_host, d_host, &t);
+        rc = FASTID_PROBE_RUN(false, 256);
     else if (f4 && n == 224)
-        rc = run_mma<true, 224>(iters, grid, nst, sync, a_host, b_host, d_host, &t);
+        rc = FASTID_PROBE_RUN(true, 224);
     else if (f4 && n == 256)
-        rc = run_mma<true, 256>(iters, grid, nst, sync, a_host, b_host, d_host, &t);
+        rc = FASTID_PROBE_RUN(true, 256);
     else
         return 1;
+#undef FASTID_PROBE_RUN
     if (ms) *ms = t.ms;
     if (clocks) *clocks = t.clocks_med;
     if (mhz) *mhz = t.mhz_med;
