@@ -136,8 +136,8 @@ class FormTuner:
 
     def choose(self, ctx: B.Context, db, queries: torch.Tensor, modes: torch.Tensor, k: int,
                threshold: int = B.NO_THRESHOLD) -> int:
-        """FASTID_FORM_* for these calls: cached, else measured now (the
-        context's form is left as it was)."""
+        """FASTID_FORM_* for these calls: cached, else measured now (a
+        measurement leaves the context's form at FASTID_FORM_AUTO)."""
         t = self._tuner
         key = self.key(db, queries.size(0), k, threshold)
         with t._lock:
