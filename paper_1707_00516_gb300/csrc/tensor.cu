@@ -209,16 +209,27 @@ __device__ __forceinline__ void cluster_sync() {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// The MMA issuer is a whole converged warp: every lane runs its loop and its
+// waits, and one lane, picked by elect.sync (the same lane every time in a
+// converged warp), issues each tcgen05.mma and tcgen05.commit -- a commit
+// tracks the operations of the thread that executes it.  A single lane
+// running the loop alone, inside a branch the rest of its warp skips, left
+// the tensor pipe idle for ~180 of every ~630 cycles of an FP4 stage.
+#define FASTID_ELECT "elect.sync _|e, 0xffffffff;\n\t"
+
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+    asm volatile("{\n\t.reg .pred e;\n\t" FASTID_ELECT
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar)
                  : "memory");
 }
 
-// Arrive (when this thread's prior tcgen05 operations complete) on the
+// Arrive (when the elected lane's prior tcgen05 operations complete) on the
 // mbarrier at the same offset in every CTA of ctamask.
 __device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t ctamask) {
     asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "{\n\t.reg .pred e;\n\t" FASTID_ELECT
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n\t}" ::"r"(
+            bar),
         "h"(ctamask)
         : "memory");
 }
@@ -251,17 +262,21 @@ __device__ __forceinline__ void tma_load_2d_cg2(uint32_t dst, const CUtensorMap 
         : "memory");
 }
 
-// Arrive on the mbarrier at the same offset in every CTA of ctamask when this
-// thread's prior cta_group::2 tcgen05 operations complete.
+// Arrive on the mbarrier at the same offset in every CTA of ctamask when the
+// elected lane's prior cta_group::2 tcgen05 operations complete.
 __device__ __forceinline__ void tc_commit_cg2_mc(uint32_t bar, uint16_t ctamask) {
     asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "{\n\t.reg .pred e;\n\t" FASTID_ELECT
+        "@e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n\t}" ::"r"(
+            bar),
         "h"(ctamask)
         : "memory");
 }
 
 __device__ __forceinline__ void tc_commit_cg2(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+    asm volatile("{\n\t.reg .pred e;\n\t" FASTID_ELECT
+                 "@e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar)
+                 : "memory");
 }
 
 // 32 lanes x 16 consecutive 32-bit columns, every column the value v.
@@ -276,22 +291,23 @@ __device__ __forceinline__ void tmem_fill16(uint32_t taddr, uint32_t v) {
 // The 4 MMAs of one 128-byte K stage into accumulator d: operand descriptors
 // +0, +2, +4, +6 (32 bytes of K each in the address field), the first MMA
 // accumulating only when acc != 0, the others always; one asm block with its
-// predicates set once.  At FP4 speed a stage is ~450 cycles of MMA work, and
-// the issuing thread's own instruction path per stage (waits, descriptors,
-// issue, commit) bounds the MMA rate, so it is kept this short.
+// predicates set once, issued by the warp's elected lane.  At FP4 speed a
+// stage is ~450 cycles of MMA work and the tensor pipe holds little more
+// than one MMA in its queue, so the issuer's own path between stages (wait,
+// descriptors, commit) must stay within about one MMA's time.
 template <bool F4, bool CG2>
 __device__ __forceinline__ void mma_stage4(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t sfa,
                                            uint32_t sfb, uint32_t acc) {
     const uint64_t a1 = ad + 2u, a2 = ad + 4u, a3 = ad + 6u, b1 = bd + 2u, b2 = bd + 4u, b3 = bd + 6u;
     if constexpr (F4) {
 #define FASTID_MMA4_F4(CG)                                                                                         \
-    asm volatile("{\n\t.reg .pred p, q;\n\t"                                                                    \
+    asm volatile("{\n\t.reg .pred p, q, e;\n\t" FASTID_ELECT                                                                    \
                  "setp.ne.b32 p, %12, 0;\n\t"                                                                  \
                  "setp.ne.b32 q, %12, 0xFFFFFFFF;\n\t"                                                         \
-                 "tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %1, %5, %9, [%10], [%11], p;\n\t" \
-                 "tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %2, %6, %9, [%10], [%11], q;\n\t" \
-                 "tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %3, %7, %9, [%10], [%11], q;\n\t" \
-                 "tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %4, %8, %9, [%10], [%11], q;\n\t}" \
+                 "@e tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %1, %5, %9, [%10], [%11], p;\n\t" \
+                 "@e tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %2, %6, %9, [%10], [%11], q;\n\t" \
+                 "@e tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %3, %7, %9, [%10], [%11], q;\n\t" \
+                 "@e tcgen05.mma.cta_group::" CG ".kind::mxf4.block_scale.scale_vec::2X [%0], %4, %8, %9, [%10], [%11], q;\n\t}" \
                  ::"r"(d), "l"(ad), "l"(a1), "l"(a2), "l"(a3), "l"(bd), "l"(b1), "l"(b2), "l"(b3), "r"(idesc),      \
                  "r"(sfa), "r"(sfb), "r"(acc)                                                                     \
                  : "memory")
@@ -304,13 +320,13 @@ __device__ __forceinline__ void mma_stage4(uint32_t d, uint64_t ad, uint64_t bd,
         (void)sfa;
         (void)sfb;
 #define FASTID_MMA4_F8(CG)                                                                                         \
-    asm volatile("{\n\t.reg .pred p, q;\n\t"                                                                    \
+    asm volatile("{\n\t.reg .pred p, q, e;\n\t" FASTID_ELECT                                                                    \
                  "setp.ne.b32 p, %10, 0;\n\t"                                                                  \
                  "setp.ne.b32 q, %10, 0xFFFFFFFF;\n\t"                                                         \
-                 "tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %1, %5, %9, p;\n\t"                          \
-                 "tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %2, %6, %9, q;\n\t"                          \
-                 "tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %3, %7, %9, q;\n\t"                          \
-                 "tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %4, %8, %9, q;\n\t}"                         \
+                 "@e tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %1, %5, %9, p;\n\t"                          \
+                 "@e tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %2, %6, %9, q;\n\t"                          \
+                 "@e tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %3, %7, %9, q;\n\t"                          \
+                 "@e tcgen05.mma.cta_group::" CG ".kind::f8f6f4 [%0], %4, %8, %9, q;\n\t}"                         \
                  ::"r"(d), "l"(ad), "l"(a1), "l"(a2), "l"(a3), "l"(bd), "l"(b1), "l"(b2), "l"(b3), "r"(idesc),      \
                  "r"(acc)                                                                                         \
                  : "memory")
@@ -768,10 +784,11 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer (2-SM pairs: the even CTA's) ----------------
+        // The whole warp, converged; one elected lane issues (see tc_commit).
         // Per stage: one barrier wait (inline when the stage is already full),
         // the stage's descriptors as constant offsets from the first stage's,
         // four MMAs in one asm block, one commit (see mma_stage4).
-        if (lane == 0 && (!CG2 || rank == 0)) {
+        if (!CG2 || rank == 0) {
             constexpr int MM = CG2 ? 2 * TC_BM : TC_BM;
             constexpr uint32_t idesc = F4 ? idesc_mxf4(MM, BN) : idesc_f8(MM, BN);
             constexpr uint32_t A_STEP = TC_A_BYTES >> 4, B_STEP = S::B_BYTES >> 4;  // descriptor units a stage
