@@ -296,10 +296,10 @@ def kernel_source_hash(form: str) -> str:
 # (profiles/), keyed by form and workload, with the source hash it was taken
 # at.  A changed kernel reports null.
 NCU_TRAFFIC = {
-    # profiles/tensor_kernel_fp4_c3_2048x20M.md: dram__bytes_read.sum 102.44 GB + dram__bytes_write.sum 42.96 MB
-    "fp4/c3": (102.437241344e9 + 42.96192e6, "e79e3e6f0b13167e"),
-    # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 163.52 GB + dram__bytes_write.sum 79.86 MB
-    "fp8/c3": (163.516140288e9 + 79.859968e6, "e79e3e6f0b13167e"),
+    # profiles/tensor_kernel_fp4_c3_2048x20M.md: dram__bytes_read.sum 91.47 GB + dram__bytes_write.sum 43.73 MB
+    "fp4/c3": (91.47440768e9 + 43.728384e6, "cb12197d40c8241a"),
+    # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 159.91 GB + dram__bytes_write.sum 79.03 MB
+    "fp8/c3": (159.906035712e9 + 79.026176e6, "cb12197d40c8241a"),
     # profiles/plain_kernel_c3_2048x20M.md: dram__bytes_read.sum 20.39 GB + dram__bytes_write.sum 17.26 MB
     "plain/c3": (20.391288576e9 + 17.264896e6, "2f82776dab16ea77"),
 }
