@@ -124,13 +124,18 @@ def measure(target_ms: float = 40.0) -> dict:
                 raise RuntimeError(f"fastid_peaks_alu({op}) returned {rc}")
             return ms.value, clk.value, mhz.value, el.value
         ms, clk, mhz, el, iters = _calibrated(run, target_ms, 256)
-        # per-SM clocks of one CTA's loop; two CTAs share an SM
-        return {"per_s": el / (ms / 1e3), "per_clk_sm": el / n_sms / clk, "sm_mhz": mhz, "ms": ms, "counts": name}
+        # per SM per clock over the whole launch (event time x measured SM
+        # clock): two CTAs of 1024 threads a SM run at once only below 33
+        # registers a thread (the carry-save probe holds more, so its CTAs run
+        # one at a time, and one CTA's own clocks would count its SM twice)
+        return {"per_s": el / (ms / 1e3), "per_clk_sm": el / n_sms / (ms * 1e3 * mhz), "sm_mhz": mhz, "ms": ms,
+                "counts": name}
 
     out["popc"] = alu(0, "POPC")
     out["lop3"] = alu(1, "LOP3")
     out["and_popc_add"] = alu(2, "POPC in AND + POPC + IADD3/2")
     out["harley_seal"] = alu(3, "word pairs counted by AND + carry-save tree + POPC/8")
+    out["carry_save8"] = alu(4, "word pairs counted by the plain kernel's step: 8 AND + 4 full adders + 4 POPC + adds")
 
     def b1():
         def run(iters):
@@ -141,7 +146,8 @@ def measure(target_ms: float = 40.0) -> dict:
                 raise RuntimeError(f"fastid_peaks_b1 returned {rc}")
             return ms.value, clk.value, mhz.value, bm.value
         ms, clk, mhz, bm, iters = _calibrated(run, target_ms, 256)
-        return {"bit_macs_per_s": bm / (ms / 1e3), "bit_macs_per_clk_sm": bm / n_sms / clk, "sm_mhz": mhz, "ms": ms}
+        return {"bit_macs_per_s": bm / (ms / 1e3), "bit_macs_per_clk_sm": bm / n_sms / (ms * 1e3 * mhz), "sm_mhz": mhz,
+                "ms": ms}
 
     out["b1_and_popc"] = b1()
     out["sms"] = n_sms

@@ -269,15 +269,21 @@ __global__ void fill_kernel(uint8_t *p, size_t n, bool f4) {
 //   op 0: x = popc(x)                      (1 POPC per element)
 //   op 1: x = lop3(x, y, z, 0x96)          (1 LOP3 per element)
 //   op 2: acc += popc(r & acc) + popc(q & acc) over 4 x 4 accumulators (the
-//         plain form's inner sequence: 2 AND, 2 POPC, 1 IADD3 per two words;
-//         the accumulator stands in for the operand loads so that nothing
-//         is loop-invariant)
+//         AND + POPC sequence: 2 AND, 2 POPC, 1 IADD3 per two words; the
+//         accumulator stands in for the operand loads so that nothing is
+//         loop-invariant)
 //   op 3: the same count by a carry-save (Harley-Seal) tree over 8 ANDed
 //         words at a time, for 4 (reference, query) pairs: per 8 words 8
 //         AND, 7 carry-save adders (2 LOP3 each: sum 0x96, majority 0xE8),
 //         one POPC of the eights and one add; the pair's `fours` word stands
 //         in for the operand loads
-// Counted elements: op 0 POPC, op 1 LOP3, op 2 POPC, op 3 word pairs.
+//   op 4: the plain kernel's step (and_popc8): per 8 words 8 AND, 4 full
+//         adders (LOP3 sum and majority), 4 POPC and the weighted
+//         multiply-adds, on 4 accumulators a thread that are the next step's
+//         query words
+// Counted elements: op 0 POPC, op 1 LOP3, op 2 POPC, op 3 and 4 word pairs.
+// Op 3 holds 49 registers a thread, so its two CTAs a SM run one after the
+// other: per-SM rates are taken over the whole launch.
 __device__ __forceinline__ uint32_t lop3_sum(uint32_t a, uint32_t b, uint32_t c) {
     uint32_t d;
     asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
@@ -292,6 +298,30 @@ __device__ __forceinline__ uint32_t lop3_maj(uint32_t a, uint32_t b, uint32_t c)
 __device__ __forceinline__ void csa(uint32_t &hi, uint32_t &lo, uint32_t a, uint32_t b, uint32_t c) {
     hi = lop3_maj(a, b, c);
     lo = lop3_sum(a, b, c);
+}
+
+// Full adder as the plain kernel writes it (non-volatile LOP3, so that the
+// compiler schedules it freely): sum 0x96, carry (majority) 0xE8.
+__device__ __forceinline__ void fa_probe(uint32_t &sum, uint32_t &carry, uint32_t a, uint32_t b, uint32_t c) {
+    asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(sum) : "r"(a), "r"(b), "r"(c));
+    asm("lop3.b32 %0, %1, %2, %3, 0xE8;" : "=r"(carry) : "r"(a), "r"(b), "r"(c));
+}
+
+// The plain comparison kernel's word-pair step, restated: popc of the AND of
+// 8 word pairs added to acc through four full adders (one LOP3 for the sum,
+// one for the carry) and weighted multiply-adds by an opaque 2.
+__device__ __forceinline__ uint32_t and_popc8_probe(const uint32_t (&r)[8], uint32_t q0, uint32_t q1, uint32_t q2,
+                                                    uint32_t q3, uint32_t acc, uint32_t two) {
+    // the query words of each full adder's three inputs differ, so that no
+    // adder factors into (adder of reference words) AND q
+    const uint32_t x0 = r[0] & q0, x1 = r[1] & q1, x2 = r[2] & q2, x3 = r[3] & q3, x4 = r[4] & q1, x5 = r[5] & q2,
+                   x6 = r[6] & q3, x7 = r[7] & q0;
+    uint32_t s1, c1, s2, c2, s3, c3, t, d;
+    fa_probe(s1, c1, x0, x1, x2);
+    fa_probe(s2, c2, x3, x4, x5);
+    fa_probe(s3, c3, s1, s2, x6);
+    fa_probe(t, d, c1, c2, c3);
+    return (__popc(d) * two + __popc(t)) * two + (acc + __popc(s3) + __popc(x7));
 }
 
 template <int OP>
@@ -354,6 +384,25 @@ __global__ void __launch_bounds__(1024) alu_probe_kernel(uint32_t seed, int iter
         }
 #pragma unroll
         for (int p = 0; p < 4; ++p) res += 8 * tot[p] + 4 * __popc(fours[p]) + 2 * __popc(twos[p]) + __popc(ones[p]);
+    } else if (OP == 4) {
+        const uint32_t two = seed == 0xFFFFFFFFu ? 3u : 2u;  // 2, opaque to the compiler
+        // four accumulators; they are the query words of the next step's
+        // ANDs (each (reference word, query word) pair once a step), so nothing
+        // is loop-invariant
+        uint32_t a0 = x[0] ^ x[7], a1 = x[1] ^ x[6], a2 = x[2] ^ x[5], a3 = x[3] ^ x[4];
+        for (int it = 0; it < iters; ++it) {
+            const uint32_t b0 = and_popc8_probe(x, a0, a1, a2, a3, a0, two);
+            const uint32_t b1 = and_popc8_probe(x, a1, a2, a3, a0, a1, two);
+            const uint32_t b2 = and_popc8_probe(x, a2, a3, a0, a1, a2, two);
+            const uint32_t b3 = and_popc8_probe(x, a3, a0, a1, a2, a3, two);
+            a0 = b0;
+            a1 = b1;
+            a2 = b2;
+            a3 = b3;
+        }
+        uint32_t acc[4] = {a0, a1, a2, a3};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) res += acc[j];
     } else {
         uint32_t acc[4][4];
 #pragma unroll
@@ -549,11 +598,12 @@ int fastid_peaks_mma(int f4, int n, int iters, int grid, int nst, int sync, cons
     return rc;
 }
 
-// ALU probe (op 0 POPC, 1 LOP3, 2 AND + POPC + IADD3) on blocks_per_sm
+// ALU probe (op 0 POPC, 1 LOP3, 2 AND + POPC + IADD3, 3 Harley-Seal, 4 the
+// plain kernel's carry-save step) on blocks_per_sm
 // CTAs of 1024 threads per SM.  *elements: counted operations of the launch.
 int fastid_peaks_alu(int op, int iters, int blocks_per_sm, double *ms, double *clocks, double *mhz,
                      double *elements) {
-    if (op < 0 || op > 3 || iters < 1 || blocks_per_sm < 1) return 1;
+    if (op < 0 || op > 4 || iters < 1 || blocks_per_sm < 1) return 1;
     const int grid = sms() * blocks_per_sm, threads = 1024;
     uint32_t *out = nullptr;
     unsigned long long *cyc = nullptr;
@@ -568,6 +618,7 @@ int fastid_peaks_alu(int op, int iters, int blocks_per_sm, double *ms, double *c
     if (op == 1) alu_probe_kernel<1><<<grid, threads>>>(12345u, iters, out, cyc);
     if (op == 2) alu_probe_kernel<2><<<grid, threads>>>(12345u, iters, out, cyc);
     if (op == 3) alu_probe_kernel<3><<<grid, threads>>>(12345u, iters, out, cyc);
+    if (op == 4) alu_probe_kernel<4><<<grid, threads>>>(12345u, iters, out, cyc);
     cudaEventRecord(e1);
     if (cudaGetLastError() != cudaSuccess || finish_timing(e0, e1, cyc, grid, &t)) goto out;
     if (elements) *elements = (double)grid * threads * (double)iters * 32.0;

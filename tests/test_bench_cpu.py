@@ -67,12 +67,13 @@ def test_roofline_peaks_from_probe():
     """Each form's peak is the probe's per-clock rate x SMs x the maximum SM
     clock, in the form's own unit."""
     import bench
-    probe = {"popc": {"per_clk_sm": 16.0}, "fp8_f8f6f4": {"flops_per_clk_sm": 16384.0},
+    probe = {"popc": {"per_clk_sm": 16.0}, "carry_save8": {"per_clk_sm": 26.5},
+             "fp8_f8f6f4": {"flops_per_clk_sm": 16384.0},
              "fp4_mxf4_n224": {"flops_per_clk_sm": 32768.0, "shape": "M128xN224xK64"},
              "fp4_mxf4_n256": {"flops_per_clk_sm": 32760.0, "shape": "M128xN256xK64"}}
     mhz = float(bench.load_peaks()[0].get("sm_max_mhz", 2070.0))
     p, unit, _ = bench.roof_peak("plain", probe, 152)
-    assert unit == "Tpopc/s" and abs(p - 16 * 152 * mhz * 1e6 / 1e12) < 1e-9
+    assert unit == "Tpopc/s" and abs(p - 26.5 * 152 * mhz * 1e6 / 1e12) < 1e-9
     p8, unit, _ = bench.roof_peak("fp8", probe, 152)
     assert unit == "TFLOP/s" and abs(p8 - 16384 * 152 * mhz * 1e6 / 1e12) < 1e-6
     assert bench.roof_peak("fp8packed", probe, 152)[0] == p8

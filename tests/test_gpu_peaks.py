@@ -47,6 +47,6 @@ def test_measure_rates_positive():
     m = peaks.measure(target_ms=5.0)
     for key in ("fp8_f8f6f4", "fp4_mxf4_n224", "fp4_mxf4_n256"):
         assert m[key]["tflops"] > 0 and m[key]["flops_per_clk_sm"] > 0
-    for key in ("popc", "lop3", "and_popc_add", "harley_seal"):
+    for key in ("popc", "lop3", "and_popc_add", "harley_seal", "carry_save8"):
         assert m[key]["per_s"] > 0 and m[key]["per_clk_sm"] > 0
     assert m["b1_and_popc"]["bit_macs_per_s"] > 0
