@@ -553,12 +553,15 @@ fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint
     FASTID_CUDA(ctx, scr.alloc(cv.off));
     uint8_t *a = at<uint8_t>(scr.p, o_a);
     float *qconst = at<float>(scr.p, o_c);
+    // spread the input queries over every tile of the operand (see
+    // spread_row_to_query)
+    const int64_t spread = n_q_pad / tensor_tile_q();
     if (f4)
         FASTID_CUDA(ctx, launch_queries_e2m1(q, ld_q, n_q, db->n_words64, db->n_loci, modes, n_q_pad, kbytes, a,
-                                             qconst, s));
+                                             qconst, spread, s));
     else
         FASTID_CUDA(ctx, launch_queries_e4m3(q, ld_q, n_q, db->n_words64, db->n_loci, modes, n_q_pad, kbytes, a,
-                                             qconst, pk, s));
+                                             qconst, pk, spread, s));
     count_launches(ctx, 1);
     FASTID_CUDA(ctx, make_operand_map(&L.map_a[0], a, n_q_pad, kbytes, tensor_tile_q()));
     L.n_panels = 1;
@@ -571,6 +574,7 @@ fastid_status prepare_tensor(fastid_ctx *ctx, const fastid_refdb *db, const uint
     L.n_rt[0] = n_rt;
     L.kpad[0] = kbytes;
     L.qconst[0] = qconst;
+    L.qspread[0] = (int32_t)spread;
     L.status = ctx->dev_status;
     return FASTID_OK;
 }

@@ -118,6 +118,24 @@ struct TcSched {
 };
 
 // Host-side description of one tensor-form launch over up to TC_MAXP panels.
+// Query spreading.  The work of a query tile depends on its queries (a
+// mixture under Eq. 1 keeps beating its current k-th best for longer than an
+// individual under the mismatch count, and its tile's epilogue competes with
+// the MMA issuer for the SM), and callers often pass queries grouped by kind,
+// which left whole tiles -- and the groups that own them -- slower than the
+// rest.  So a tensor call spreads the input queries over the operand's s tiles
+// with stride s: operand row r (tile r / 128, lane r % 128) holds input query
+// (r % 128) s + r / 128, and input query q sits at row (q % s) 128 + q / s.
+// s <= 1 is the identity.  A bijection on [0, 128 s); rows whose query is
+// >= n_q are padding.  (2048 x 20M, top-32: FP4 20.4 -> 18.9 ms, FP8 40.8 ->
+// 38.2 ms with the C3 queries, individuals first and mixtures after.)
+__host__ __device__ __forceinline__ int64_t spread_row_to_query(int64_t r, int64_t s) {
+    return s <= 1 ? r : (r % TC_TILE_Q) * s + r / TC_TILE_Q;
+}
+__host__ __device__ __forceinline__ int64_t spread_query_to_row(int64_t q, int64_t s) {
+    return s <= 1 ? q : (q % s) * TC_TILE_Q + q / s;
+}
+
 struct TcLaunch {
     int32_t n_panels;
     int32_t pair;  // 2-CTA clusters sharing reference stages (groups are clusters, tiles are pairs)
@@ -131,6 +149,9 @@ struct TcLaunch {
     int64_t n_rt[TC_MAXP];
     int32_t kpad[TC_MAXP];  // operand row bytes (a multiple of 128)
     const float *qconst[TC_MAXP];
+    // Query spreading (see spread_row_to_query): the operand's tiles, or 0 / 1
+    // where operand row r holds input query r (batched plans).
+    int32_t qspread[TC_MAXP];
     TcSched sched[TC_MAXP];
     int32_t order[TC_MAXP];  // panel order of every group's walk
     int32_t n_groups;  // work groups of the launch: max of a * b over panels
@@ -215,7 +236,7 @@ cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_src
                              int32_t kpad, uint8_t *out, int max_blocks, cudaStream_t s);
 cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
                                 const uint8_t *modes, int64_t n_q_pad, int32_t kpad, uint8_t *out, float *qconst,
-                                bool half, cudaStream_t s);
+                                bool half, int64_t spread, cudaStream_t s);
 // TMA map over packed rows for packed-reference (PK) launches: boxes of 2
 // words x 256 rows (FP8 stages) or 4 words x 224 rows (FP4 stages).
 cudaError_t make_packed_map(CUtensorMap *map, const uint64_t *packed, int64_t rows, int64_t ld64, int box_words = 2,
@@ -228,7 +249,7 @@ cudaError_t launch_refs_e2m1(const uint64_t *packed, int64_t ld64, int64_t n_src
                              int32_t kbytes, uint8_t *out, int max_blocks, cudaStream_t s);
 cudaError_t launch_queries_e2m1(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
                                 const uint8_t *modes, int64_t n_q_pad, int32_t kbytes, uint8_t *out, float *qconst,
-                                cudaStream_t s);
+                                int64_t spread, cudaStream_t s);
 
 cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s);
 cudaError_t launch_prep_jobs(const PrepJob *jobs, int64_t n_jobs, cudaStream_t s);

@@ -253,6 +253,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
         L.n_rt[p] = n_rt[p];
         L.kpad[p] = (int32_t)kbytes(p);
         L.qconst[p] = reinterpret_cast<const float *>(W + o_qc[p]);
+        L.qspread[p] = 1;  // prep jobs place every batch row themselves
     }
     L.k = k;
     L.epi = EPI_TOPK;

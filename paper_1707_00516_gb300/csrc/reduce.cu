@@ -80,6 +80,7 @@ struct MergeSched {
     // this launch's reference indices taken + ref_offset
     int32_t accumulate;
     int64_t ref_offset;
+    int64_t qspread;  // single-call jobs: output j is input query j (see spread_query_to_row)
 };
 
 // Debug builds (FASTID_DEBUG) check every slot a merge reads against the
@@ -115,7 +116,7 @@ __global__ void topk_merge_sched_kernel(const uint64_t *__restrict__ partial, co
         jb.out_s = out_s + j * k;
         jb.out_i = out_i + j * k;
         jb.panel = 0;
-        jb.q = (int32_t)j;
+        jb.q = (int32_t)spread_query_to_row(j, M.qspread);  // its operand row
     }
     const TcSched &sc = M.sc[jb.panel];
     const int64_t qt = jb.q / TC_TILE_Q, ql = jb.q - qt * TC_TILE_Q;
@@ -358,6 +359,7 @@ cudaError_t launch_merge_sched(const uint64_t *partial, const TcLaunch &L, const
     for (int p = 0; p < TC_MAXP; ++p) M.sc[p] = L.sched[p];
     M.n_slots = L.n_slots;
     M.status = L.status;
+    M.qspread = L.qspread[0];
     const int wpb = 8;
     int64_t blocks = (n_jobs + wpb - 1) / wpb;
     topk_merge_sched_kernel<<<(unsigned)blocks, wpb * 32, 0, s>>>(partial, M, jobs, n_jobs, out_scores, out_idx);

@@ -86,6 +86,7 @@ struct PanelDesc {
     int32_t n_kb;         // K stages of 128 operand bytes
     TcSched sc;
     const float *qconst;  // c_q per padded query row
+    int32_t qspread;      // see spread_row_to_query
 };
 
 struct TcMaps {
@@ -920,9 +921,10 @@ __global__ void __launch_bounds__(PK ? TC_THREADS + pk_threads(KM) : TC_THREADS,
                 const int64_t re = min(rc + W.chunk, W.r_hi);
                 for (int32_t qq = W.q_lo; qq < W.q_hi && ok; ++qq) {
                     const int64_t qt = PAIR ? 2 * (int64_t)qq + rank : qq;
-                    const int64_t q = qt * TC_BM + row;
+                    const int64_t qr = qt * TC_BM + row;                     // operand row
+                    const int64_t q = spread_row_to_query(qr, P.qspread);  // input query
                     const bool qvalid = q < P.n_q;
-                    const float cq = P.qconst[q];
+                    const float cq = P.qconst[qr];
                     const float cut0 = qvalid ? tplus1 - cq : -__int_as_float(0x7f800000);
                     uint64_t *slot = args.partial + (W.slot + (qq - W.q_lo)) * (int64_t)k * TC_BM + row;
                     if (topk && rc > W.r_lo) {
@@ -1190,14 +1192,17 @@ __device__ __forceinline__ void encode_query_row_f4(const uint64_t *__restrict__
     if (lane == 0) *qc = mis ? (float)pc : 0.f;
 }
 
+// Operand row r encodes input query spread_row_to_query(r, spread).
 __global__ void queries_e2m1_kernel(const uint64_t *__restrict__ q, int64_t ld_q, int64_t n_q, int32_t n_words,
                                     int32_t n_loci, const uint8_t *__restrict__ modes, int64_t n_q_pad,
-                                    int32_t kbytes, uint8_t *__restrict__ out, float *__restrict__ qconst) {
+                                    int32_t kbytes, uint8_t *__restrict__ out, float *__restrict__ qconst,
+                                    int64_t spread) {
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n_q_pad; r += warps_total) {
-        const bool valid = r < n_q;
-        encode_query_row_f4(valid ? q + r * ld_q : nullptr, valid && modes[r] == FASTID_MODE_MISMATCH, n_words,
+        const int64_t src = spread_row_to_query(r, spread);
+        const bool valid = src < n_q;
+        encode_query_row_f4(valid ? q + src * ld_q : nullptr, valid && modes[src] == FASTID_MODE_MISMATCH, n_words,
                             n_loci, kbytes, out + r * (int64_t)kbytes, qconst + r, lane);
     }
 }
@@ -1205,13 +1210,14 @@ __global__ void queries_e2m1_kernel(const uint64_t *__restrict__ q, int64_t ld_q
 __global__ void queries_e4m3_kernel(const uint64_t *__restrict__ q, int64_t ld_q, int64_t n_q, int32_t n_words,
                                     int32_t n_loci, const uint8_t *__restrict__ modes, int64_t n_q_pad,
                                     int32_t kpad, uint8_t *__restrict__ out, float *__restrict__ qconst,
-                                    uint32_t one, bool pk) {
+                                    uint32_t one, bool pk, int64_t spread) {
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n_q_pad; r += warps_total) {
-        const bool valid = r < n_q;
-        encode_query_row(valid ? q + r * ld_q : nullptr, valid && modes[r] == FASTID_MODE_MISMATCH, n_words, n_loci,
-                         kpad, out + r * (int64_t)kpad, qconst + r, lane, one, pk);
+        const int64_t src = spread_row_to_query(r, spread);
+        const bool valid = src < n_q;
+        encode_query_row(valid ? q + src * ld_q : nullptr, valid && modes[src] == FASTID_MODE_MISMATCH, n_words,
+                         n_loci, kpad, out + r * (int64_t)kpad, qconst + r, lane, one, pk);
     }
 }
 
@@ -1287,11 +1293,11 @@ cudaError_t launch_refs_e2m1(const uint64_t *packed, int64_t ld64, int64_t n_src
 
 cudaError_t launch_queries_e2m1(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
                                 const uint8_t *modes, int64_t n_q_pad, int32_t kbytes, uint8_t *out, float *qconst,
-                                cudaStream_t s) {
+                                int64_t spread, cudaStream_t s) {
     int64_t blocks = (n_q_pad + 7) / 8;
     if (blocks > 65535) blocks = 65535;
     queries_e2m1_kernel<<<(unsigned)blocks, 256, 0, s>>>(q, ld_q, n_q, n_words, n_loci, modes, n_q_pad, kbytes, out,
-                                                         qconst);
+                                                         qconst, spread);
     return cudaGetLastError();
 }
 
@@ -1307,11 +1313,11 @@ cudaError_t launch_refs_e4m3(const uint64_t *packed, int64_t ld64, int64_t n_src
 
 cudaError_t launch_queries_e4m3(const uint64_t *q, int64_t ld_q, int64_t n_q, int32_t n_words, int32_t n_loci,
                                 const uint8_t *modes, int64_t n_q_pad, int32_t kpad, uint8_t *out, float *qconst,
-                                bool half, cudaStream_t s) {
+                                bool half, int64_t spread, cudaStream_t s) {
     int64_t blocks = (n_q_pad + 7) / 8;
     if (blocks > 65535) blocks = 65535;
     queries_e4m3_kernel<<<(unsigned)blocks, 256, 0, s>>>(q, ld_q, n_q, n_words, n_loci, modes, n_q_pad, kpad, out,
-                                                         qconst, half ? 0x30u : 0x38u, half);
+                                                         qconst, half ? 0x30u : 0x38u, half, spread);
     return cudaGetLastError();
 }
 
@@ -1422,6 +1428,7 @@ cudaError_t launch_tensor_multi(int bn, const TcLaunch &L, cudaStream_t s) {
         a.panel[p].n_kb = L.kpad[p] / TC_BK;
         a.panel[p].sc = L.sched[p];
         a.panel[p].qconst = L.qconst[p];
+        a.panel[p].qspread = L.qspread[p];
         a.order[p] = L.order[p];
     }
     a.threshold = L.threshold;
