@@ -296,12 +296,12 @@ def kernel_source_hash(form: str) -> str:
 # (profiles/), keyed by form and workload, with the source hash it was taken
 # at.  A changed kernel reports null.
 NCU_TRAFFIC = {
-    # profiles/tensor_kernel_fp4_c3_2048x20M.md: dram__bytes_read.sum 91.47 GB + dram__bytes_write.sum 43.73 MB
-    "fp4/c3": (91.47440768e9 + 43.728384e6, "cb12197d40c8241a"),
-    # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 159.91 GB + dram__bytes_write.sum 79.03 MB
-    "fp8/c3": (159.906035712e9 + 79.026176e6, "cb12197d40c8241a"),
-    # profiles/plain_kernel_c3_2048x20M.md: dram__bytes_read.sum 23.70 GB + dram__bytes_write.sum 22.24 MB
-    "plain/c3": (23.69595008e9 + 22.239488e6, "593e99216de7aa93"),
+    # profiles/tensor_kernel_fp4_c3_2048x20M.md: dram__bytes_read.sum 42.28 GB + dram__bytes_write.sum 43.27 MB
+    "fp4/c3": (42.278863872e9 + 43.27296e6, "21977c727191ffc8"),
+    # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 75.96 GB + dram__bytes_write.sum 78.97 MB
+    "fp8/c3": (75.961072896e9 + 78.967552e6, "21977c727191ffc8"),
+    # profiles/plain_kernel_c3_2048x20M.md: dram__bytes_read.sum 23.04 GB + dram__bytes_write.sum 20.56 MB
+    "plain/c3": (23.043629824e9 + 20.556032e6, "4f253956ab45a8ec"),
 }
 
 
