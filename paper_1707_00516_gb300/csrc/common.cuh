@@ -149,8 +149,9 @@ struct TcLaunch {
     int64_t n_rt[TC_MAXP];
     int32_t kpad[TC_MAXP];  // operand row bytes (a multiple of 128)
     const float *qconst[TC_MAXP];
-    // Query spreading (see spread_row_to_query): the operand's tiles, or 0 / 1
-    // where operand row r holds input query r (batched plans).
+    // Query spreading (see spread_row_to_query): the panel's operand tiles
+    // (0 or 1: operand row r holds input query r).  Batched plans spread each
+    // panel's queries in batch order and give the merge their rows.
     int32_t qspread[TC_MAXP];
     TcSched sched[TC_MAXP];
     int32_t order[TC_MAXP];  // panel order of every group's walk

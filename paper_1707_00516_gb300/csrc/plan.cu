@@ -214,7 +214,8 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
             const fastid_batch &B = batches[b];
             const int p = B.panel;
             for (int64_t i = 0; i < B.n_q; ++i) {
-                const int64_t r = fill[p]++;
+                // the panel's queries, in batch order, spread over its tiles
+                const int64_t r = spread_query_to_row(fill[p]++, rows_pad[p] / TC_TILE_Q);
                 PrepJob &j = prep[prep_base[p] + r];
                 j.src = B.queries_dev + i * B.ld_q;
                 j.mode = B.modes_dev + i;
@@ -253,7 +254,7 @@ fastid_status fastid_plan_create(fastid_ctx *ctx, const fastid_refdb *const *dbs
         L.n_rt[p] = n_rt[p];
         L.kpad[p] = (int32_t)kbytes(p);
         L.qconst[p] = reinterpret_cast<const float *>(W + o_qc[p]);
-        L.qspread[p] = 1;  // prep jobs place every batch row themselves
+        L.qspread[p] = (int32_t)(rows_pad[p] / TC_TILE_Q);  // see the prep jobs
     }
     L.k = k;
     L.epi = EPI_TOPK;
