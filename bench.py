@@ -411,7 +411,7 @@ def time_form(args, s, form, step_fn, pairs_per_step, n_loci, dev, probe):
         roof["frac_of_nominal_ratio_peak"] = achieved / nominal
     key = f"{form}/{args.config}"
     # the captured counters hold for the unmodified workload only
-    tr = None if (args.refs or args.queries) else NCU_TRAFFIC.get(key)
+    tr = None if (args.refs or args.queries or args.k) else NCU_TRAFFIC.get(key)
     roof["traffic"] = tr[0] if tr and tr[1] == kernel_source_hash(form) else None
     return {"value": value, "ms_per_step": ms / args.steps, "roofline": roof, "clocks": clocks,
             "gpu_launches": int(prof["all_launches"])}
@@ -909,6 +909,7 @@ def main(argv=None):
                     help="override the number of references (smaller captures for profiling)")
     ap.add_argument("--queries", type=int, default=None,
                     help="c1-c3: override the number of queries (the recipe's first N)")
+    ap.add_argument("--k", type=int, default=None, help="c1-c3: top-k size instead of the workload's")
     ap.add_argument("--seconds", type=float, default=30.0, help="c5: measured serving time")
     ap.add_argument("--serving-seconds", type=float, default=10.0, help="c3: measured time of the serving sub-run")
     ap.add_argument("--batched-steps", type=int, default=10, help="c3: graph replays of the batched sub-run")
@@ -943,6 +944,11 @@ def main(argv=None):
         w["n_q"] = args.queries
         w["workload"] = w["workload"].replace(f"{old}q_", f"{args.queries}q_").replace(f"{old}mix_",
                                                                                        f"{args.queries}mix_")
+    if args.k:
+        if "n_q" not in w:
+            ap.error("--k applies to c1, c2 and c3")
+        w["workload"] = w["workload"].replace(f"top{w['k']}", f"top{args.k}")
+        w["k"] = args.k
     if args.impl == "reference":
         run_reference(args, w)
         return
