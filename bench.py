@@ -538,7 +538,9 @@ def run_gpu(args, w):
 
 def run_streamed(args, w):
     """The workload with its references in pinned HOST memory, streamed
-    through the device in blocks by fastid_topk_streamed (tensor form)."""
+    through the device in blocks by fastid_topk_streamed: FP8 (each block
+    expanded to the FP8 operand), or with --form fp4packed / fp8packed / plain
+    that form over each block's packed rows."""
     import torch
     from paper_1707_00516_gb300 import binding as B
     from paper_1707_00516_gb300 import peaks as P
@@ -549,7 +551,9 @@ def run_streamed(args, w):
     gen.build_gpu()
     build()
     probe = P.measure()
-    s = Searcher(0, B.FORM_TENSOR)
+    form = args.form if args.form in ("fp8", "fp8packed", "fp4packed", "plain") else "fp8"
+    s = Searcher(0, getattr(B, FORMS[form][0]))
+    sflags = B.REFS_TENSOR if form == "fp8" else 0
     seed = gen.config_seed(w["cfg"])
     n_refs, n_loci, k, T = w["n_refs"], w["n_loci"], w["k"], w["threshold"]
     thr = gen.maf_thresholds(seed, n_loci)
@@ -587,9 +591,9 @@ def run_streamed(args, w):
     del probe_d
 
     def step():
-        B.fastid_topk_streamed(s.ctx, host, n_loci, B.REFS_TENSOR, block, q, modes, k, T, sc, ix)
+        B.fastid_topk_streamed(s.ctx, host, n_loci, sflags, block, q, modes, k, T, sc, ix)
 
-    r = time_form(args, s, "fp8", step, n_q * n_refs, n_loci, dev, probe)
+    r = time_form(args, s, form, step, n_q * n_refs, n_loci, dev, probe)
     # end to end: packed queries in from pinned memory, results out, each step
     hq = q.cpu().pin_memory()
     hm = modes.cpu().pin_memory()
@@ -611,13 +615,13 @@ def run_streamed(args, w):
         nxt = min(min(block, n_refs), 2 * nxt)
         n_blocks += 1
     cfg = workload_config(w)
-    cfg.update({"workload": w["workload"] + f"_refs_streamed_from_pinned_host_block{block}",
+    cfg.update({"workload": w["workload"] + f"_refs_streamed_from_pinned_host_block{block}", "form": form,
                 "blocks_per_step": n_blocks, "host_bytes_per_step": int(host.numel() * 8),
                 "h2d_gbps_pinned_probe": h2d_gbps,
                 "l2": "inputs larger than L2 (references copied from host every step)"})
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": FORMS["fp8"][2], "data": "synthetic", "config": cfg,
+            "vs_baseline": None, "dtype": FORMS[form][2], "data": "synthetic", "config": cfg,
             "e2e": {"value": n_q * n_refs * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(hq.numel() * 8 + hm.numel() + host.numel() * 8),
                     "d2h_bytes_per_step": int(hs.numel() * 4 + hi.numel() * 8)},

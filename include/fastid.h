@@ -298,8 +298,10 @@ fastid_status fastid_compare(fastid_ctx *ctx, const fastid_refdb *db, const uint
  *              pageable memory works but serialises them.  It must stay valid
  *              and unchanged until the stream has passed this call.
  *  n_refs      1 .. 2^31 - 1;  flags: 0 or FASTID_REFS_TENSOR (expand each
- *              block to the FP8 operand and use the tensor form under
- *              FASTID_FORM_AUTO), as in fastid_load_refs.
+ *              block to the FP8 operand, which FASTID_FORM_TENSOR then reads).
+ *              Every other case reads each block's packed rows in the
+ *              context's form: plain, or FP8 or FP4 expanded on chip
+ *              (FASTID_FORM_AUTO: FP4).
  *  block_refs  largest block (>= 1; the first blocks are smaller, from
  *              block_refs / 8 doubling, so that the first comparison starts
  *              early).  Two blocks are on the device at once, each holding
