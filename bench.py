@@ -296,10 +296,10 @@ def kernel_source_hash(form: str) -> str:
 # (profiles/), keyed by form and workload, with the source hash it was taken
 # at.  A changed kernel reports null.
 NCU_TRAFFIC = {
-    # profiles/tensor_kernel_fp4_c3_2048x20M.md: dram__bytes_read.sum 42.28 GB + dram__bytes_write.sum 43.27 MB
-    "fp4/c3": (42.278863872e9 + 43.27296e6, "21977c727191ffc8"),
-    # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 75.96 GB + dram__bytes_write.sum 78.97 MB
-    "fp8/c3": (75.961072896e9 + 78.967552e6, "21977c727191ffc8"),
+    # profiles/tensor_kernel_fp4_c3_2048x20M.md: dram__bytes_read.sum 25.01 GB + dram__bytes_write.sum 39.98 MB
+    "fp4/c3": (25.012413952e9 + 39.982848e6, "9f95518100d29482"),
+    # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 76.39 GB + dram__bytes_write.sum 78.66 MB
+    "fp8/c3": (76.389554176e9 + 78.660864e6, "9f95518100d29482"),
     # profiles/plain_kernel_c3_2048x20M.md: dram__bytes_read.sum 23.04 GB + dram__bytes_write.sum 20.56 MB
     "plain/c3": (23.043629824e9 + 20.556032e6, "4f253956ab45a8ec"),
 }
@@ -538,9 +538,9 @@ def run_gpu(args, w):
 
 def run_streamed(args, w):
     """The workload with its references in pinned HOST memory, streamed
-    through the device in blocks by fastid_topk_streamed: FP8 (each block
-    expanded to the FP8 operand), or with --form fp4packed / fp8packed / plain
-    that form over each block's packed rows."""
+    through the device in blocks by fastid_topk_streamed: FP4 over each
+    block's packed rows (the library's AUTO choice), or with --form fp8 each
+    block expanded to the FP8 operand, or fp8packed / plain over the rows."""
     import torch
     from paper_1707_00516_gb300 import binding as B
     from paper_1707_00516_gb300 import peaks as P
@@ -551,7 +551,7 @@ def run_streamed(args, w):
     gen.build_gpu()
     build()
     probe = P.measure()
-    form = args.form if args.form in ("fp8", "fp8packed", "fp4packed", "plain") else "fp8"
+    form = args.form if args.form in ("fp8", "fp8packed", "fp4packed", "plain") else "fp4packed"
     s = Searcher(0, getattr(B, FORMS[form][0]))
     sflags = B.REFS_TENSOR if form == "fp8" else 0
     seed = gen.config_seed(w["cfg"])
