@@ -43,8 +43,10 @@ def run(s, db, Q, modes, n_loci, k, T):
     torch.cuda.synchronize()
     assert B.fastid_sync_status(s.ctx) == B.OK
     n = int(hc.item())
-    return (sc.cpu().numpy(), ix.cpu().numpy(), (hq[:n].cpu().numpy(), hr[:n].cpu().numpy(), hs[:n].cpu().numpy()),
-            full.cpu().numpy())
+    # scores as uint32, the library's type (empty top-k slots hold 2^32 - 1)
+    return (sc.cpu().numpy().view(np.uint32), ix.cpu().numpy(),
+            (hq[:n].cpu().numpy(), hr[:n].cpu().numpy(), hs[:n].cpu().numpy().view(np.uint32)),
+            full.cpu().numpy().view(np.uint32))
 
 
 @pytest.mark.parametrize("form", sorted(FORMS))
@@ -58,7 +60,7 @@ def test_results_do_not_depend_on_query_order(case, form):
     es, ei = oracle.topk(exp, k, T)
     assert np.array_equal(a_s, es) and np.array_equal(a_i, ei)
     assert np.array_equal(b_s, es[perm]) and np.array_equal(b_i, ei[perm])
-    assert np.array_equal(a_f, exp.astype(np.int64)) and np.array_equal(b_f, exp[perm].astype(np.int64))
+    assert np.array_equal(a_f, exp) and np.array_equal(b_f, exp[perm])
     hq, hr, hsc = oracle.hits(exp, 70)
     assert 0 < hq.size < 200_000
     assert np.array_equal(a_h[0], hq) and np.array_equal(a_h[1], hr) and np.array_equal(a_h[2], hsc)
