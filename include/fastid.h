@@ -464,8 +464,8 @@ fastid_status fastid_plan_destroy(fastid_plan *plan);
  * allocates nothing; the caller still provides inputs and outputs.
  *
  *  - A request whose scratch would exceed FASTID_NOALLOC_SCRATCH_BYTES
- *    (roughly: padded queries x loci / 8, plus ~10 MB of lists for k = 32 on
- *    a 152-SM GPU) returns FASTID_EINVAL with the size it needed in
+ *    (roughly: padded queries x loci / 8, plus ~20 MB of lists for k = 32 on
+ *    a 152-SM GPU, two CTAs a SM) returns FASTID_EINVAL with the size it needed in
  *    fastid_last_error; nothing is enqueued.
  *  - The first call on a device looks up the array's device address there
  *    (and may make CUDA load that device code); make that first call before
@@ -480,7 +480,7 @@ fastid_status fastid_plan_destroy(fastid_plan *plan);
  *    the GPU -- on different streams or host threads, or with different
  *    contexts -- race on it: serialise them.
  */
-#define FASTID_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define FASTID_NOALLOC_SCRATCH_BYTES (32u << 20)
 fastid_status fastid_topk_noalloc(fastid_ctx *ctx, const fastid_refdb *db, const uint64_t *queries_dev,
                                   int64_t ld_q, int64_t n_q, const uint8_t *modes_dev, int32_t k,
                                   uint32_t threshold, uint32_t *out_scores_dev, int64_t *out_idx_dev,

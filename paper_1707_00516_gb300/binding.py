@@ -26,7 +26,7 @@ REFS_TENSOR, REFS_FP4 = 1, 2
 MAX_K = 32
 MAX_LOCI = 65536
 NO_THRESHOLD = 0xFFFFFFFF
-NOALLOC_SCRATCH_BYTES = 16 << 20
+NOALLOC_SCRATCH_BYTES = 32 << 20
 VIEW_ALIGN = 256
 (VARIANT_AUTO, VARIANT_TENSOR_N256, VARIANT_TENSOR_N128, VARIANT_TENSOR_PAIR, VARIANT_TENSOR_FP4,
  VARIANT_TENSOR_FP4_PAIR, VARIANT_TENSOR_PAIR_2SM, VARIANT_TENSOR_FP4_PAIR_2SM) = range(8)

@@ -14,7 +14,8 @@
 //     mode 1: a = 1, b = 0    ->  |R| - G       = popc(R AND NOT Q)  (Eq. 1)
 //
 // CTA tile: 128 references x 128 queries, 256 threads, each thread owns 8
-// references (rows tr + 16 i) and 8 queries (rows tq + 16 j) of the tile.
+// references (rows tr + 16 i) and 8 queries (rows tq + 16 j) of the tile;
+// two CTAs an SM.
 // The grid is persistent: CTA c walks the units [c U / G, (c+1) U / G) of the
 // query-tile-major list of (query tile, reference tile) units, so within one
 // query tile a CTA sees references in increasing order.
@@ -141,8 +142,27 @@ __device__ __forceinline__ uint32_t and_popc8(const uint4 ra, const uint4 rb, co
     return (__popc(d) * two + __popc(t)) * two + (acc + __popc(s3) + __popc(x7));
 }
 
+// A reference operand's 16 bytes, read from shared memory for every four
+// query columns.  The 8 x 8 register tile then holds its 64 counters, four
+// query columns and one reference row, within 128 registers, so two CTAs
+// share an SM: four warps per scheduler instead of two, to hide the POPC and
+// LOP3 latencies.  Holding all eight reference rows instead takes 177
+// registers and one CTA per SM (2048 x 20M: 480 ms against 435 ms); reading
+// the row for every single query column keeps two CTAs but triples the
+// shared-memory wavefronts (459 ms).  The volatile load keeps the compiler
+// from merging the two reads of a row back into registers; within a warp it
+// is a broadcast of two addresses, one shared-memory wavefront.
+__device__ __forceinline__ uint4 lds128_once(const uint32_t *p) {
+    uint4 v;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(a));
+    return v;
+}
+
 template <int EPI>
-__global__ void __launch_bounds__(PL_THREADS) plain_kernel(const PlainArgs args) {
+__global__ void __launch_bounds__(PL_THREADS, 2) plain_kernel(const PlainArgs args) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint32_t(*sR)[PL_TR][KCP] = reinterpret_cast<uint32_t(*)[PL_TR][KCP]>(smem_raw);
     uint32_t(*sQ)[PL_TQ][KCP] =
@@ -230,18 +250,23 @@ __global__ void __launch_bounds__(PL_THREADS) plain_kernel(const PlainArgs args)
             static_assert(PL_KC % 8 == 0, "eight-word carry-save groups");
 #pragma unroll
             for (int kk = 0; kk < PL_KC; kk += 8) {
-                uint4 ra[8], rb[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    ra[i] = *reinterpret_cast<const uint4 *>(&sR[st][tr + 16 * i][kk]);
-                    rb[i] = *reinterpret_cast<const uint4 *>(&sR[st][tr + 16 * i][kk + 4]);
-                }
+                for (int jh = 0; jh < 8; jh += 4) {  // four query columns at a time
+                    uint4 qa[4], qb[4];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const uint4 qa = *reinterpret_cast<const uint4 *>(&sQ[st][tq + 16 * j][kk]);
-                    const uint4 qb = *reinterpret_cast<const uint4 *>(&sQ[st][tq + 16 * j][kk + 4]);
+                    for (int j = 0; j < 4; ++j) {
+                        qa[j] = *reinterpret_cast<const uint4 *>(&sQ[st][tq + 16 * (jh + j)][kk]);
+                        qb[j] = *reinterpret_cast<const uint4 *>(&sQ[st][tq + 16 * (jh + j)][kk + 4]);
+                    }
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) acc[i][j] = and_popc8(ra[i], rb[i], qa, qb, acc[i][j], args.two);
+                    for (int i = 0; i < 8; ++i) {
+                        // read once per four query columns (see lds128_once)
+                        const uint4 ra = lds128_once(&sR[st][tr + 16 * i][kk]);
+                        const uint4 rb = lds128_once(&sR[st][tr + 16 * i][kk + 4]);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            acc[i][jh + j] = and_popc8(ra, rb, qa[j], qb[j], acc[i][jh + j], args.two);
+                    }
                 }
             }
             __syncthreads();

@@ -102,9 +102,9 @@ def test_noalloc_allocates_nothing(env):
 
 def test_noalloc_rejects_oversized_request(env):
     B, s, db, thr, n_refs, n_loci, seed, R = env
-    # 70,000 padded queries x 1024 bits of loci = 8.96 MB of padded queries
-    # alone, plus the lists: over the fixed 16 MiB
-    n_q = 70000
+    # 150,000 padded queries x 1024 bits of loci = 19.2 MB of padded queries
+    # alone, plus ~50 MB of lists: over the fixed 32 MiB
+    n_q = 150000
     q = torch.zeros((n_q, (n_loci + 63) // 64), dtype=torch.int64, device="cuda")
     modes = torch.ones(n_q, dtype=torch.uint8, device="cuda")
     sc = torch.empty((n_q, 32), dtype=torch.int32, device="cuda")
