@@ -204,13 +204,14 @@ def refuse_multi_gpu(args):
 # ----------------------------------------------------------------------------
 
 def oracle_sample_step(q_alleles: np.ndarray, modes: np.ndarray, seed: int, n_refs: int, thr: np.ndarray,
-                       sample_rows: np.ndarray, k: int, threshold: int):
+                       sample_rows: np.ndarray, k: int, threshold: int, threads: int = 0):
     """The oracle on a bounded sample: every query against the sampled
-    references (per-locus scores, then top-k over the sample)."""
+    references (per-locus scores, then top-k over the sample), on `threads`
+    host threads (0: all)."""
     import oracle
     R = gen.allele_rows(seed, gen.STREAM_DB, sample_rows, thr)
     t0 = time.perf_counter()
-    mis, une = oracle.scores(R, q_alleles)
+    mis, une = oracle.scores(R, q_alleles, threads)
     s = oracle.select(mis, une, modes)
     oracle.topk(s, k, threshold, ref_ids=sample_rows)
     return time.perf_counter() - t0
@@ -232,9 +233,16 @@ def cpu_baseline(w: dict, recipe, thr, target_s: float = 12.0):
         t = oracle_sample_step(q, modes, seed, w["n_refs"], thr, rows, w["k"], w["threshold"])
         if t >= 0.6 * target_s or S == S_max:
             break
-    return {"value": q.shape[0] * S / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+    cores = oracle.max_threads()
+    # the same oracle on one host thread, over a sample sized to about 3 s
+    S1 = int(max(8, min(S, 3.0 * S / (max(t, 1e-3) * max(1, cores)))))
+    rows1 = np.sort(rng.choice(w["n_refs"], S1, replace=False))
+    t1 = oracle_sample_step(q, modes, seed, w["n_refs"], thr, rows1, w["k"], w["threshold"], threads=1)
+    return {"value": q.shape[0] * S / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"all {q.shape[0]} queries x {S} sampled references (per-locus scores + top-{w['k']}), "
-                      f"{t:.1f} s"}
+                      f"{t:.1f} s",
+            "single_thread": {"value": q.shape[0] * S1 / t1, "unit": UNIT, "cores": 1,
+                              "sample": f"all {q.shape[0]} queries x {S1} sampled references, {t1:.1f} s"}}
 
 
 def run_reference(args, w):
