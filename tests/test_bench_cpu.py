@@ -79,3 +79,22 @@ def test_roofline_peaks_from_probe():
     assert bench.roof_peak("fp8packed", probe, 152)[0] == p8
     p4, _, how = bench.roof_peak("fp4", probe, 152)
     assert abs(p4 - 32768 * 152 * mhz * 1e6 / 1e12) < 1e-6 and "N224" in how
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    """The default line's cpu_baseline: the oracle on every host core over a
+    calibrated sample, and the same oracle on one thread beside it (a small
+    C3-shaped workload, so that the test takes seconds)."""
+    import gen
+    import oracle
+    oracle.build()
+    w = dict(bench.WORKLOADS["c3"])
+    w["n_refs"] = 100_000
+    recipe = bench.recipe_for("c3", n_refs=w["n_refs"], n_q=64)
+    thr = gen.maf_thresholds(gen.config_seed(w["cfg"]), w["n_loci"])
+    cb = bench.cpu_baseline(w, recipe, thr, target_s=0.5)
+    assert cb["kind"] == "oracle" and cb["cores"] == oracle.max_threads() and cb["value"] > 0
+    one = cb["single_thread"]
+    assert one["cores"] == 1 and one["value"] > 0 and one["unit"] == cb["unit"]
+    # one thread is never much faster than all of them
+    assert one["value"] < 1.5 * cb["value"]
