@@ -55,12 +55,15 @@ class _Slot:
 
 def slot_device_bytes(n_loci: int, max_wave: int, k: int, tensor: bool, sms: int = 152) -> int:
     """Device memory one slot can hold at once: its buffers plus the scratch
-    fastid_topk takes for a full wave."""
+    fastid_topk takes for a full wave: the query operand and the per-segment
+    top-k lists, at most 4 x SMs lists of 128 queries (the plain kernel's two
+    CTAs an SM, each over at most two query tiles for waves up to 38,912
+    queries; the tensor kernel's slots are fewer)."""
     words = (n_loci + 63) // 64
     kpad = (n_loci + 127) // 128 * 128
     n_pad = (max_wave + 127) // 128 * 128
     buffers = max_wave * (8 * words + 1 + 12 * k)
-    scratch = n_pad * (kpad + 4 if tensor else 8 * words + 8) + sms * 3 * 128 * k * 8
+    scratch = n_pad * (kpad + 4 if tensor else 8 * words + 8) + sms * 4 * 128 * k * 8
     return buffers + scratch
 
 
