@@ -66,3 +66,45 @@ def test_mutant_is_caught(name, tmp_path, golden_dir, monkeypatch):
 
 def test_unmutated_passes(golden_dir):
     assert _pins_pass(golden_dir)
+
+
+# The oracle's Python steps (mode selection, top-k, hit list), mutated in a
+# copy of the module's source; the pins of those steps must catch each one.
+PY_MUTANTS = {
+    "threshold_exclusive": ("keep = np.nonzero(s[q] <= threshold)[0]", "keep = np.nonzero(s[q] < threshold)[0]"),
+    "ties_by_descending_ref": ("order = keep[np.lexsort((ids[keep], s[q, keep]))][:k]",
+                               "order = keep[np.lexsort((-ids[keep], s[q, keep]))][:k]"),
+    "modes_swapped": ("return np.where(m, une, mis).astype(np.uint32)",
+                      "return np.where(m, mis, une).astype(np.uint32)"),
+    "hits_by_ref_first": ("order = np.lexsort((rid, qid))", "order = np.lexsort((qid, rid))"),
+}
+
+
+def _py_pins_pass():
+    import test_oracle_pins as P
+    checks = [P.test_topk_ties_and_threshold, P.test_topk_against_python_sorted, P.test_hits_against_python,
+              P.test_planted_recovery]
+    for c in checks:
+        try:
+            c()
+        except AssertionError:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_python_mutant_is_caught(name, monkeypatch):
+    import types
+    src = open(oracle.__file__).read()
+    old, new = PY_MUTANTS[name]
+    assert src.count(old) == 1, name
+    mut = types.ModuleType("oracle_mutant")
+    mut.__file__ = oracle.__file__  # the C library resolves next to the real module
+    exec(compile(src.replace(old, new), oracle.__file__, "exec"), mut.__dict__)
+    for fname in ("select", "topk", "hits"):
+        monkeypatch.setattr(oracle, fname, getattr(mut, fname))
+    assert not _py_pins_pass(), f"mutant {name} survived the pins"
+
+
+def test_python_unmutated_passes():
+    assert _py_pins_pass()
