@@ -192,6 +192,21 @@ __global__ void __launch_bounds__(PL_THREADS, 2) plain_kernel(const PlainArgs ar
 
     // Loader mapping: each stage is 128 rows x 16 words per operand = 512
     // 16-byte chunks; 256 threads copy 2 chunks of R and 2 of Q.
+    // Stage s of a unit goes to buffer (g + s) & 1, g counting the stages of
+    // the CTA's earlier units, so that the next unit's first stage can be
+    // copied into the free buffer during this unit's last stage and epilogue.
+    auto issue_stage = [&](int st, const uint32_t *gR_, const uint32_t *gQ_, int kc) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            int chunk = tid + t * PL_THREADS;  // 0..511
+            int row = chunk >> 2, part = chunk & 3;
+            cp_async16(&sR[st][row][part * 4], gR_ + row * args.ld32 + kc * PL_KC + part * 4);
+            cp_async16(&sQ[st][row][part * 4], gQ_ + row * args.ld32 + kc * PL_KC + part * 4);
+        }
+        cp_async_commit();
+    };
+    int g = 0;
+    bool staged = false;  // this unit's first stage is already in flight
     int seg = 0;
     int64_t qt_prev = -1;
     for (int64_t u = u_begin; u < u_end; ++u) {
@@ -220,28 +235,22 @@ __global__ void __launch_bounds__(PL_THREADS, 2) plain_kernel(const PlainArgs ar
         const uint32_t *gR = args.refs32 + r0 * args.ld32;
         const uint32_t *gQ = args.q32 + q0 * args.ld32;
 
-        auto load_stage = [&](int st, int kc) {
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                int chunk = tid + t * PL_THREADS;  // 0..511
-                int row = chunk >> 2, part = chunk & 3;
-                cp_async16(&sR[st][row][part * 4], gR + row * args.ld32 + kc * PL_KC + part * 4);
-                cp_async16(&sQ[st][row][part * 4], gQ + row * args.ld32 + kc * PL_KC + part * 4);
-            }
-            cp_async_commit();
-        };
-
         uint32_t acc[8][8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[i][j] = 0;
 
-        load_stage(0, 0);
+        if (!staged) issue_stage(g & 1, gR, gQ, 0);
         for (int kc = 0; kc < args.n_kc; ++kc) {
-            const int st = kc & 1;
+            const int st = (g + kc) & 1;
             if (kc + 1 < args.n_kc) {
-                load_stage(st ^ 1, kc + 1);
+                issue_stage(st ^ 1, gR, gQ, kc + 1);
+                cp_async_wait<1>();
+            } else if (u + 1 < u_end) {  // the next unit's first stage
+                const int64_t qn = (u + 1) / P.n_rt;
+                const int64_t rn = (u + 1) - qn * P.n_rt;
+                issue_stage(st ^ 1, args.refs32 + rn * PL_TR * args.ld32, args.q32 + qn * PL_TQ * args.ld32, 0);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
@@ -271,6 +280,8 @@ __global__ void __launch_bounds__(PL_THREADS, 2) plain_kernel(const PlainArgs ar
             }
             __syncthreads();
         }
+        g += args.n_kc;
+        staged = u + 1 < u_end;
 
         // ---- epilogue: scores ----
         uint32_t nr[8];
