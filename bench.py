@@ -308,8 +308,8 @@ NCU_TRAFFIC = {
     "fp4/c3": (25.012413952e9 + 39.982848e6, "9f95518100d29482"),
     # profiles/tensor_kernel_c3_2048x20M.md: dram__bytes_read.sum 76.39 GB + dram__bytes_write.sum 78.66 MB
     "fp8/c3": (76.389554176e9 + 78.660864e6, "9f95518100d29482"),
-    # profiles/plain_kernel_c3_2048x20M.md: dram__bytes_read.sum 50.54 GB + dram__bytes_write.sum 29.03 MB
-    "plain/c3": (50.540628992e9 + 29.025792e6, "af95ea6864f04d36"),
+    # profiles/plain_kernel_c3_2048x20M.md: dram__bytes_read.sum 45.61 GB + dram__bytes_write.sum 28.82 MB
+    "plain/c3": (45.612705280e9 + 28.819456e6, "a0d17b3f0ba88167"),
 }
 
 
