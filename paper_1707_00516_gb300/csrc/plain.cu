@@ -147,8 +147,9 @@ __device__ __forceinline__ uint32_t and_popc8(const uint4 ra, const uint4 rb, co
 // query columns and one reference row, within 128 registers, so two CTAs
 // share an SM: four warps per scheduler instead of two, to hide the POPC and
 // LOP3 latencies.  Holding all eight reference rows instead takes 177
-// registers and one CTA per SM (2048 x 20M: 480 ms against 435 ms); reading
-// the row for every single query column keeps two CTAs but triples the
+// registers and one CTA per SM (2048 x 20M: 480 ms against 435 ms, both
+// without the cross-unit copy of the next unit's first stage); reading the
+// row for every single query column keeps two CTAs but triples the
 // shared-memory wavefronts (459 ms).  The volatile load keeps the compiler
 // from merging the two reads of a row back into registers; within a warp it
 // is a broadcast of two addresses, one shared-memory wavefront.
