@@ -108,3 +108,29 @@ def test_peaks_operand_encoding():
     v = np.array([[1, -1, 0, 1]])
     assert encode(v, False).tolist() == [[0x38, 0xB8, 0x00, 0x38]]
     assert encode(v, True).tolist() == [[0xA2, 0x20]]
+
+
+def test_readme_c_example_compiles_and_links(lib, tmp_path):
+    """The README's C example compiles as C11 against include/fastid.h with
+    every warning an error, and links against libfastid.so and the CUDA
+    runtime with no undefined symbol (nothing is run)."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc missing")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        pytest.skip("CUDA headers missing")
+    readme = open(os.path.join(os.path.dirname(INCLUDE), "README.md")).read()
+    blocks = re.findall(r"```c\n(.*?)```", readme, flags=re.S)
+    assert len(blocks) == 1
+    src = tmp_path / "example.c"
+    src.write_text(blocks[0])
+    libdir = os.path.dirname(LIB)
+    cudalib = next((d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"))
+                    if os.path.exists(os.path.join(d, "libcudart.so"))), None)
+    if cudalib is None:
+        pytest.skip("libcudart missing")
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-shared", "-fPIC", "-I", INCLUDE,
+                    "-I", os.path.join(cuda, "include"), str(src), "-o", str(tmp_path / "libexample.so"),
+                    "-L", libdir, "-lfastid", "-L", cudalib, "-lcudart", "-Wl,--no-undefined"],
+                   check=True, capture_output=True, text=True)
